@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of direct TSQR on GB300 (Benson, Gleich, Demmel, arXiv:1301.1071).
+
+Default workload: the stability-sweep matrix, m = 8,000,000 x n = 25, FP64,
+A = G diag(sigma) V^T with sigma log-spaced from 1 to 1e-15 (synthetic,
+seeded).  One step = one direct-TSQR forward pass (Step 1 local Householder of
+every row block, the Step-2 tree of Alg. 2 with the top QR and sign fix, and
+Step 3 Q formation) on inputs already resident in HBM.  Inputs (1.6 GB) are
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload sweep|small] [--no-extras]
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+plain FP64 Householder QR) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import tsqr_inputs as ti  # noqa: E402
+
+METRIC = "direct-TSQR rows/s and HBM GB/s (fwd; fwd+bwd) at stated ||Q^TQ-I||, 1 GB300"
+HBM_PEAK_FALLBACK = 6800.0  # GB/s, used only when MEASURED_PEAKS.json is absent
+FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (152 SMs x ~2 DFMA/clk x 2 flop x 2.07 GHz)
+
+WORKLOADS = {
+    "sweep": dict(m=8_000_000, n=25, dtype="f64", kappa=1e15, block_rows=0, seed=ti.SEED_SWEEP,
+                  name="stability-sweep matrix 8,000,000x25 FP64, A=G diag(sigma) V^T, "
+                       "sigma log-spaced 1..1e-15 (kappa 1e15)"),
+    "small": dict(m=100_000, n=10, dtype="f64", kappa=None, block_rows=1000, seed=ti.SEED_SMALL,
+                  name="100,000x10 FP64 i.i.d. N(0,1), row blocks of 1,000"),
+}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, device=None) -> float:
+    """Max of a scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(rows_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job rows/s of `world` replicas, each factoring `rows_per_rank`
+    rows per step, timed by the slowest rank."""
+    return rows_per_rank * world * steps / (max_ms * 1e-3)
+
+
+def make_input(w, rows=None):
+    """The workload matrix, or only its first `rows` rows."""
+    if w["kappa"] is None:
+        return ti.gaussian(w["m"], w["n"], w["seed"], rows=rows)
+    return ti.conditioned(w["m"], w["n"], w["kappa"], w["seed"], rows=rows)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", HBM_PEAK_FALLBACK)), "measured"
+    return HBM_PEAK_FALLBACK, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1301_1071_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{kernel}@{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tsqr_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(A_host: np.ndarray, target_s: float = 12.0, max_rows: int = 2_000_000):
+    """The oracle (plain single-threaded FP64 Householder QR with explicit Q)
+    on a bounded row sample of the same matrix."""
+    import oracle
+    n = A_host.shape[1]
+    rows = 100_000
+    t0 = time.perf_counter()
+    oracle.householder_qr(A_host[:rows])
+    t = time.perf_counter() - t0
+    if t < target_s / 3:
+        rows = int(min(max_rows, A_host.shape[0], rows * target_s / max(t, 1e-3)))
+        t0 = time.perf_counter()
+        oracle.householder_qr(A_host[:rows])
+        t = time.perf_counter() - t0
+    return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows:,} rows x {n} of the workload matrix, one thin QR (Q and R), "
+                      f"{t:.1f} s"}
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    rows = min(w["m"], 1_000_000)
+    sample = make_input(w, rows=rows)
+    for _ in range(args.warmup):
+        oracle.householder_qr(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.householder_qr(sample)
+    dt = time.perf_counter() - t0
+    value = rows * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w["name"], "m": w["m"], "n": w["n"]},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {rows:,} rows x {w['n']} of the workload matrix per step"},
+        "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true", help="skip comparators / fwd+bwd / cpu baseline")
+    ap.add_argument("--m", type=int, default=0, help="override the row count (profiling a smaller case)")
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.m:
+        w["m"] = args.m
+        w["name"] = w["name"].replace(f"{WORKLOADS[args.workload]['m']:,}", f"{args.m:,}")
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+    import paper_1301_1071_gb300 as T
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    m, n = w["m"], w["n"]
+    A_host = make_input(w)
+    A = torch.from_numpy(A_host).to(dev)
+    Q = torch.empty_like(A)
+    R = torch.empty(n, n, dtype=torch.float64, device=dev)
+    work = torch.empty(T.workspace_size(T.OP_DIRECT, m, n, A.dtype, w["block_rows"]), dtype=torch.uint8,
+                       device=dev)
+    bench_kw = dict(block_rows=w["block_rows"], work=work, out=(Q, R), check=False)
+
+    for _ in range(args.warmup):
+        T.direct(A, **bench_kw)
+    torch.cuda.synchronize()
+    T.direct(A, block_rows=w["block_rows"], work=work, out=(Q, R), check=True)  # raises on a device error
+
+    # ---- device-resident timed region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    start.record()
+    for k in range(args.steps):
+        T.direct(A, stage_events=evs[k], **bench_kw)
+    end.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    total_ms = reduce_max(start.elapsed_time(end), dev)
+    ms_step = total_ms / args.steps
+    st1 = [e[0].elapsed_time(e[1]) for e in evs]
+    st2 = [e[1].elapsed_time(e[2]) for e in evs]
+    st3 = [e[2].elapsed_time(e[3]) for e in evs]
+    s1, s2, s3 = statistics.mean(st1), statistics.mean(st2), statistics.mean(st3)
+    rows_s = replica_throughput(m, args.steps, ws, total_ms)
+    elem = 8 if A.dtype == torch.float64 else 4
+    alg_bytes = 4 * m * n * elem
+    gbs = alg_bytes / (ms_step * 1e-3) / 1e9
+    hbm_peak, peak_src = load_peaks()
+
+    # dominant kernel: Step 1 (k_local_qr) or Step 3 (k_form_q); both are
+    # binary64 FMA-bound: 2 m n^2 algorithmic flops per launch
+    dom, dom_ms = ("k_local_qr", s1) if s1 >= s3 else ("k_form_q", s3)
+    flops = 2.0 * m * n * n
+    achieved = flops / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": load_traffic(dom, args.workload),
+                "kernel": dom, "peak_source": "nominal FP64 rate (recipe table); probe measured 1196 GFLOP/s",
+                "hbm_view": {"achieved_gbs": 2 * m * n * elem / (dom_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                             "frac": 2 * m * n * elem / (dom_ms * 1e-3) / 1e9 / hbm_peak,
+                             "peak_source": peak_src}}
+
+    # ---- accuracy at the stated kappa (library check with torch, FP64)
+    with torch.no_grad():
+        G = Q.T @ Q
+        G -= torch.eye(n, dtype=G.dtype, device=dev)
+        orth2 = float(torch.linalg.eigvalsh(G.cpu()).abs().max())
+        res = 0.0
+        an = 0.0
+        for r0 in range(0, m, 1 << 21):
+            blk = A[r0:r0 + (1 << 21)]
+            res += float(((blk - Q[r0:r0 + (1 << 21)] @ R) ** 2).sum())
+            an += float((blk ** 2).sum())
+        resF = (res / an) ** 0.5
+
+    # ---- end to end: pinned host A -> device, factor, Q and R back to the host
+    Ah = torch.from_numpy(A_host).pin_memory()
+    Qh = torch.empty_like(Ah).pin_memory()
+    Rh = torch.empty(n, n, dtype=torch.float64).pin_memory()
+    for _ in range(1):
+        A.copy_(Ah, non_blocking=True)
+        T.direct(A, **bench_kw)
+        Qh.copy_(Q, non_blocking=True)
+        Rh.copy_(R, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k_e2e = max(3, args.steps // 2)
+    barrier()
+    e0.record()
+    for _ in range(k_e2e):
+        A.copy_(Ah, non_blocking=True)
+        T.direct(A, **bench_kw)
+        Qh.copy_(Q, non_blocking=True)
+        Rh.copy_(R, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = reduce_max(e0.elapsed_time(e1), dev)
+    e2e = {"value": replica_throughput(m, k_e2e, ws, e2e_ms), "unit": "rows/s",
+           "h2d_bytes_per_step": m * n * elem, "d2h_bytes_per_step": m * n * elem + n * n * 8}
+
+    launches = T.launch_count(T.OP_DIRECT, m, n, A.dtype, w["block_rows"]) * args.steps
+    line = {
+        "metric": METRIC, "value": rows_s, "unit": "rows/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "m": m, "n": n, "block_rows": w["block_rows"] or "auto",
+                   "l2": "inputs (1.6 GB) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
+        "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm_peak,
+        "orth_error_2": orth2, "residual_F": resF,
+        "step_ms": {"step1_local_qr": s1, "step2_tree": s2, "step3_form_q": s3},
+        "step_fractions": {"step1": s1 / (s1 + s2 + s3), "step2": s2 / (s1 + s2 + s3),
+                           "step3": s3 / (s1 + s2 + s3)},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+
+    if not args.no_extras and rank == 0:
+        line["extras"] = extras(T, torch, A, n, m, dev)
+    if not args.no_extras and rank == 0:
+        line["cpu_baseline"] = cpu_baseline(A_host)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(T, torch, A, n, m, dev, steps=3):
+    """fwd+bwd and the unstable comparators on the same matrix."""
+    out = {}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    def orth(Qx):
+        G = Qx.T @ Qx
+        G -= torch.eye(n, dtype=G.dtype, device=dev)
+        return float(torch.linalg.eigvalsh(G.double().cpu()).abs().max())
+
+    g = torch.Generator(device=dev)
+    g.manual_seed(ti.SEED_GRAD)
+    WQ = torch.randn(A.shape, dtype=A.dtype, device=dev, generator=g)
+    WR = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    Q, R = T.direct(A)
+
+    def fb():
+        Qx, Rx = T.direct(A, check=False)
+        T.backward(Qx, Rx, WQ, WR, check=False)
+
+    ms = timed(fb)
+    out["fwd_bwd"] = {"rows_s": m / (ms * 1e-3), "ms": ms,
+                      "hbm_gbs_algorithmic": 9 * m * n * A.element_size() / (ms * 1e-3) / 1e9}
+    for name, fn in [("cholqr", lambda: T.cholqr(A, refine=0, check=False)),
+                     ("cholqr_ir", lambda: T.cholqr(A, refine=1, check=False)),
+                     ("indirect_ir", lambda: T.indirect_refine(A, refine=1, check=False))]:
+        try:
+            ms = timed(fn)
+            Qx, _ = fn()
+            torch.cuda.synchronize()
+            err = orth(Qx)
+        except Exception as e:  # a breakdown is a result, not a crash
+            ms, err = float("nan"), f"{type(e).__name__}: {e}"
+        out[name] = {"rows_s": m / (ms * 1e-3) if ms == ms else None, "ms": ms, "orth_error_2": err}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * tsqr.h -- C-ABI of the GB300 (sm_103a) direct-TSQR library.
+ *
+ * Method: A. R. Benson, D. F. Gleich, J. Demmel, "Direct QR factorizations
+ * for tall-and-skinny matrices in MapReduce architectures" (arXiv:1301.1071).
+ *
+ * Problem statement (Sec. I): A is m x n, full rank, m >> n; the thin QR
+ * factorisation is A = Q R with Q m x n (orthonormal columns) and R n x n
+ * upper triangular.  This library normalises diag(R) >= 0, which makes the
+ * factorisation unique for full-rank A (Sec. II-A).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are dense ROW-MAJOR (the paper's row-wise layout, Sec. III-A):
+ *    element (i, j) of A is A[i * lda + j].  Version 1 requires every leading
+ *    dimension to equal n and every base pointer to be 16-byte aligned, else
+ *    TSQR_ERR_ALIGN is returned.
+ *  - All data pointers (A, Q, R, U, S, V, dQ, dR, dA, work) are DEVICE
+ *    pointers owned by the caller.  The library allocates no device memory;
+ *    it keeps no pointer after a call returns.  Inputs are read-only.
+ *  - dtype selects the storage (and compute) type of the tall matrices
+ *    (A, Q, U, dQ, dA): TSQR_F64 (IEEE binary64) or TSQR_F32 (binary32).
+ *    The small n x n matrices R, V, dR and the singular values S are always
+ *    binary64, as are all stacked R factors and the reduction tree (Step 2).
+ *  - work / work_bytes: device workspace of at least the size returned by
+ *    tsqr_workspace_size() for the same (op, m, n, dtype, opts).  It holds
+ *    the device status word, the stacked R factors, the compact-WY T factors
+ *    and the Step-2 coefficient blocks.  Its first 256 bytes are the status
+ *    header; the rest need no initialisation.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call only enqueues work on it and returns; argument, shape,
+ *    alignment and workspace errors are returned synchronously, before any
+ *    launch.  Data-dependent errors (NOT_SPD, SINGULAR, NONFINITE, TIMEOUT,
+ *    NOCONV) are written to the status word in the workspace: read them with
+ *    tsqr_read_status(), or set opts->sync = 1 to have the call synchronise
+ *    the stream and return that status.  No kernel traps.
+ *  - Calls that share a workspace must be ordered (same stream).
+ */
+#ifndef TSQR_GB300_H
+#define TSQR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSQR_NMAX 100 /* largest supported n */
+
+typedef enum tsqr_status {
+  TSQR_OK = 0,
+  TSQR_ERR_ARG = 1,       /* null pointer, bad enum/option value */
+  TSQR_ERR_SHAPE = 2,     /* n < 1, n > TSQR_NMAX, m < n, block_rows out of range */
+  TSQR_ERR_ALIGN = 3,     /* a leading dimension != n, or a pointer not 16-byte aligned */
+  TSQR_ERR_WORKSPACE = 4, /* work == NULL or work_bytes too small */
+  TSQR_ERR_CUDA = 5,      /* a CUDA runtime call or launch failed */
+  TSQR_ERR_NOT_SPD = 6,   /* device: Cholesky breakdown (cholqr) */
+  TSQR_ERR_SINGULAR = 7,  /* device: zero diagonal of R where R^-1 is applied */
+  TSQR_ERR_NONFINITE = 8, /* device: NaN or Inf met in an input or a result */
+  TSQR_ERR_TIMEOUT = 9,   /* device: a bounded wait on a bulk copy gave up */
+  TSQR_ERR_NOCONV = 10    /* device: the Jacobi SVD of R did not converge */
+} tsqr_status;
+
+typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
+
+/* Which computation a workspace is sized for. */
+typedef enum tsqr_op {
+  TSQR_OP_DIRECT = 0,
+  TSQR_OP_SVD = 1,
+  TSQR_OP_CHOLQR = 2,
+  TSQR_OP_INDIRECT = 3,
+  TSQR_OP_BACKWARD = 4
+} tsqr_op;
+
+typedef struct tsqr_opts {
+  int64_t block_rows; /* rows per Step-1 row block; 0 = automatic.  Must be >= n
+                         and no larger than the kernel's per-block capacity. */
+  int32_t tree_fanout; /* R factors merged per Step-2 tree node; 0 = automatic (>= 2) */
+  int32_t sync;        /* 1 = synchronise the stream and return the device status */
+  /* Optional stage timing (tsqr_direct, tsqr_svd): NULL, or 4 cudaEvent_t
+     handles (as void*) recorded on the stream at the start, after Step 1,
+     after Step 2 (tree up, top QR, SVD, tree down) and after Step 3. */
+  void* const* stage_events;
+  int32_t reserved[2]; /* must be zero */
+} tsqr_opts;
+
+/*
+ * Workspace bytes needed by `op` for an m x n matrix of `dtype` under `opts`
+ * (NULL = defaults).  Host-only; launches nothing.
+ */
+tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
+                                const tsqr_opts* opts, size_t* bytes);
+
+/*
+ * Direct TSQR (Sec. III-B, with the recursive Step 2 of Sec. III-C, Alg. 2):
+ *   Step 1: each row block A_i (block_rows rows, the last one may be short)
+ *           is factored by Householder QR, A_i = Q1_i R_i; Q1_i is kept in
+ *           compact-WY form (Y_i written into Q's storage, T_i into work).
+ *   Step 2: the stacked R_i (p*n x n, binary64) are factored, recursively
+ *           while the stack is taller than one tree node (Alg. 2), giving the
+ *           coefficient blocks Q2_i and R.
+ *   Step 3: Q_i = Q1_i Q2_i, written over Y_i.
+ * In:  A (m x n, dtype, lda == n).  Out: Q (m x n, dtype, ldq == n; may NOT
+ * alias A), R (n x n binary64, ldr == n, upper triangular, diag(R) >= 0).
+ */
+tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                        void* Q, int64_t ldq, double* R, int64_t ldr,
+                        void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
+
+/*
+ * SVD variant (Sec. III-B, SVD paragraph): Step 2 also computes
+ * R = U_R diag(S) V^T (one-sided Jacobi in binary64, S descending, each
+ * (u_j, v_j) signed so that the largest-|.| entry of v_j is positive) and
+ * U_R is folded into the coefficient blocks, so Step 3 writes U = Q U_R
+ * directly without writing Q (same data passes as the QR).
+ * Out: U (m x n, dtype), S (n, binary64), V (n x n binary64, ldv == n).
+ */
+tsqr_status tsqr_svd(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                     void* U, int64_t ldu, double* S, double* V, int64_t ldv,
+                     void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
+
+/*
+ * Cholesky QR (Sec. II-A; Q = A R^{-1} of Sec. II-C): R = chol(A^T A) with
+ * A^T A accumulated in binary64, Q = A R^{-1}.  refine_steps >= 0 extra
+ * passes repeat the method on the computed Q (iterative refinement, Sec. I):
+ * Q <- Q R2^{-1}, R <- R2 R (binary64).  A Cholesky breakdown sets
+ * TSQR_ERR_NOT_SPD in the status word (Q, R are then undefined).
+ */
+tsqr_status cholqr(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                   void* Q, int64_t ldq, double* R, int64_t ldr, int32_t refine_steps,
+                   void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
+
+/*
+ * Indirect TSQR with iterative refinement (Sec. II-B, II-C): R1 from the
+ * R-only TSQR of A (Steps 1-2 without Q1/Q2), Q0 = A R1^{-1}; each of the
+ * refine_steps passes repeats it on the computed Q: R2 from TSQR(Q0),
+ * Q = Q0 R2^{-1}, R = R2 R1 (binary64).  A zero diagonal in R sets
+ * TSQR_ERR_SINGULAR.
+ */
+tsqr_status tsqr_indirect_refine(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                                 void* Q, int64_t ldq, double* R, int64_t ldr, int32_t refine_steps,
+                                 void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
+
+/*
+ * Adjoint of the thin QR (not in the paper; the differentiation form):
+ *   M = R dR^T - dQ^T Q,  copyltu(M) = tril(M) + tril(M, -1)^T,
+ *   dA = (dQ + Q copyltu(M)) R^{-T}.
+ * Q (m x n, dtype) and R (n x n binary64) are the saved forward outputs.
+ * dQ (m x n, dtype) and dR (n x n binary64; only its upper triangle is read)
+ * may each be NULL, meaning zero.  Out: dA (m x n, dtype).  A zero diagonal
+ * in R sets TSQR_ERR_SINGULAR.
+ */
+tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const double* dR,
+                          int64_t m, int64_t n, int32_t dtype, void* dA,
+                          void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
+
+/*
+ * Number of kernel launches one call of `op` makes for this shape and opts
+ * (refine_steps applies to TSQR_OP_CHOLQR / TSQR_OP_INDIRECT).  Host-only.
+ */
+tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* opts,
+                              int32_t refine_steps, int32_t* launches);
+
+/*
+ * Synchronises `stream` and returns the device status word of the last call
+ * that used `work` (TSQR_OK if it succeeded).
+ */
+tsqr_status tsqr_read_status(const void* work, void* stream);
+
+/* Static, human-readable name of a status code. */
+const char* tsqr_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSQR_GB300_H */

@@ -74,6 +74,7 @@ def _load():
         "oracle_householder_qr": [P, I64, I64, P, P],
         "oracle_householder_r": [P, I64, I64, P],
         "oracle_right_solve_upper": [P, I64, I64, P, P],
+        "oracle_upper_inverse": [P, I64, P],
         "oracle_cholqr": [P, I64, I64, ctypes.c_int, P, P],
         "oracle_indirect_refine": [P, I64, I64, ctypes.c_int, P, P],
         "oracle_qr_backward": [P, P, P, P, I64, I64, P],
@@ -132,6 +133,15 @@ def right_solve_upper(B, R):
     m, n = B.shape
     X = np.empty((m, n))
     _check(_load().oracle_right_solve_upper(_p(B), m, n, _p(R), _p(X)), "right_solve_upper")
+    return X
+
+
+def upper_inverse(R):
+    """R^{-1} of an upper-triangular R by back substitution (Sec. II-C)."""
+    R = _f64(R)
+    n = R.shape[0]
+    X = np.empty((n, n))
+    _check(_load().oracle_upper_inverse(_p(R), n, _p(X)), "upper_inverse")
     return X
 
 

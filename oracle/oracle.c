@@ -185,6 +185,37 @@ int oracle_right_solve_upper(const double* B, int64_t m, int64_t n, const double
   return OR_OK;
 }
 
+/* Inverse of the upper-triangular n x n R by back substitution on the
+ * columns of I (Sec. II-C: "compute the inverse of R and multiply by A").
+ * Returns OR_ERR_SINGULAR on a zero pivot. */
+int oracle_upper_inverse(const double* R, int64_t n, double* X) {
+  for (int64_t j = 0; j < n; ++j)
+    if (R[j * n + j] == 0.0) return OR_ERR_SINGULAR;
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t i = n - 1; i >= 0; --i) {
+      if (i > c) { X[i * n + c] = 0.0; continue; }
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int64_t k = i + 1; k <= c; ++k) s -= R[i * n + k] * X[k * n + c];
+      X[i * n + c] = s / R[i * n + i];
+    }
+  return OR_OK;
+}
+
+/* X = B R^{-1} with R^{-1} formed explicitly (Sec. II-C), row by row. */
+static int apply_inverse(const double* B, int64_t m, int64_t n, const double* R, double* X) {
+  double* Ri = (double*)malloc(sizeof(double) * (size_t)(n * n));
+  int st = oracle_upper_inverse(R, n, Ri);
+  if (st == OR_OK)
+    for (int64_t i = 0; i < m; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int64_t k = 0; k <= j; ++k) s += B[i * n + k] * Ri[k * n + j];
+        X[i * n + j] = s;
+      }
+  free(Ri);
+  return st;
+}
+
 /* C = A B for n x n row-major matrices. */
 static void matmul_nn(const double* A, const double* B, int64_t n, double* C) {
   for (int64_t i = 0; i < n; ++i)
@@ -225,7 +256,8 @@ static void gram(const double* A, int64_t m, int64_t n, double* G) {
 }
 
 /*
- * Cholesky QR (Sec. II-A): R = chol(A^T A), Q = A R^{-1} (Sec. II-C).
+ * Cholesky QR (Sec. II-A): R = chol(A^T A), Q = A R^{-1} with R^{-1} formed
+ * explicitly (Sec. II-C).
  * refine_steps extra passes repeat the same method on the computed Q
  * (iterative refinement, Sec. I): Q <- Q R2^{-1}, R <- R2 R.
  */
@@ -238,13 +270,13 @@ int oracle_cholqr(const double* A, int64_t m, int64_t n, int refine_steps, doubl
   int st = OR_OK;
   gram(A, m, n, G);
   st = cholesky_upper(G, n, R);
-  if (st == OR_OK) st = oracle_right_solve_upper(A, m, n, R, Q);
+  if (st == OR_OK) st = apply_inverse(A, m, n, R, Q);
   for (int s = 0; s < refine_steps && st == OR_OK; ++s) {
     gram(Q, m, n, G);
     st = cholesky_upper(G, n, R2);
     if (st != OR_OK) break;
     memcpy(Qt, Q, sizeof(double) * (size_t)(m * n));
-    st = oracle_right_solve_upper(Qt, m, n, R2, Q);
+    st = apply_inverse(Qt, m, n, R2, Q);
     matmul_nn(R2, R, n, RR);
     memcpy(R, RR, sizeof(double) * (size_t)(n * n));
   }
@@ -263,12 +295,12 @@ int oracle_indirect_refine(const double* A, int64_t m, int64_t n, int refine_ste
   double* RR = (double*)malloc(sizeof(double) * (size_t)(n * n));
   double* Qt = (double*)malloc(sizeof(double) * (size_t)(m * n));
   int st = oracle_householder_r(A, m, n, R);
-  if (st == OR_OK) st = oracle_right_solve_upper(A, m, n, R, Q);
+  if (st == OR_OK) st = apply_inverse(A, m, n, R, Q);
   for (int s = 0; s < refine_steps && st == OR_OK; ++s) {
     st = oracle_householder_r(Q, m, n, R2);
     if (st != OR_OK) break;
     memcpy(Qt, Q, sizeof(double) * (size_t)(m * n));
-    st = oracle_right_solve_upper(Qt, m, n, R2, Q);
+    st = apply_inverse(Qt, m, n, R2, Q);
     matmul_nn(R2, R, n, RR);
     memcpy(R, RR, sizeof(double) * (size_t)(n * n));
   }
@@ -329,11 +361,15 @@ int oracle_qr_backward(const double* Q, const double* R, const double* dQ, const
 /* Long-double pins and the SVD of R (Sec. III-B, SVD paragraph).            */
 /* ------------------------------------------------------------------------ */
 
-/* Cyclic Jacobi eigenvalues of the symmetric n x n S (long double); the
- * eigenvalues are returned unsorted in ev. */
+/* Cyclic threshold Jacobi eigenvalues of the symmetric n x n S (long double);
+ * the eigenvalues are returned unsorted in ev.  A rotation is skipped when
+ * |a_pq| is negligible next to the larger diagonal entry; the iteration stops
+ * after a sweep without rotations or once the off-diagonal norm is below
+ * n * eps * ||S||_F (long-double eps). */
 int oracle_sym_eig_ld(const long double* S, int64_t n, long double* ev) {
   long double* a = (long double*)malloc(sizeof(long double) * (size_t)(n * n));
   memcpy(a, S, sizeof(long double) * (size_t)(n * n));
+  const long double eps = LDBL_EPSILON;
   int conv = 0;
   for (int sweep = 0; sweep < 100 && !conv; ++sweep) {
     long double off = 0.0L, tot = 0.0L;
@@ -342,11 +378,14 @@ int oracle_sym_eig_ld(const long double* S, int64_t n, long double* ev) {
         tot += a[i * n + j] * a[i * n + j];
         if (i != j) off += a[i * n + j] * a[i * n + j];
       }
-    if (off <= (long double)LDBL_EPSILON * LDBL_EPSILON * tot || off == 0.0L) { conv = 1; break; }
+    if (off == 0.0L || off <= (long double)(n * n) * eps * eps * tot) { conv = 1; break; }
+    int rotated = 0;
     for (int64_t p = 0; p < n - 1; ++p)
       for (int64_t q = p + 1; q < n; ++q) {
         long double apq = a[p * n + q];
-        if (apq == 0.0L) continue;
+        long double dmax = fabsl(a[p * n + p]) > fabsl(a[q * n + q]) ? fabsl(a[p * n + p]) : fabsl(a[q * n + q]);
+        if (apq == 0.0L || fabsl(apq) <= eps * dmax) continue;
+        rotated = 1;
         long double theta = (a[q * n + q] - a[p * n + p]) / (2.0L * apq);
         long double t = (theta >= 0 ? 1.0L : -1.0L) / (fabsl(theta) + sqrtl(theta * theta + 1.0L));
         long double c = 1.0L / sqrtl(t * t + 1.0L), s = t * c;
@@ -361,6 +400,7 @@ int oracle_sym_eig_ld(const long double* S, int64_t n, long double* ev) {
           a[q * n + k] = s * apk + c * aqk;
         }
       }
+    if (!rotated) conv = 1;
   }
   for (int64_t i = 0; i < n; ++i) ev[i] = a[i * n + i];
   free(a);

@@ -1,0 +1,268 @@
+"""GB300-native direct TSQR (Benson, Gleich, Demmel, arXiv:1301.1071).
+
+Thin Python binding over the C-ABI of ``include/tsqr.h`` (libtsqr_gb300.so).
+It only marshals arguments: torch provides device memory and the current
+stream; every step of the factorisation runs in the library's CUDA kernels.
+There is no CPU fallback -- the functions raise if the library or a CUDA
+device is unavailable.
+
+    Q, R = direct(A)                 # Sec. III-B direct TSQR (Alg. 2 tree)
+    U, S, V = svd(A)                 # SVD variant, U = Q U_R
+    Q, R = cholqr(A, refine=0)       # Cholesky QR (+ refinement)
+    Q, R = indirect_refine(A, 1)     # indirect TSQR + refinement
+    dA = backward(Q, R, dQ, dR)      # QR adjoint
+    QRFunction.apply(A)              # autograd wrapper
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+__all__ = ["direct", "svd", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
+           "workspace_size", "launch_count", "library_path", "load", "STATUS"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libtsqr_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+F64, F32 = 0, 1
+OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD = 0, 1, 2, 3, 4
+NMAX = 100
+STATUS = {0: "TSQR_OK", 1: "TSQR_ERR_ARG", 2: "TSQR_ERR_SHAPE", 3: "TSQR_ERR_ALIGN",
+          4: "TSQR_ERR_WORKSPACE", 5: "TSQR_ERR_CUDA", 6: "TSQR_ERR_NOT_SPD", 7: "TSQR_ERR_SINGULAR",
+          8: "TSQR_ERR_NONFINITE", 9: "TSQR_ERR_TIMEOUT", 10: "TSQR_ERR_NOCONV"}
+
+
+class TSQRError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("block_rows", ctypes.c_int64), ("tree_fanout", ctypes.c_int32),
+                ("sync", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Loads libtsqr_gb300.so (building it with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P, I64, I32, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+        OP = ctypes.POINTER(Opts)
+        sigs = {
+            "tsqr_workspace_size": [I32, I64, I64, I32, OP, ctypes.POINTER(SZ)],
+            "tsqr_direct": [P, I64, I64, I64, I32, P, I64, P, I64, P, SZ, OP, P],
+            "tsqr_svd": [P, I64, I64, I64, I32, P, I64, P, P, I64, P, SZ, OP, P],
+            "cholqr": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
+            "tsqr_indirect_refine": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
+            "tsqr_backward": [P, P, P, P, I64, I64, I32, P, P, SZ, OP, P],
+            "tsqr_read_status": [P, P],
+            "tsqr_launch_count": [I32, I64, I64, I32, OP, I32, ctypes.POINTER(I32)],
+        }
+        for name, args in sigs.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.tsqr_status_string.argtypes = [I32]
+        lib.tsqr_status_string.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype} (float64 or float32)")
+
+
+def _check_tall(A: torch.Tensor):
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor (there is no CPU path)")
+    if A.dim() != 2:
+        raise ValueError("A must be 2-D")
+    m, n = A.shape
+    if n < 1 or n > NMAX or m < n:
+        raise ValueError(f"unsupported shape {tuple(A.shape)}: need 1 <= n <= {NMAX} and m >= n")
+    return m, n
+
+
+def _opts(block_rows=0, fanout=0, sync=False, events=None) -> Opts:
+    o = Opts()
+    o.block_rows = int(block_rows)
+    o.tree_fanout = int(fanout)
+    o.sync = 1 if sync else 0
+    if events is not None:
+        arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+        o._events_keepalive = arr
+        o.stage_events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
+    return o
+
+
+def launch_count(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fanout=0, refine=0) -> int:
+    """Kernel launches of one call (host-only query)."""
+    lib = load()
+    code = F64 if dtype == torch.float64 else F32
+    out = ctypes.c_int32(0)
+    o = _opts(block_rows, fanout)
+    _raise(lib.tsqr_launch_count(op, m, n, code, ctypes.byref(o), int(refine), ctypes.byref(out)),
+           "tsqr_launch_count")
+    return int(out.value)
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _raise(st: int, what: str):
+    if st != 0:
+        raise TSQRError(st, what)
+
+
+def workspace_size(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fanout=0) -> int:
+    lib = load()
+    code = F64 if dtype == torch.float64 else F32
+    out = ctypes.c_size_t(0)
+    o = _opts(block_rows, fanout)
+    _raise(lib.tsqr_workspace_size(op, m, n, code, ctypes.byref(o), ctypes.byref(out)), "tsqr_workspace_size")
+    return int(out.value)
+
+
+def _workspace(op, m, n, dtype, device, block_rows, fanout, work):
+    need = workspace_size(op, m, n, dtype, block_rows, fanout)
+    if work is None or work.numel() < need:
+        work = torch.empty(need, dtype=torch.uint8, device=device)
+    return work
+
+
+def _status(work: torch.Tensor, what: str, check: bool):
+    if check:
+        st = load().tsqr_read_status(_ptr(work), _stream(work.device))
+        _raise(st, what)
+
+
+def direct(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
+           out: tuple | None = None, check: bool = True, stage_events=None):
+    """Direct TSQR: returns (Q, R), Q m x n in A's dtype, R n x n float64,
+    diag(R) >= 0.  ``check`` synchronises and raises on a device error.
+    ``stage_events``: 4 torch.cuda.Event recorded at the start and after
+    Steps 1, 2 and 3."""
+    m, n = _check_tall(A)
+    A = A.contiguous()
+    lib = load()
+    Q, R = out if out is not None else (torch.empty_like(A), torch.empty(n, n, dtype=torch.float64, device=A.device))
+    work = _workspace(OP_DIRECT, m, n, A.dtype, A.device, block_rows, fanout, work)
+    o = _opts(block_rows, fanout, events=stage_events)
+    st = lib.tsqr_direct(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, _ptr(work), work.numel(),
+                         ctypes.byref(o), _stream(A.device))
+    _raise(st, "tsqr_direct")
+    _status(work, "tsqr_direct", check)
+    return Q, R
+
+
+def svd(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
+        check: bool = True):
+    """SVD via direct TSQR: A = U diag(S) V^T (U m x n in A's dtype; S, V float64)."""
+    m, n = _check_tall(A)
+    A = A.contiguous()
+    lib = load()
+    U = torch.empty_like(A)
+    S = torch.empty(n, dtype=torch.float64, device=A.device)
+    V = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    work = _workspace(OP_SVD, m, n, A.dtype, A.device, block_rows, fanout, work)
+    o = _opts(block_rows, fanout)
+    st = lib.tsqr_svd(_ptr(A), m, n, n, _dtype_code(A), _ptr(U), n, _ptr(S), _ptr(V), n, _ptr(work),
+                      work.numel(), ctypes.byref(o), _stream(A.device))
+    _raise(st, "tsqr_svd")
+    _status(work, "tsqr_svd", check)
+    return U, S, V
+
+
+def cholqr(A: torch.Tensor, refine: int = 0, work: torch.Tensor | None = None, check: bool = True):
+    """Cholesky QR (+ `refine` refinement passes): returns (Q, R)."""
+    m, n = _check_tall(A)
+    A = A.contiguous()
+    lib = load()
+    Q = torch.empty_like(A)
+    R = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    work = _workspace(OP_CHOLQR, m, n, A.dtype, A.device, 0, 0, work)
+    o = _opts()
+    st = lib.cholqr(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, int(refine), _ptr(work),
+                    work.numel(), ctypes.byref(o), _stream(A.device))
+    _raise(st, "cholqr")
+    _status(work, "cholqr", check)
+    return Q, R
+
+
+def indirect_refine(A: torch.Tensor, refine: int = 1, block_rows: int = 0, fanout: int = 0,
+                    work: torch.Tensor | None = None, check: bool = True):
+    """Indirect TSQR + `refine` refinement passes: returns (Q, R)."""
+    m, n = _check_tall(A)
+    A = A.contiguous()
+    lib = load()
+    Q = torch.empty_like(A)
+    R = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    work = _workspace(OP_INDIRECT, m, n, A.dtype, A.device, block_rows, fanout, work)
+    o = _opts(block_rows, fanout)
+    st = lib.tsqr_indirect_refine(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, int(refine),
+                                  _ptr(work), work.numel(), ctypes.byref(o), _stream(A.device))
+    _raise(st, "tsqr_indirect_refine")
+    _status(work, "tsqr_indirect_refine", check)
+    return Q, R
+
+
+def backward(Q: torch.Tensor, R: torch.Tensor, dQ: torch.Tensor | None, dR: torch.Tensor | None,
+             work: torch.Tensor | None = None, check: bool = True):
+    """QR adjoint: dA = (dQ + Q copyltu(M)) R^{-T}, M = R dR^T - dQ^T Q."""
+    m, n = _check_tall(Q)
+    Q = Q.contiguous()
+    R = R.to(torch.float64).contiguous()
+    dQ = None if dQ is None else dQ.to(Q.dtype).contiguous()
+    dR = None if dR is None else dR.to(torch.float64).contiguous()
+    lib = load()
+    dA = torch.empty_like(Q)
+    work = _workspace(OP_BACKWARD, m, n, Q.dtype, Q.device, 0, 0, work)
+    o = _opts()
+    st = lib.tsqr_backward(_ptr(Q), _ptr(R), _ptr(dQ), _ptr(dR), m, n, _dtype_code(Q), _ptr(dA), _ptr(work),
+                           work.numel(), ctypes.byref(o), _stream(Q.device))
+    _raise(st, "tsqr_backward")
+    _status(work, "tsqr_backward", check)
+    return dA
+
+
+class QRFunction(torch.autograd.Function):
+    """Thin QR with the hand-written adjoint: forward = direct TSQR, backward =
+    tsqr_backward on the saved Q and R.  R is returned in A's dtype."""
+
+    @staticmethod
+    def forward(ctx, A):
+        Q, R = direct(A)
+        ctx.save_for_backward(Q, R)
+        return Q, R.to(A.dtype)
+
+    @staticmethod
+    def backward(ctx, gQ, gR):
+        Q, R = ctx.saved_tensors
+        dR = None if gR is None else torch.triu(gR.to(torch.float64))
+        return backward(Q, R, gQ, dR)

@@ -1,0 +1,411 @@
+// capi.cu -- the extern "C" boundary (include/tsqr.h): argument checks, the
+// plan, and the launch sequence of each computation on the caller's stream.
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "../../include/tsqr.h"
+#include "launch.h"
+#include "plan.h"
+#include "small.cuh"
+
+namespace tsqr {
+
+cudaError_t launch_local_qr_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, void*, double*,
+                                double*, int32_t*, cudaStream_t);
+cudaError_t launch_local_qr_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, void*, double*,
+                                double*, int32_t*, cudaStream_t);
+cudaError_t launch_form_q_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, const double*,
+                              const double*, int64_t, void*, int32_t*, cudaStream_t);
+cudaError_t launch_form_q_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, const double*,
+                              const double*, int64_t, void*, int32_t*, cudaStream_t);
+
+cudaError_t launch_rowmul_f64(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
+                              int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
+cudaError_t launch_rowmul_f32(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
+                              int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
+cudaError_t launch_gram_f64(const void*, const void*, int64_t, int, int, int, int, double*, int32_t*, cudaStream_t);
+cudaError_t launch_gram_f32(const void*, const void*, int64_t, int, int, int, int, double*, int32_t*, cudaStream_t);
+
+cudaError_t launch_rowmul(int esz, const KernelCfg& k, const void* X, const double* M1, const void* Y,
+                          const double* M2, int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,
+                          cudaStream_t st) {
+  return esz == 8 ? launch_rowmul_f64(k, X, M1, Y, M2, m, n, b, p, out, status, st)
+                  : launch_rowmul_f32(k, X, M1, Y, M2, m, n, b, p, out, status, st);
+}
+
+cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n, double* part, double* G,
+                        int32_t* status, cudaStream_t st) {
+  const GramGeom g = gram_geom(m, n, esz);
+  cudaError_t e = esz == 8 ? launch_gram_f64(X, Y, m, n, g.chunk, g.grid, g.nt, part, status, st)
+                           : launch_gram_f32(X, Y, m, n, g.chunk, g.grid, g.nt, part, status, st);
+  if (e != cudaSuccess) return e;
+  return launch_gram_reduce(part, g.grid, n, G, status, st);
+}
+
+cudaError_t launch_local_qr(int esz, const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t p,
+                            void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+  return esz == 8 ? launch_local_qr_f64(k, A, m, n, b, p, Y, Rst, Tst, status, st)
+                  : launch_local_qr_f32(k, A, m, n, b, p, Y, Rst, Tst, status, st);
+}
+
+cudaError_t launch_form_q(int esz, const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t p,
+                          const double* T, const double* C, int64_t cblocks, void* Q, int32_t* status,
+                          cudaStream_t st) {
+  return esz == 8 ? launch_form_q_f64(k, Y, m, n, b, p, T, C, cblocks, Q, status, st)
+                  : launch_form_q_f32(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
+}
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int esz_of(int32_t dtype) { return dtype == TSQR_F64 ? 8 : (dtype == TSQR_F32 ? 4 : 0); }
+
+tsqr_status check_opts(const tsqr_opts* o) {
+  if (!o) return TSQR_OK;
+  for (int i = 0; i < 2; ++i)
+    if (o->reserved[i] != 0) return TSQR_ERR_ARG;
+  if (o->block_rows < 0 || o->tree_fanout < 0 || o->tree_fanout == 1) return TSQR_ERR_ARG;
+  return TSQR_OK;
+}
+
+char* at(void* work, size_t off) { return static_cast<char*>(work) + off; }
+
+int32_t* status_ptr(void* work) { return reinterpret_cast<int32_t*>(work); }
+
+tsqr_status finish(void* work, const tsqr_opts* o, cudaStream_t st) {
+  if (cudaGetLastError() != cudaSuccess) return TSQR_ERR_CUDA;
+  if (o && o->sync) return tsqr_read_status(work, st);
+  return TSQR_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + nb && pb < pa + na;
+}
+
+// Shared argument checks of the tall-matrix entry points.
+tsqr_status check_tall(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, const tsqr_opts* o) {
+  if (!A) return TSQR_ERR_ARG;
+  if (esz_of(dtype) == 0) return TSQR_ERR_ARG;
+  tsqr_status s = check_opts(o);
+  if (s != TSQR_OK) return s;
+  if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  if (lda != n || !aligned16(A)) return TSQR_ERR_ALIGN;
+  return TSQR_OK;
+}
+
+// Direct TSQR on a built plan.  ctop_extra (optional) is launched between the
+// sign fix and the down pass (the SVD variant folds U_R into Ctop there).
+tsqr_status mark(const tsqr_opts* o, int i, cudaStream_t st) {
+  if (!o || !o->stage_events || !o->stage_events[i]) return TSQR_OK;
+  return cudaEventRecord(static_cast<cudaEvent_t>(o->stage_events[i]), st) == cudaSuccess ? TSQR_OK
+                                                                                          : TSQR_ERR_CUDA;
+}
+
+template <class Extra>
+tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t ldr, void* work,
+                       cudaStream_t st, const tsqr_opts* o, Extra extra) {
+  const int n = static_cast<int>(P.n);
+  int32_t* status = status_ptr(work);
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t), st) != cudaSuccess) return TSQR_ERR_CUDA;
+  const size_t L = P.levels.size();
+  auto S = [&](size_t l) { return reinterpret_cast<double*>(at(work, P.levels[l].off_S)); };
+  auto T = [&](size_t l) { return reinterpret_cast<double*>(at(work, P.levels[l].off_T)); };
+  double* ctop = reinterpret_cast<double*>(at(work, P.off_ctop));
+
+  // Step 1: local QR of every row block; Y_0 is written into Q's storage.
+  const Level& l0 = P.levels[0];
+  if (mark(o, 0, st) != TSQR_OK) return TSQR_ERR_CUDA;
+  if (launch_local_qr(P.esz, P.cfg0, A, P.m, n, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
+    return TSQR_ERR_CUDA;
+  if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
+  // Step 2 (Alg. 2): the stack of level l-1 is the tall input of level l.
+  for (size_t l = 1; l < L; ++l) {
+    const Level& lv = P.levels[l];
+    if (launch_local_qr(8, P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, S(l - 1), S(l), T(l), status, st) !=
+        cudaSuccess)
+      return TSQR_ERR_CUDA;
+  }
+  if (launch_sign_fix(S(L - 1), n, R, ldr, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  if (extra(ctop) != TSQR_OK) return TSQR_ERR_CUDA;
+  // Down the tree: the Q of level l's stack is the coefficient of level l-1.
+  for (size_t l = L - 1; l >= 1; --l) {
+    const Level& lv = P.levels[l];
+    const double* C = (l == L - 1) ? ctop : S(l);
+    const int64_t cb = (l == L - 1) ? 1 : lv.p;
+    if (launch_form_q(8, P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, T(l), C, cb, S(l - 1), status, st) !=
+        cudaSuccess)
+      return TSQR_ERR_CUDA;
+  }
+  // Step 3: Q_i = Q1_i Q2_i over the Y_i held in Q.
+  if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
+  const double* C0 = (L == 1) ? ctop : S(0);
+  const int64_t cb0 = (L == 1) ? 1 : l0.p;
+  if (launch_form_q(P.esz, P.cfg0, Q, P.m, n, l0.b, l0.p, T(0), C0, cb0, Q, status, st) != cudaSuccess)
+    return TSQR_ERR_CUDA;
+  return mark(o, 3, st);
+}
+
+// R factor only (indirect TSQR, Sec. II-B): Steps 1-2 without Y/T/Q2, then
+// the sign normalisation into R (n x n, leading dimension n).  `ctop` receives
+// the (unused) sign matrix.
+tsqr_status run_r_only(const Plan& P, int esz, const void* X, double* R, void* work, cudaStream_t st) {
+  const int n = static_cast<int>(P.n);
+  int32_t* status = status_ptr(work);
+  const size_t L = P.levels.size();
+  auto S = [&](size_t l) { return reinterpret_cast<double*>(at(work, P.levels[l].off_S)); };
+  double* ctop = reinterpret_cast<double*>(at(work, P.off_ctop));
+  const Level& l0 = P.levels[0];
+  if (launch_local_qr(esz, P.cfg0, X, P.m, n, l0.b, l0.p, nullptr, S(0), nullptr, status, st) != cudaSuccess)
+    return TSQR_ERR_CUDA;
+  for (size_t l = 1; l < L; ++l) {
+    const Level& lv = P.levels[l];
+    if (launch_local_qr(8, P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, nullptr, S(l), nullptr, status, st) !=
+        cudaSuccess)
+      return TSQR_ERR_CUDA;
+  }
+  if (launch_sign_fix(S(L - 1), n, R, n, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  return TSQR_OK;
+}
+
+// out = X M1 (+ Y M2) over the row blocks of the Step-1 configuration.
+tsqr_status rowmul(const Plan& P, const void* X, const double* M1, const void* Y, const double* M2, void* out,
+                   int32_t* status, cudaStream_t st) {
+  const int64_t b = (X && Y) ? P.cfg0.rm_rows / 2 : P.cfg0.rm_rows;
+  const int64_t p = (P.m + b - 1) / b;
+  return launch_rowmul(P.esz, P.cfg0, X, M1, Y, M2, P.m, (int)P.n, b, p, out, status, st) == cudaSuccess
+             ? TSQR_OK
+             : TSQR_ERR_CUDA;
+}
+
+tsqr_status copy_r(double* R, int64_t ldr, const double* src, int64_t n, cudaStream_t st) {
+  return cudaMemcpy2DAsync(R, ldr * sizeof(double), src, n * sizeof(double), n * sizeof(double), n,
+                           cudaMemcpyDeviceToDevice, st) == cudaSuccess
+             ? TSQR_OK
+             : TSQR_ERR_CUDA;
+}
+
+#define TSQR_TRY(x)                       \
+  do {                                    \
+    tsqr_status _s = (x);                 \
+    if (_s != TSQR_OK) return _s;         \
+  } while (0)
+#define TSQR_CUDA(x) TSQR_TRY((x) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA)
+
+tsqr_status plan_for(int op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* o, size_t work_bytes,
+                     const void* work, Plan* P) {
+  int rc = make_plan(m, n, esz_of(dtype), o ? o->block_rows : 0, o ? o->tree_fanout : 0, P);
+  if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
+  if (!work || !aligned16(work) || work_bytes < op_bytes(*P, op)) return TSQR_ERR_WORKSPACE;
+  return TSQR_OK;
+}
+
+}  // namespace
+}  // namespace tsqr
+
+using namespace tsqr;
+
+extern "C" {
+
+const char* tsqr_status_string(int32_t s) {
+  switch (s) {
+    case TSQR_OK: return "TSQR_OK";
+    case TSQR_ERR_ARG: return "TSQR_ERR_ARG: invalid argument";
+    case TSQR_ERR_SHAPE: return "TSQR_ERR_SHAPE: unsupported shape";
+    case TSQR_ERR_ALIGN: return "TSQR_ERR_ALIGN: leading dimension or alignment";
+    case TSQR_ERR_WORKSPACE: return "TSQR_ERR_WORKSPACE: workspace missing or too small";
+    case TSQR_ERR_CUDA: return "TSQR_ERR_CUDA: CUDA runtime error";
+    case TSQR_ERR_NOT_SPD: return "TSQR_ERR_NOT_SPD: Cholesky breakdown";
+    case TSQR_ERR_SINGULAR: return "TSQR_ERR_SINGULAR: zero diagonal in R";
+    case TSQR_ERR_NONFINITE: return "TSQR_ERR_NONFINITE: NaN or Inf";
+    case TSQR_ERR_TIMEOUT: return "TSQR_ERR_TIMEOUT: bounded wait expired";
+    case TSQR_ERR_NOCONV: return "TSQR_ERR_NOCONV: Jacobi SVD did not converge";
+    default: return "unknown tsqr_status";
+  }
+}
+
+tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* opts,
+                              int32_t refine_steps, int32_t* launches) {
+  if (!launches || refine_steps < 0) return TSQR_ERR_ARG;
+  const int esz = esz_of(dtype);
+  if (esz == 0) return TSQR_ERR_ARG;
+  tsqr_status s = check_opts(opts);
+  if (s != TSQR_OK) return s;
+  Plan P;
+  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P);
+  if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
+  const int L = static_cast<int>(P.levels.size());
+  switch (op) {
+    case TSQR_OP_DIRECT: *launches = 2 * L + 1; break;        // L up, sign fix, L down
+    case TSQR_OP_SVD: *launches = 2 * L + 2; break;           // + Jacobi SVD
+    case TSQR_OP_CHOLQR: *launches = 4 * (1 + refine_steps) + refine_steps; break;  // gram, reduce, chol, rowmul (+ combine)
+    case TSQR_OP_INDIRECT: *launches = (L + 3) * (1 + refine_steps) + refine_steps; break;
+    case TSQR_OP_BACKWARD: *launches = 4; break;              // gram, reduce, prep, rowmul
+    default: return TSQR_ERR_ARG;
+  }
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_read_status(const void* work, void* stream) {
+  if (!work) return TSQR_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t h = 0;
+  if (cudaMemcpyAsync(&h, work, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TSQR_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TSQR_ERR_CUDA;
+  return static_cast<tsqr_status>(h);
+}
+
+tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* opts,
+                                size_t* bytes) {
+  if (!bytes) return TSQR_ERR_ARG;
+  const int esz = esz_of(dtype);
+  if (esz == 0) return TSQR_ERR_ARG;
+  tsqr_status s = check_opts(opts);
+  if (s != TSQR_OK) return s;
+  if (op < TSQR_OP_DIRECT || op > TSQR_OP_BACKWARD) return TSQR_ERR_ARG;
+  Plan P;
+  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P);
+  if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
+  *bytes = op_bytes(P, op);
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, void* Q, int64_t ldq,
+                        double* R, int64_t ldr, void* work, size_t work_bytes, const tsqr_opts* opts,
+                        void* stream) {
+  tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
+  if (s != TSQR_OK) return s;
+  if (!Q || !R) return TSQR_ERR_ARG;
+  if (ldq != n || ldr != n || !aligned16(Q)) return TSQR_ERR_ALIGN;
+  const int esz = esz_of(dtype);
+  if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
+  Plan P;
+  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P);
+  if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
+  if (!work || work_bytes < P.bytes || !aligned16(work)) return TSQR_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = run_direct(P, A, Q, R, ldr, work, st, opts, [](double*) { return TSQR_OK; });
+  if (s != TSQR_OK) return s;
+  return finish(work, opts, st);
+}
+
+tsqr_status tsqr_svd(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, void* U, int64_t ldu,
+                     double* S, double* V, int64_t ldv, void* work, size_t work_bytes, const tsqr_opts* opts,
+                     void* stream) {
+  tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
+  if (s != TSQR_OK) return s;
+  if (!U || !S || !V) return TSQR_ERR_ARG;
+  if (ldu != n || ldv != n || !aligned16(U)) return TSQR_ERR_ALIGN;
+  const int esz = esz_of(dtype);
+  if (overlaps(A, (size_t)m * n * esz, U, (size_t)m * n * esz)) return TSQR_ERR_ARG;
+  Plan P;
+  TSQR_TRY(plan_for(TSQR_OP_SVD, m, n, dtype, opts, work_bytes, work, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* Rt = reinterpret_cast<double*>(at(work, P.off_small));
+  int32_t* status = status_ptr(work);
+  const int ni = static_cast<int>(n);
+  TSQR_TRY(run_direct(P, A, U, Rt, n, work, st, opts, [&](double* ctop) {
+    return launch_jacobi_svd(Rt, n, ni, ctop, S, V, ldv, status, st) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA;
+  }));
+  return finish(work, opts, st);
+}
+
+tsqr_status cholqr(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, void* Q, int64_t ldq,
+                   double* R, int64_t ldr, int32_t refine_steps, void* work, size_t work_bytes,
+                   const tsqr_opts* opts, void* stream) {
+  tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
+  if (s != TSQR_OK) return s;
+  if (!Q || !R || refine_steps < 0) return TSQR_ERR_ARG;
+  if (ldq != n || ldr != n || !aligned16(Q)) return TSQR_ERR_ALIGN;
+  const int esz = esz_of(dtype);
+  if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
+  Plan P;
+  TSQR_TRY(plan_for(TSQR_OP_CHOLQR, m, n, dtype, opts, work_bytes, work, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t* status = status_ptr(work);
+  const size_t nn = (size_t)n * n;
+  double* part = reinterpret_cast<double*>(at(work, P.off_part));
+  double* G = reinterpret_cast<double*>(at(work, P.off_gsmall));
+  double* R1 = G + nn;
+  double* R2 = G + 2 * nn;
+  double* Rinv = G + 3 * nn;
+  const int ni = static_cast<int>(n);
+  TSQR_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  // Sec. II-A: A^T A = sum_p A_p^T A_p, Cholesky, then Q = A R^{-1} (Sec. II-C)
+  TSQR_CUDA(launch_gram(esz, A, A, m, ni, part, G, status, st));
+  TSQR_CUDA(launch_chol_inv(G, ni, R1, Rinv, status, st));
+  TSQR_TRY(rowmul(P, A, Rinv, nullptr, nullptr, Q, status, st));
+  for (int r = 0; r < refine_steps; ++r) {  // iterative refinement: repeat on the computed Q
+    TSQR_CUDA(launch_gram(esz, Q, Q, m, ni, part, G, status, st));
+    TSQR_CUDA(launch_chol_inv(G, ni, R2, Rinv, status, st));
+    TSQR_TRY(rowmul(P, Q, Rinv, nullptr, nullptr, Q, status, st));
+    TSQR_CUDA(launch_tri_mul(R2, R1, ni, R1, n, st));
+  }
+  TSQR_TRY(copy_r(R, ldr, R1, n, st));
+  return finish(work, opts, st);
+}
+
+tsqr_status tsqr_indirect_refine(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, void* Q,
+                                 int64_t ldq, double* R, int64_t ldr, int32_t refine_steps, void* work,
+                                 size_t work_bytes, const tsqr_opts* opts, void* stream) {
+  tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
+  if (s != TSQR_OK) return s;
+  if (!Q || !R || refine_steps < 0) return TSQR_ERR_ARG;
+  if (ldq != n || ldr != n || !aligned16(Q)) return TSQR_ERR_ALIGN;
+  const int esz = esz_of(dtype);
+  if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
+  Plan P;
+  TSQR_TRY(plan_for(TSQR_OP_INDIRECT, m, n, dtype, opts, work_bytes, work, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t* status = status_ptr(work);
+  const size_t nn = (size_t)n * n;
+  double* R1 = reinterpret_cast<double*>(at(work, P.off_small));
+  double* R2 = R1 + nn;
+  double* Rinv = R1 + 2 * nn;
+  const int ni = static_cast<int>(n);
+  TSQR_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  // Sec. II-B: R from the TSQR reduction; Sec. II-C: Q = A R^{-1}
+  TSQR_TRY(run_r_only(P, esz, A, R1, work, st));
+  TSQR_CUDA(launch_rinv(R1, n, ni, Rinv, status, st));
+  TSQR_TRY(rowmul(P, A, Rinv, nullptr, nullptr, Q, status, st));
+  for (int r = 0; r < refine_steps; ++r) {  // refinement: repeat on the computed Q
+    TSQR_TRY(run_r_only(P, esz, Q, R2, work, st));
+    TSQR_CUDA(launch_rinv(R2, n, ni, Rinv, status, st));
+    TSQR_TRY(rowmul(P, Q, Rinv, nullptr, nullptr, Q, status, st));
+    TSQR_CUDA(launch_tri_mul(R2, R1, ni, R1, n, st));
+  }
+  TSQR_TRY(copy_r(R, ldr, R1, n, st));
+  return finish(work, opts, st);
+}
+
+tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const double* dR, int64_t m, int64_t n,
+                          int32_t dtype, void* dA, void* work, size_t work_bytes, const tsqr_opts* opts,
+                          void* stream) {
+  tsqr_status s = check_tall(Q, m, n, n, dtype, opts);
+  if (s != TSQR_OK) return s;
+  if (!R || !dA) return TSQR_ERR_ARG;
+  if (!aligned16(dA) || (dQ && !aligned16(dQ))) return TSQR_ERR_ALIGN;
+  Plan P;
+  TSQR_TRY(plan_for(TSQR_OP_BACKWARD, m, n, dtype, opts, work_bytes, work, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t* status = status_ptr(work);
+  const size_t nn = (size_t)n * n;
+  const int esz = esz_of(dtype);
+  double* part = reinterpret_cast<double*>(at(work, P.off_part));
+  double* G = reinterpret_cast<double*>(at(work, P.off_gsmall));
+  double* M1 = G + nn;
+  double* M2 = G + 2 * nn;
+  const int ni = static_cast<int>(n);
+  TSQR_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  if (dQ) TSQR_CUDA(launch_gram(esz, dQ, Q, m, ni, part, G, status, st));  // G = dQ^T Q
+  TSQR_CUDA(launch_bwd_prep(R, dR, dQ ? G : nullptr, ni, M1, M2, status, st));
+  // dA = (dQ + Q copyltu(M)) R^{-T} = dQ R^{-T} + Q (copyltu(M) R^{-T})
+  TSQR_TRY(rowmul(P, dQ, M1, Q, M2, dA, status, st));
+  return finish(work, opts, st);
+}
+
+}  // extern "C"

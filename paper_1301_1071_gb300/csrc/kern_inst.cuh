@@ -1,0 +1,102 @@
+// kern_inst.cuh -- instantiates the TSQR kernels for one (storage, compute)
+// type pair and four register tiles (R_i rows per thread, at most T_i threads
+// per CTA so that registers x threads <= 64K); included once per dtype
+// translation unit.  KernelCfg::tile selects the tile.
+#pragma once
+
+#include "launch.h"
+#include "qr_kernels.cuh"
+#include "tall_kernels.cuh"
+
+namespace tsqr {
+
+template <int R, int MAXT>
+static cudaError_t local_qr_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t p,
+                              TSQR_S* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+  if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
+  auto fn = k_local_qr<TSQR_S, TSQR_T, kNpc, R, MAXT>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_qr);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)p, k.NT, k.smem_qr, st>>>(A, m, n, (int)b, k.CS, k.NRG, Y, Rst, Tst, status);
+  return cudaGetLastError();
+}
+
+template <int R, int MAXT>
+static cudaError_t form_q_R(const KernelCfg& k, const TSQR_S* Y, int64_t m, int n, int64_t b, int64_t p,
+                            const double* T, const double* C, int64_t cblocks, TSQR_S* Q, int32_t* status,
+                            cudaStream_t st) {
+  if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
+  auto fn = k_form_q<TSQR_S, TSQR_T, kNpc, R, MAXT>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fq);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)p, k.NT, k.smem_fq, st>>>(Y, m, n, (int)b, k.fq_rows, k.CS, k.NRG, T, C, cblocks, Q, status);
+  return cudaGetLastError();
+}
+
+cudaError_t TSQR_LOCAL_QR_NAME(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t p,
+                               void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+  const TSQR_S* a = static_cast<const TSQR_S*>(A);
+  TSQR_S* y = static_cast<TSQR_S*>(Y);
+  switch (k.tile) {
+    case 0: return local_qr_R<TSQR_R0, TSQR_T0>(k, a, m, n, b, p, y, Rst, Tst, status, st);
+    case 1: return local_qr_R<TSQR_R1, TSQR_T1>(k, a, m, n, b, p, y, Rst, Tst, status, st);
+    case 2: return local_qr_R<TSQR_R2, TSQR_T2>(k, a, m, n, b, p, y, Rst, Tst, status, st);
+    case 3: return local_qr_R<TSQR_R3, TSQR_T3>(k, a, m, n, b, p, y, Rst, Tst, status, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t TSQR_FORM_Q_NAME(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t p,
+                             const double* T, const double* C, int64_t cblocks, void* Q, int32_t* status,
+                             cudaStream_t st) {
+  const TSQR_S* y = static_cast<const TSQR_S*>(Y);
+  TSQR_S* q = static_cast<TSQR_S*>(Q);
+  switch (k.tile) {
+    case 0: return form_q_R<TSQR_R0, TSQR_T0>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
+    case 1: return form_q_R<TSQR_R1, TSQR_T1>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
+    case 2: return form_q_R<TSQR_R2, TSQR_T2>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
+    case 3: return form_q_R<TSQR_R3, TSQR_T3>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int R, int MAXT>
+static cudaError_t rowmul_R(const KernelCfg& k, const TSQR_S* X, const double* M1, const TSQR_S* Y,
+                            const double* M2, int64_t m, int n, int64_t b, int64_t p, TSQR_S* out,
+                            int32_t* status, cudaStream_t st) {
+  if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
+  auto fn = k_rowmul<TSQR_S, TSQR_T, kNpc, R, MAXT>;
+  const size_t smem = k.smem_rm;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)p, k.NT, smem, st>>>(X, M1, Y, M2, m, n, (int)b, k.rm_rows, k.CS, k.NRG, out, status);
+  return cudaGetLastError();
+}
+
+cudaError_t TSQR_ROWMUL_NAME(const KernelCfg& k, const void* X, const double* M1, const void* Y, const double* M2,
+                             int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,
+                             cudaStream_t st) {
+  const TSQR_S* x = static_cast<const TSQR_S*>(X);
+  const TSQR_S* y = static_cast<const TSQR_S*>(Y);
+  TSQR_S* o = static_cast<TSQR_S*>(out);
+  switch (k.tile) {
+    case 0: return rowmul_R<TSQR_R0, TSQR_T0>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 1: return rowmul_R<TSQR_R1, TSQR_T1>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 2: return rowmul_R<TSQR_R2, TSQR_T2>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 3: return rowmul_R<TSQR_R3, TSQR_T3>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t TSQR_GRAM_NAME(const void* X, const void* Y, int64_t m, int n, int chunk, int grid, int nt,
+                           double* part, int32_t* status, cudaStream_t st) {
+  const size_t smem = 2 * align_up((size_t)chunk * n * sizeof(TSQR_S), 16) + 16;
+  auto fn = k_gram<TSQR_S>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, nt, smem, st>>>(static_cast<const TSQR_S*>(X), static_cast<const TSQR_S*>(Y), m, n, chunk, part,
+                             status);
+  return cudaGetLastError();
+}
+
+}  // namespace tsqr

@@ -1,0 +1,127 @@
+// plan.cpp -- see plan.h.
+#include "plan.h"
+
+#include <algorithm>
+
+#include "../../include/tsqr.h"
+#include "launch.h"
+#include "layout.cuh"
+
+namespace tsqr {
+
+static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Register-tile heights and their thread bounds (must match kern_f64.cu /
+// kern_f32.cu): registers x threads stay within the 64K register file.
+struct TileChoice { int R, maxt; };
+constexpr int kNumTiles = 4;
+static const TileChoice kTiles64[kNumTiles] = {{12, 320}, {8, 448}, {4, 640}, {8, 640}};
+static const TileChoice kTiles32[kNumTiles] = {{24, 320}, {16, 448}, {8, 640}, {16, 640}};
+
+bool choose_cfg(int esz, int n, KernelCfg* out) {
+  if (n < 1 || n > TSQR_NMAX) return false;
+  const int CS = (n + kNpc - 1) / kNpc;
+  const int NPAD = CS * kNpc;
+  const TileChoice* tiles = esz == 8 ? kTiles64 : kTiles32;
+  KernelCfg best;
+  for (int ti = 0; ti < kNumTiles; ++ti) {
+    const int R = tiles[ti].R;
+    for (int NRG = tiles[ti].maxt / (32 * CS); NRG >= 1; --NRG) {
+      const int B = 32 * NRG * R;
+      const int NT = 32 * CS * NRG;
+      if (B < n) break;
+      size_t a = LocalQrSmem(B, n, NT / 32, NPAD, esz, esz).total;
+      if (a > kSmemMax) continue;
+      int fq_rows = B;  // k_form_q stages its block in chunks of fq_rows rows
+      while (fq_rows > 32 && FormQSmem(fq_rows, n, NPAD, esz, esz).total > kSmemMax) fq_rows -= 32;
+      size_t f = FormQSmem(fq_rows, n, NPAD, esz, esz).total;
+      if (f > kSmemMax) continue;
+      int rm_rows = B;  // k_rowmul also stages two n x NPAD matrices: shrink its stage
+      while (rm_rows > 32 && RowMulSmem(rm_rows, n, NPAD, esz, esz).total > kSmemMax) rm_rows -= 32;
+      if (RowMulSmem(rm_rows, n, NPAD, esz, esz).total > kSmemMax) continue;
+      if (B > best.B) {  // largest row block wins; ties keep the earlier tile
+        best.npc = kNpc; best.R = R; best.CS = CS; best.NRG = NRG; best.NT = NT; best.B = B;
+        best.smem_qr = a; best.smem_fq = f; best.tile = ti; best.fq_rows = fq_rows;
+        best.rm_rows = rm_rows; best.smem_rm = RowMulSmem(rm_rows, n, NPAD, esz, esz).total;
+      }
+      break;
+    }
+  }
+  if (best.B == 0) return false;
+  *out = best;
+  return true;
+}
+
+GramGeom gram_geom(int64_t m, int n, int esz) {
+  GramGeom g;
+  int64_t chunk = (int64_t)(kSmemMax - 64) / (2 * (int64_t)n * esz);
+  chunk = chunk > 1024 ? 1024 : chunk;
+  chunk = chunk / 16 * 16;
+  if (chunk < 16) chunk = 16;
+  g.chunk = (int)chunk;
+  const int64_t nchunks = (m + chunk - 1) / chunk;
+  g.grid = (int)(nchunks < kMaxGramParts ? nchunks : kMaxGramParts);
+  const int nt4 = (n + 3) / 4;
+  int nt = (nt4 * nt4 + 31) / 32 * 32;
+  g.nt = nt < 256 ? 256 : (nt > 1024 ? 1024 : nt);
+  return g;
+}
+
+size_t op_bytes(const Plan& P, int op) {
+  return (op == TSQR_OP_CHOLQR || op == TSQR_OP_BACKWARD) ? P.bytes_gram : P.bytes;
+}
+
+int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan) {
+  if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  Plan P;
+  P.m = m;
+  P.n = n;
+  P.esz = esz;
+  if (!choose_cfg(esz, (int)n, &P.cfg0) || !choose_cfg(8, (int)n, &P.cfg64)) return TSQR_ERR_SHAPE;
+  int64_t b0 = block_rows > 0 ? block_rows : P.cfg0.B;
+  if (b0 < n || b0 > P.cfg0.B) return TSQR_ERR_SHAPE;
+  // tree node = f stacked R factors, f >= 2
+  int64_t fmax = P.cfg64.B / n;
+  int64_t f = fanout > 0 ? fanout : fmax;
+  if (f < 2 || f > fmax) return TSQR_ERR_SHAPE;
+
+  Level l0;
+  l0.rows = m;
+  l0.b = b0;
+  l0.p = (m + b0 - 1) / b0;
+  P.levels.push_back(l0);
+  while (P.levels.back().p > 1) {
+    Level l;
+    l.rows = P.levels.back().p * n;
+    l.b = f * n;
+    l.p = (l.rows + l.b - 1) / l.b;
+    P.levels.push_back(l);
+  }
+  size_t o = kHeaderBytes;
+  const size_t nn = (size_t)n * n * sizeof(double);
+  for (auto& l : P.levels) {
+    l.off_S = o;
+    o = al16(o + (size_t)l.p * nn);
+    l.off_T = o;
+    o = al16(o + (size_t)l.p * nn);
+  }
+  P.off_ctop = o;
+  o = al16(o + nn);
+  P.off_small = o;
+  o = al16(o + kSmallSlots * nn);
+  P.bytes = o;
+  GramGeom g = gram_geom(m, (int)n, esz);
+  P.gram_chunk = g.chunk;
+  P.gram_grid = g.grid;
+  P.gram_nt = g.nt;
+  o = kHeaderBytes;
+  P.off_part = o;
+  o = al16(o + (size_t)g.grid * nn);
+  P.off_gsmall = o;
+  o = al16(o + kSmallSlots * nn);
+  P.bytes_gram = o;
+  *plan = P;
+  return TSQR_OK;
+}
+
+}  // namespace tsqr

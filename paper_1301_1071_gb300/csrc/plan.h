@@ -1,0 +1,64 @@
+// plan.h -- host-side plan of a direct-TSQR call: kernel configuration per
+// dtype and n, row-block partition (Step 1), recursive tree levels (Step 2,
+// Alg. 2) and the workspace layout.  Pure host code, unit-testable.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace tsqr {
+
+constexpr int kNpc = 5;                // columns per thread (register tile width)
+constexpr size_t kSmemMax = 232448;    // 227 KB dynamic shared memory per CTA
+constexpr size_t kHeaderBytes = 256;   // status word + padding at the start of work
+
+struct KernelCfg {
+  int npc = kNpc;
+  int R = 0;    // rows per thread
+  int CS = 0;   // column slices (warps per row group)
+  int NRG = 0;  // row groups of 32 rows
+  int NT = 0;   // threads per CTA = 32 * CS * NRG
+  int B = 0;    // rows per CTA capacity = 32 * NRG * R
+  size_t smem_qr = 0, smem_fq = 0;
+  int tile = 0;     // index of the register tile (kern_f64.cu / kern_f32.cu)
+  int fq_rows = 0;  // rows per staged chunk of k_form_q (<= B)
+  int rm_rows = 0;  // staged rows per CTA of k_rowmul (<= B; halves hold two inputs)
+  size_t smem_rm = 0;
+};
+
+// Picks the register tile for storage/compute size `esz` (8 or 4) and n.
+bool choose_cfg(int esz, int n, KernelCfg* out);
+
+struct Level {
+  int64_t rows = 0;  // rows of this level's input matrix
+  int64_t b = 0;     // rows per block
+  int64_t p = 0;     // number of blocks
+  size_t off_S = 0;  // byte offset of the p blocks of R (n x n, binary64)
+  size_t off_T = 0;  // byte offset of the p blocks of T (n x n, binary64)
+};
+
+struct Plan {
+  int64_t m = 0, n = 0;
+  int esz = 8;           // element size of the tall matrices
+  KernelCfg cfg0;        // Step-1 kernel config (dtype of A)
+  KernelCfg cfg64;       // tree kernel config (binary64)
+  std::vector<Level> levels;  // levels[0] = Step 1; levels[1..] = tree
+  size_t off_ctop = 0;   // n x n binary64 top coefficient (sign matrix, or D U_R)
+  size_t off_small = 0;  // scratch for small n x n work (SVD, Cholesky, ...)
+  size_t bytes = 0;      // workspace of the TSQR-based ops (direct, svd, indirect)
+  // Gram-based ops (cholqr, backward): partial Grams + small scratch
+  int gram_chunk = 0, gram_grid = 0, gram_nt = 0;
+  size_t off_part = 0, off_gsmall = 0, bytes_gram = 0;
+};
+
+constexpr int kSmallSlots = 8;  // n x n binary64 matrices in each small scratch area
+constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM of a GB300)
+
+// Workspace bytes of `op` (tsqr_op) under a built plan.
+size_t op_bytes(const Plan& P, int op);
+
+// Builds the plan; returns 0 or a tsqr_status code.
+int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan);
+
+}  // namespace tsqr

@@ -1,0 +1,371 @@
+// small.cu -- single-CTA binary64 kernels on n x n matrices (n <= 100).
+// See small.cuh for the contract of each launcher.
+#include <cfloat>
+
+#include "device.cuh"
+#include "small.cuh"
+
+namespace tsqr {
+
+// ---------------------------------------------------------------------------
+__global__ void k_sign_fix(const double* __restrict__ Rraw, int n, double* __restrict__ Rout, int64_t ldr,
+                           double* __restrict__ Ctop, int32_t* status) {
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx % n;
+    const double rik = Rraw[idx];
+    if (!isfinite(rik)) set_status(status, TSQR_ERR_NONFINITE);
+    const double d = Rraw[i * n + i] < 0.0 ? -1.0 : 1.0;
+    Rout[i * ldr + k] = (k >= i) ? d * rik : 0.0;
+    Ctop[idx] = (i == k) ? d : 0.0;
+  }
+}
+
+cudaError_t launch_sign_fix(const double* Rraw, int n, double* Rout, int64_t ldr, double* Ctop, int32_t* status,
+                            cudaStream_t st) {
+  k_sign_fix<<<1, 256, 0, st>>>(Rraw, n, Rout, ldr, Ctop, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Inverse of the upper-triangular R (smem copy `r`, n x n) into `x`, column
+// by column (one thread per column, back substitution).  Returns false (all
+// threads) if a diagonal entry is zero or not finite.
+__device__ bool cta_upper_inverse(const double* r, int n, double* x) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (r[j * n + j] == 0.0 || !isfinite(r[j * n + j])) bad = 1;
+  __syncthreads();
+  if (bad) return false;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = n - 1; i >= 0; --i) {
+      double v;
+      if (i > c) {
+        v = 0.0;
+      } else {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int k = i + 1; k <= c; ++k) s = fma(-r[i * n + k], x[k * n + c], s);
+        v = s / r[i * n + i];
+      }
+      x[i * n + c] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Cholesky QR's small step (Sec. II-A): R = chol(G) (upper, G = R^T R), and
+// Rinv = R^{-1} for Q = A R^{-1} (Sec. II-C computes the inverse of R and
+// multiplies by A).  Breakdown -> TSQR_ERR_NOT_SPD.
+__global__ void k_chol_inv(const double* __restrict__ G, int n, double* __restrict__ R, double* __restrict__ Rinv,
+                           int32_t* status) {
+  extern __shared__ __align__(16) double sm[];
+  double* a = sm;          // n x n: G, then R in its upper triangle
+  double* x = sm + n * n;  // n x n: R^{-1}
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) a[idx] = G[idx];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double s = a[j * n + j];
+      for (int k = 0; k < j; ++k) s = fma(-a[k * n + j], a[k * n + j], s);
+      if (!(s > 0.0) || !isfinite(s)) {
+        fail = 1;
+      } else {
+        a[j * n + j] = sqrt(s);
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+    const double rjj = a[j * n + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      double t = a[j * n + i];
+      for (int k = 0; k < j; ++k) t = fma(-a[k * n + j], a[k * n + i], t);
+      a[j * n + i] = t / rjj;
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (threadIdx.x == 0) set_status(status, TSQR_ERR_NOT_SPD);
+    return;
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx % n;
+    if (k < i) a[idx] = 0.0;
+  }
+  __syncthreads();
+  if (!cta_upper_inverse(a, n, x)) {
+    if (threadIdx.x == 0) set_status(status, TSQR_ERR_NOT_SPD);
+    return;
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    R[idx] = a[idx];
+    Rinv[idx] = x[idx];
+  }
+}
+
+cudaError_t launch_chol_inv(const double* G, int n, double* R, double* Rinv, int32_t* status, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)n * n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_chol_inv<<<1, 128, smem, st>>>(G, n, R, Rinv, status);
+  return cudaGetLastError();
+}
+
+// Rinv = R^{-1} of an upper-triangular R (ldr); zero diagonal -> SINGULAR.
+__global__ void k_rinv(const double* __restrict__ R, int64_t ldr, int n, double* __restrict__ Rinv,
+                       int32_t* status) {
+  extern __shared__ __align__(16) double sm[];
+  double* a = sm;
+  double* x = sm + n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx % n;
+    a[idx] = (k >= i) ? R[i * ldr + k] : 0.0;
+  }
+  __syncthreads();
+  if (!cta_upper_inverse(a, n, x)) {
+    if (threadIdx.x == 0) set_status(status, TSQR_ERR_SINGULAR);
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Rinv[idx] = 0.0;
+    return;
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Rinv[idx] = x[idx];
+}
+
+cudaError_t launch_rinv(const double* R, int64_t ldr, int n, double* Rinv, int32_t* status, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)n * n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_rinv<<<1, 128, smem, st>>>(R, ldr, n, Rinv, status);
+  return cudaGetLastError();
+}
+
+// Rout = R2 R1 (both upper triangular; the refinement's R = R2 R1).  Rout may
+// alias R1: the product is formed in shared memory first.
+__global__ void k_tri_mul(const double* __restrict__ R2, const double* R1, int n, double* Rout, int64_t ldr) {
+  extern __shared__ __align__(16) double sm[];
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx % n;
+    double s = 0.0;
+    for (int l = i; l <= k; ++l) s = fma(R2[i * n + l], R1[l * n + k], s);
+    sm[idx] = (k >= i) ? s : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Rout[(idx / n) * ldr + idx % n] = sm[idx];
+}
+
+cudaError_t launch_tri_mul(const double* R2, const double* R1, int n, double* Rout, int64_t ldr, cudaStream_t st) {
+  const size_t smem = (size_t)n * n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_tri_mul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tri_mul<<<1, 256, smem, st>>>(R2, R1, n, Rout, ldr);
+  return cudaGetLastError();
+}
+
+// Adjoint's small step: M = R dR^T - G (G = dQ^T Q; dR upper part only; either
+// may be NULL), C = copyltu(M) = tril(M) + tril(M,-1)^T, M1 = R^{-T},
+// M2 = C R^{-T}.  Then dA = dQ M1 + Q M2.  Zero diagonal -> SINGULAR.
+__global__ void k_bwd_prep(const double* __restrict__ R, const double* __restrict__ dR,
+                           const double* __restrict__ G, int n, double* __restrict__ M1, double* __restrict__ M2,
+                           int32_t* status) {
+  extern __shared__ __align__(16) double sm[];
+  double* r = sm;              // R (upper)
+  double* x = sm + n * n;      // R^{-1}
+  double* mm = sm + 2 * n * n; // M, then C
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, k = idx % n;
+    r[idx] = (k >= i) ? R[idx] : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    double s = 0.0;
+    if (dR)
+      for (int k = (i > j ? i : j); k < n; ++k) s = fma(r[i * n + k], dR[j * n + k], s);  // dR upper: k >= j
+    if (G) s -= G[idx];
+    mm[idx] = s;
+  }
+  __syncthreads();
+  const bool ok = cta_upper_inverse(r, n, x);
+  if (!ok) {
+    if (threadIdx.x == 0) set_status(status, TSQR_ERR_SINGULAR);
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      M1[idx] = 0.0;
+      M2[idx] = 0.0;
+    }
+    return;
+  }
+  // C = copyltu(M) in place: read both triangles first
+  double cvals[40];
+  const int per = (n * n + blockDim.x - 1) / blockDim.x;  // <= 40 for n <= 100, blockDim >= 256
+  for (int t = 0; t < per; ++t) {
+    const int idx = threadIdx.x + t * blockDim.x;
+    if (idx < n * n) {
+      const int i = idx / n, j = idx % n;
+      cvals[t] = (i >= j) ? mm[i * n + j] : mm[j * n + i];
+    }
+  }
+  __syncthreads();
+  for (int t = 0; t < per; ++t) {
+    const int idx = threadIdx.x + t * blockDim.x;
+    if (idx < n * n) mm[idx] = cvals[t];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int k = idx / n, c = idx % n;
+    M1[idx] = x[c * n + k];  // R^{-T}
+    double s = 0.0;
+    for (int l = c; l < n; ++l) s = fma(mm[k * n + l], x[c * n + l], s);  // (C R^{-T})_{kc}
+    M2[idx] = s;
+  }
+}
+
+cudaError_t launch_bwd_prep(const double* R, const double* dR, const double* G, int n, double* M1, double* M2,
+                            int32_t* status, cudaStream_t st) {
+  const size_t smem = 3 * (size_t)n * n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_bwd_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_bwd_prep<<<1, 256, smem, st>>>(R, dR, G, n, M1, M2, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// SVD of the n x n R (Sec. III-B, SVD paragraph) by one-sided (Hestenes)
+// Jacobi in binary64: columns of W = R are rotated pairwise (round-robin
+// tournament, one pair per warp) until mutually orthogonal; then
+// S_j = ||W_j||, U_R = W diag(S)^{-1}, S sorted descending, each (u_j, v_j)
+// signed so that the largest-|.| entry of v_j is positive (lowest index wins
+// a tie).  The top coefficient is replaced by Ctop D-diagonal times U_R so
+// that Step 3 writes U = Q U_R directly.
+__global__ void k_jacobi_svd(const double* __restrict__ R, int64_t ldr, int n, double* __restrict__ Ctop,
+                             double* __restrict__ S, double* __restrict__ V, int64_t ldv, int32_t* status) {
+  extern __shared__ __align__(16) double sm[];
+  const int np = (n + 1) & ~1;   // even number of slots (a dummy column when n is odd)
+  double* w = sm;                // column-major: column c at w[c * n]
+  double* v = sm + np * n;       // column-major V
+  double* sv = sm + 2 * np * n;  // singular values (unsorted)
+  double* d = sv + np;           // diagonal of the incoming Ctop (the sign matrix D)
+  int* slot = reinterpret_cast<int*>(d + np);  // tournament slots, later the ranks
+  __shared__ int rotated;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int idx = threadIdx.x; idx < np * n; idx += blockDim.x) {
+    const int c = idx / n, i = idx % n;
+    w[idx] = (c < n) ? ((c >= i) ? R[i * ldr + c] : 0.0) : 0.0;
+    v[idx] = (c < n && c == i) ? 1.0 : 0.0;
+  }
+  for (int t = threadIdx.x; t < np; t += blockDim.x) {
+    slot[t] = t;
+    d[t] = (t < n) ? Ctop[t * n + t] : 0.0;
+  }
+  __syncthreads();
+  const double tol = DBL_EPSILON * n;
+  bool converged = false;
+  for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pr = warp; pr < np / 2; pr += nw) {
+        int p = slot[pr], q = slot[np - 1 - pr];
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q >= n) continue;  // dummy column
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          const double a = w[p * n + i], b = w[q * n + i];
+          al = fma(a, a, al);
+          be = fma(b, b, be);
+          ga = fma(a, b, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+          if (lane == 0) rotated = 1;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          for (int i = lane; i < n; i += 32) {
+            const double a = w[p * n + i], b = w[q * n + i];
+            w[p * n + i] = c * a - s * b;
+            w[q * n + i] = s * a + c * b;
+            const double va = v[p * n + i], vb = v[q * n + i];
+            v[p * n + i] = c * va - s * vb;
+            v[q * n + i] = s * va + c * vb;
+          }
+        }
+      }
+      __syncthreads();
+      // next round of the tournament: slot 0 stays, the others rotate by one
+      if (threadIdx.x == 0) {
+        const int last = slot[np - 1];
+        for (int t = np - 1; t > 1; --t) slot[t] = slot[t - 1];
+        slot[1] = last;
+      }
+      __syncthreads();
+    }
+    converged = (rotated == 0);
+    __syncthreads();
+  }
+  if (!converged && threadIdx.x == 0) set_status(status, TSQR_ERR_NOCONV);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double s2 = 0.0;
+    for (int i = 0; i < n; ++i) s2 = fma(w[c * n + i], w[c * n + i], s2);
+    sv[c] = sqrt(s2);
+  }
+  __syncthreads();
+  // rank by descending singular value (ties by index); sign from v's largest entry
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    int rank = 0;
+    for (int k = 0; k < n; ++k)
+      if (sv[k] > sv[c] || (sv[k] == sv[c] && k < c)) ++rank;
+    int imax = 0;
+    for (int i = 1; i < n; ++i)
+      if (fabs(v[c * n + i]) > fabs(v[c * n + imax])) imax = i;
+    const double sg = v[c * n + imax] < 0.0 ? -1.0 : 1.0;
+    const double inv = sv[c] > 0.0 ? 1.0 / sv[c] : 0.0;
+    S[rank] = sv[c];
+    for (int i = 0; i < n; ++i) {
+      V[i * ldv + rank] = sg * v[c * n + i];
+      w[c * n + i] = sg * w[c * n + i] * inv;  // column c of U_R (this thread owns it)
+    }
+    slot[c] = rank;
+  }
+  __syncthreads();
+  // new top coefficient D U_R (U_R column c lands at position rank(c))
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, c = idx % n;
+    Ctop[i * n + slot[c]] = d[i] * w[c * n + i];
+  }
+}
+
+cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop, double* S, double* V,
+                              int64_t ldv, int32_t* status, cudaStream_t st) {
+  const int np = (n + 1) & ~1;
+  const size_t smem = (2 * (size_t)np * n + 2 * np) * sizeof(double) + np * sizeof(int) + 16;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_jacobi_svd<<<1, 512, smem, st>>>(R, ldr, n, Ctop, S, V, ldv, status);
+  return cudaGetLastError();
+}
+
+// G = sum over the nparts partials, in index order (one thread per entry).
+__global__ void k_gram_reduce(const double* __restrict__ part, int nparts, int n, double* __restrict__ G,
+                              int32_t* status) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += part[static_cast<int64_t>(p) * n * n + e];
+  if (!isfinite(s)) set_status(status, TSQR_ERR_NONFINITE);
+  G[e] = s;
+}
+
+cudaError_t launch_gram_reduce(const double* part, int nparts, int n, double* G, int32_t* status,
+                               cudaStream_t st) {
+  const int threads = 256;
+  k_gram_reduce<<<(n * n + threads - 1) / threads, threads, 0, st>>>(part, nparts, n, G, status);
+  return cudaGetLastError();
+}
+
+}  // namespace tsqr

@@ -1,0 +1,82 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/tsqr.h declares; host-side planning checks need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tsqr.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1301_1071_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ["tsqr_direct", "tsqr_svd", "cholqr", "tsqr_indirect_refine", "tsqr_backward",
+                 "tsqr_workspace_size", "tsqr_status_string", "tsqr_read_status"]:
+        assert want in names, want
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), f"missing export {name}"
+
+
+def test_status_strings(lib):
+    lib.tsqr_status_string.restype = ctypes.c_char_p
+    assert lib.tsqr_status_string(0) == b"TSQR_OK"
+    assert b"NOT_SPD" in lib.tsqr_status_string(6)
+    assert b"unknown" in lib.tsqr_status_string(99)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("block_rows", ctypes.c_int64), ("tree_fanout", ctypes.c_int32),
+                ("sync", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+def _ws(lib, op, m, n, dtype, block_rows=0, fanout=0):
+    f = lib.tsqr_workspace_size
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Opts),
+                  ctypes.POINTER(ctypes.c_size_t)]
+    f.restype = ctypes.c_int
+    o = Opts(block_rows, fanout, 0, None)
+    out = ctypes.c_size_t(0)
+    st = f(op, m, n, dtype, ctypes.byref(o), ctypes.byref(out))
+    return st, out.value
+
+
+def test_workspace_size_host_only(lib):
+    st, b = _ws(lib, 0, 8_000_000, 25, 0)
+    assert st == 0
+    # one binary64 R and T block per row block dominates: well under the data size
+    assert 0 < b < 8_000_000 * 25 * 8 // 4
+    st2, b2 = _ws(lib, 0, 100_000, 10, 0, block_rows=1000)
+    assert st2 == 0 and b2 >= 100 * 2 * 10 * 10 * 8
+
+
+@pytest.mark.parametrize("m,n,dt,b,f,want", [
+    (10, 20, 0, 0, 0, 2),       # m < n
+    (100, 0, 0, 0, 0, 2),       # n < 1
+    (1000, 101, 0, 0, 0, 2),    # n > NMAX
+    (1000, 10, 0, 5, 0, 2),     # block_rows < n
+    (1000, 10, 0, 0, 1, 1),     # fanout 1
+    (1000, 10, 7, 0, 0, 1),     # bad dtype
+])
+def test_workspace_size_rejects(lib, m, n, dt, b, f, want):
+    st, _ = _ws(lib, 0, m, n, dt, b, f)
+    assert st == want

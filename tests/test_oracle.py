@@ -221,6 +221,14 @@ def test_indirect_refine_matches_and_degrades():
     assert st == 0 and oracle.orth_error(Q1)[0] < 1e-13  # one refinement step repairs it
 
 
+def test_upper_inverse():
+    R = np.triu(ti.gaussian(6, 6, 49)) + 3 * np.eye(6)
+    X = oracle.upper_inverse(R)
+    assert np.all(np.tril(X, -1) == 0.0)
+    assert np.max(np.abs(X @ R - np.eye(6))) <= 1e-14
+    assert np.max(np.abs(R @ X - np.eye(6))) <= 1e-14
+
+
 def test_right_solve_upper():
     R = np.triu(ti.gaussian(5, 5, 47)) + 3 * np.eye(5)
     X0 = ti.gaussian(9, 5, 48)
@@ -378,6 +386,20 @@ def test_gram_dot2_cancellation():
     x = np.array([[1e16], [1.0], [-1e16], [1.0]])
     y = np.ones((4, 1))
     assert oracle.gram_dot2(x, y)[0, 0] == 2.0
+
+
+@pytest.mark.parametrize("n", [37, 64, 100])
+def test_orth_error_converges_at_large_n(n):
+    # exactly orthonormal Hadamard columns: the checker must converge and give ~0
+    H = _hadamard(8)[:, :n] / 16.0
+    e2, eF = oracle.orth_error(H)
+    assert e2 <= 4 * EPS and eF <= 4 * EPS
+    A = ti.gaussian(3000, n, 80 + n)
+    Q, R = oracle.householder_qr(A)
+    e2, _ = oracle.orth_error(Q)
+    assert e2 <= 1e-14
+    rF, r2 = oracle.residual(A, Q, R)
+    assert rF <= n * EPS and r2 <= n * EPS
 
 
 def test_sym_eig_closed_form():

@@ -34,12 +34,14 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
-def gaussian(m: int, n: int, seed: int, dtype=np.float64) -> np.ndarray:
-    """m x n i.i.d. N(0, 1), generated in FP64 row chunks then cast."""
+def gaussian(m: int, n: int, seed: int, dtype=np.float64, rows: int | None = None) -> np.ndarray:
+    """m x n i.i.d. N(0, 1), generated in FP64 row chunks then cast.  `rows`
+    returns only the first rows of that matrix (a sample of the workload)."""
     rng = _rng(seed)
-    out = np.empty((m, n), dtype=dtype)
-    for r0 in range(0, m, _ROW_CHUNK):
-        r1 = min(m, r0 + _ROW_CHUNK)
+    mm = m if rows is None else min(m, rows)
+    out = np.empty((mm, n), dtype=dtype)
+    for r0 in range(0, mm, _ROW_CHUNK):
+        r1 = min(mm, r0 + _ROW_CHUNK)
         out[r0:r1] = rng.standard_normal((r1 - r0, n))
     return out
 
@@ -59,28 +61,29 @@ def log_spaced(n: int, hi: float, lo: float) -> np.ndarray:
     return np.logspace(np.log10(hi), np.log10(lo), n)
 
 
-def _spectral(m: int, n: int, sigma: np.ndarray, seed: int, dtype) -> np.ndarray:
+def _spectral(m: int, n: int, sigma: np.ndarray, seed: int, dtype, rows: int | None = None) -> np.ndarray:
     rng = _rng(seed)
     v = random_orthogonal(n, seed + 7919)
     mix = (sigma[:, None] * v.T)  # diag(sigma) V^T
-    out = np.empty((m, n), dtype=dtype)
+    mm = m if rows is None else min(m, rows)
+    out = np.empty((mm, n), dtype=dtype)
     scale = 1.0 / np.sqrt(m)
-    for r0 in range(0, m, _ROW_CHUNK):
-        r1 = min(m, r0 + _ROW_CHUNK)
+    for r0 in range(0, mm, _ROW_CHUNK):
+        r1 = min(mm, r0 + _ROW_CHUNK)
         g = rng.standard_normal((r1 - r0, n)) * scale
         out[r0:r1] = g @ mix
     return out
 
 
-def conditioned(m: int, n: int, kappa: float, seed: int, dtype=np.float64) -> np.ndarray:
+def conditioned(m: int, n: int, kappa: float, seed: int, dtype=np.float64, rows: int | None = None) -> np.ndarray:
     """A = G diag(sigma) V^T, G ~ N(0, 1/m), sigma log-spaced 1 .. 1/kappa."""
-    return _spectral(m, n, log_spaced(n, 1.0, 1.0 / kappa), seed, dtype)
+    return _spectral(m, n, log_spaced(n, 1.0, 1.0 / kappa), seed, dtype, rows)
 
 
-def power_spectrum(m: int, n: int, seed: int, dtype=np.float64) -> np.ndarray:
+def power_spectrum(m: int, n: int, seed: int, dtype=np.float64, rows: int | None = None) -> np.ndarray:
     """A = G diag(j^-2) V^T, j = 1..n, G ~ N(0, 1/m)."""
     sigma = 1.0 / np.arange(1, n + 1, dtype=np.float64) ** 2
-    return _spectral(m, n, sigma, seed, dtype)
+    return _spectral(m, n, sigma, seed, dtype, rows)
 
 
 def column_scaled(m: int, n: int, lo: float, seed: int, dtype=np.float64) -> np.ndarray:
