@@ -253,6 +253,9 @@ def main():
 
     # ---- device-resident timed region
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    for e in (x for step in evs for x in step):
+        e.record()  # torch creates the CUDA event on first record; the library then re-records it
+    torch.cuda.synchronize()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = ClockSampler(local)
     barrier()

@@ -64,6 +64,16 @@ typedef enum tsqr_status {
 
 typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
 
+/* Arithmetic of the tall passes (Step 1 and Step 3) for TSQR_F64 data.
+ * NATIVE: IEEE binary64 throughout.
+ * DF64:   binary64 storage, double-float arithmetic (pairs of binary32,
+ *         ~48-bit significand) in Step 1 and Step 3, each row block scaled by
+ *         a power of two (exact); the Step-2 tree, the SVD of R and all n x n
+ *         work stay binary64.  Targets ||Q^TQ - I|| and the residual at the
+ *         1e-13 level for kappa up to ~1e15.  Only tsqr_direct and tsqr_svd
+ *         honour it; TSQR_F32 data require NATIVE. */
+typedef enum tsqr_prec { TSQR_PREC_NATIVE = 0, TSQR_PREC_DF64 = 1 } tsqr_prec;
+
 /* Which computation a workspace is sized for. */
 typedef enum tsqr_op {
   TSQR_OP_DIRECT = 0,
@@ -82,7 +92,8 @@ typedef struct tsqr_opts {
      handles (as void*) recorded on the stream at the start, after Step 1,
      after Step 2 (tree up, top QR, SVD, tree down) and after Step 3. */
   void* const* stage_events;
-  int32_t reserved[2]; /* must be zero */
+  int32_t prec;        /* tsqr_prec (default 0 = NATIVE) */
+  int32_t reserved;    /* must be zero */
 } tsqr_opts;
 
 /*

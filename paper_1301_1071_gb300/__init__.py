@@ -30,6 +30,7 @@ _lock = threading.Lock()
 _lib = None
 
 F64, F32 = 0, 1
+PREC = {"native": 0, "df64": 1}
 OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD = 0, 1, 2, 3, 4
 NMAX = 100
 STATUS = {0: "TSQR_OK", 1: "TSQR_ERR_ARG", 2: "TSQR_ERR_SHAPE", 3: "TSQR_ERR_ALIGN",
@@ -46,7 +47,7 @@ class TSQRError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("block_rows", ctypes.c_int64), ("tree_fanout", ctypes.c_int32),
                 ("sync", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -104,24 +105,28 @@ def _check_tall(A: torch.Tensor):
     return m, n
 
 
-def _opts(block_rows=0, fanout=0, sync=False, events=None) -> Opts:
+def _opts(block_rows=0, fanout=0, sync=False, events=None, prec="native") -> Opts:
     o = Opts()
     o.block_rows = int(block_rows)
     o.tree_fanout = int(fanout)
     o.sync = 1 if sync else 0
+    o.prec = PREC[prec]
     if events is not None:
+        if any(not e.cuda_event for e in events):
+            raise ValueError("stage events must have been recorded once (torch creates them lazily)")
         arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
         o._events_keepalive = arr
         o.stage_events = ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p))
     return o
 
 
-def launch_count(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fanout=0, refine=0) -> int:
+def launch_count(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fanout=0, refine=0,
+                 prec="native") -> int:
     """Kernel launches of one call (host-only query)."""
     lib = load()
     code = F64 if dtype == torch.float64 else F32
     out = ctypes.c_int32(0)
-    o = _opts(block_rows, fanout)
+    o = _opts(block_rows, fanout, prec=prec)
     _raise(lib.tsqr_launch_count(op, m, n, code, ctypes.byref(o), int(refine), ctypes.byref(out)),
            "tsqr_launch_count")
     return int(out.value)
@@ -140,17 +145,17 @@ def _raise(st: int, what: str):
         raise TSQRError(st, what)
 
 
-def workspace_size(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fanout=0) -> int:
+def workspace_size(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fanout=0, prec="native") -> int:
     lib = load()
     code = F64 if dtype == torch.float64 else F32
     out = ctypes.c_size_t(0)
-    o = _opts(block_rows, fanout)
+    o = _opts(block_rows, fanout, prec=prec)
     _raise(lib.tsqr_workspace_size(op, m, n, code, ctypes.byref(o), ctypes.byref(out)), "tsqr_workspace_size")
     return int(out.value)
 
 
-def _workspace(op, m, n, dtype, device, block_rows, fanout, work):
-    need = workspace_size(op, m, n, dtype, block_rows, fanout)
+def _workspace(op, m, n, dtype, device, block_rows, fanout, work, prec="native"):
+    need = workspace_size(op, m, n, dtype, block_rows, fanout, prec)
     if work is None or work.numel() < need:
         work = torch.empty(need, dtype=torch.uint8, device=device)
     return work
@@ -163,17 +168,17 @@ def _status(work: torch.Tensor, what: str, check: bool):
 
 
 def direct(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
-           out: tuple | None = None, check: bool = True, stage_events=None):
+           out: tuple | None = None, check: bool = True, stage_events=None, prec: str = "native"):
     """Direct TSQR: returns (Q, R), Q m x n in A's dtype, R n x n float64,
     diag(R) >= 0.  ``check`` synchronises and raises on a device error.
     ``stage_events``: 4 torch.cuda.Event recorded at the start and after
-    Steps 1, 2 and 3."""
+    Steps 1, 2 and 3.  ``prec``: "native" or "df64" (FP64 data only)."""
     m, n = _check_tall(A)
     A = A.contiguous()
     lib = load()
     Q, R = out if out is not None else (torch.empty_like(A), torch.empty(n, n, dtype=torch.float64, device=A.device))
-    work = _workspace(OP_DIRECT, m, n, A.dtype, A.device, block_rows, fanout, work)
-    o = _opts(block_rows, fanout, events=stage_events)
+    work = _workspace(OP_DIRECT, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
+    o = _opts(block_rows, fanout, events=stage_events, prec=prec)
     st = lib.tsqr_direct(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, _ptr(work), work.numel(),
                          ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_direct")
@@ -182,7 +187,7 @@ def direct(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Te
 
 
 def svd(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
-        check: bool = True):
+        check: bool = True, prec: str = "native"):
     """SVD via direct TSQR: A = U diag(S) V^T (U m x n in A's dtype; S, V float64)."""
     m, n = _check_tall(A)
     A = A.contiguous()
@@ -190,8 +195,8 @@ def svd(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tenso
     U = torch.empty_like(A)
     S = torch.empty(n, dtype=torch.float64, device=A.device)
     V = torch.empty(n, n, dtype=torch.float64, device=A.device)
-    work = _workspace(OP_SVD, m, n, A.dtype, A.device, block_rows, fanout, work)
-    o = _opts(block_rows, fanout)
+    work = _workspace(OP_SVD, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
+    o = _opts(block_rows, fanout, prec=prec)
     st = lib.tsqr_svd(_ptr(A), m, n, n, _dtype_code(A), _ptr(U), n, _ptr(S), _ptr(V), n, _ptr(work),
                       work.numel(), ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_svd")

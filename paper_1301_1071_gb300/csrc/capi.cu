@@ -20,6 +20,10 @@ cudaError_t launch_form_q_f64(const KernelCfg&, const void*, int64_t, int, int64
 cudaError_t launch_form_q_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, const double*,
                               const double*, int64_t, void*, int32_t*, cudaStream_t);
 
+cudaError_t launch_local_qr_df64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, void*, double*,
+                                 double*, int32_t*, cudaStream_t);
+cudaError_t launch_form_q_df64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, const double*,
+                               const double*, int64_t, void*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f64(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f32(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
@@ -27,11 +31,11 @@ cudaError_t launch_rowmul_f32(const KernelCfg&, const void*, const double*, cons
 cudaError_t launch_gram_f64(const void*, const void*, int64_t, int, int, int, int, double*, int32_t*, cudaStream_t);
 cudaError_t launch_gram_f32(const void*, const void*, int64_t, int, int, int, int, double*, int32_t*, cudaStream_t);
 
-cudaError_t launch_rowmul(int esz, const KernelCfg& k, const void* X, const double* M1, const void* Y,
+cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, const void* Y,
                           const double* M2, int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,
                           cudaStream_t st) {
-  return esz == 8 ? launch_rowmul_f64(k, X, M1, Y, M2, m, n, b, p, out, status, st)
-                  : launch_rowmul_f32(k, X, M1, Y, M2, m, n, b, p, out, status, st);
+  return k.kind == kKindF32 ? launch_rowmul_f32(k, X, M1, Y, M2, m, n, b, p, out, status, st)
+                            : launch_rowmul_f64(k, X, M1, Y, M2, m, n, b, p, out, status, st);
 }
 
 cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n, double* part, double* G,
@@ -43,17 +47,25 @@ cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n,
   return launch_gram_reduce(part, g.grid, n, G, status, st);
 }
 
-cudaError_t launch_local_qr(int esz, const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t p,
-                            void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
-  return esz == 8 ? launch_local_qr_f64(k, A, m, n, b, p, Y, Rst, Tst, status, st)
-                  : launch_local_qr_f32(k, A, m, n, b, p, Y, Rst, Tst, status, st);
+cudaError_t launch_local_qr(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t p, void* Y,
+                            double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+  switch (k.kind) {
+    case kKindF64: return launch_local_qr_f64(k, A, m, n, b, p, Y, Rst, Tst, status, st);
+    case kKindF32: return launch_local_qr_f32(k, A, m, n, b, p, Y, Rst, Tst, status, st);
+    case kKindDF64: return launch_local_qr_df64(k, A, m, n, b, p, Y, Rst, Tst, status, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_form_q(int esz, const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t p,
+cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t p,
                           const double* T, const double* C, int64_t cblocks, void* Q, int32_t* status,
                           cudaStream_t st) {
-  return esz == 8 ? launch_form_q_f64(k, Y, m, n, b, p, T, C, cblocks, Q, status, st)
-                  : launch_form_q_f32(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
+  switch (k.kind) {
+    case kKindF64: return launch_form_q_f64(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
+    case kKindF32: return launch_form_q_f32(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
+    case kKindDF64: return launch_form_q_df64(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 namespace {
@@ -64,8 +76,8 @@ int esz_of(int32_t dtype) { return dtype == TSQR_F64 ? 8 : (dtype == TSQR_F32 ? 
 
 tsqr_status check_opts(const tsqr_opts* o) {
   if (!o) return TSQR_OK;
-  for (int i = 0; i < 2; ++i)
-    if (o->reserved[i] != 0) return TSQR_ERR_ARG;
+  if (o->reserved != 0) return TSQR_ERR_ARG;
+  if (o->prec != TSQR_PREC_NATIVE && o->prec != TSQR_PREC_DF64) return TSQR_ERR_ARG;
   if (o->block_rows < 0 || o->tree_fanout < 0 || o->tree_fanout == 1) return TSQR_ERR_ARG;
   return TSQR_OK;
 }
@@ -119,13 +131,13 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   // Step 1: local QR of every row block; Y_0 is written into Q's storage.
   const Level& l0 = P.levels[0];
   if (mark(o, 0, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  if (launch_local_qr(P.esz, P.cfg0, A, P.m, n, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
+  if (launch_local_qr(P.cfg0, A, P.m, n, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
   // Step 2 (Alg. 2): the stack of level l-1 is the tall input of level l.
   for (size_t l = 1; l < L; ++l) {
     const Level& lv = P.levels[l];
-    if (launch_local_qr(8, P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, S(l - 1), S(l), T(l), status, st) !=
+    if (launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, S(l - 1), S(l), T(l), status, st) !=
         cudaSuccess)
       return TSQR_ERR_CUDA;
   }
@@ -136,7 +148,7 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
     const Level& lv = P.levels[l];
     const double* C = (l == L - 1) ? ctop : S(l);
     const int64_t cb = (l == L - 1) ? 1 : lv.p;
-    if (launch_form_q(8, P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, T(l), C, cb, S(l - 1), status, st) !=
+    if (launch_form_q(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, T(l), C, cb, S(l - 1), status, st) !=
         cudaSuccess)
       return TSQR_ERR_CUDA;
   }
@@ -144,7 +156,7 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
   const double* C0 = (L == 1) ? ctop : S(0);
   const int64_t cb0 = (L == 1) ? 1 : l0.p;
-  if (launch_form_q(P.esz, P.cfg0, Q, P.m, n, l0.b, l0.p, T(0), C0, cb0, Q, status, st) != cudaSuccess)
+  if (launch_form_q(P.cfg0, Q, P.m, n, l0.b, l0.p, T(0), C0, cb0, Q, status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   return mark(o, 3, st);
 }
@@ -159,11 +171,11 @@ tsqr_status run_r_only(const Plan& P, int esz, const void* X, double* R, void* w
   auto S = [&](size_t l) { return reinterpret_cast<double*>(at(work, P.levels[l].off_S)); };
   double* ctop = reinterpret_cast<double*>(at(work, P.off_ctop));
   const Level& l0 = P.levels[0];
-  if (launch_local_qr(esz, P.cfg0, X, P.m, n, l0.b, l0.p, nullptr, S(0), nullptr, status, st) != cudaSuccess)
+  if (launch_local_qr(P.cfg0, X, P.m, n, l0.b, l0.p, nullptr, S(0), nullptr, status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   for (size_t l = 1; l < L; ++l) {
     const Level& lv = P.levels[l];
-    if (launch_local_qr(8, P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, nullptr, S(l), nullptr, status, st) !=
+    if (launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, nullptr, S(l), nullptr, status, st) !=
         cudaSuccess)
       return TSQR_ERR_CUDA;
   }
@@ -176,7 +188,7 @@ tsqr_status rowmul(const Plan& P, const void* X, const double* M1, const void* Y
                    int32_t* status, cudaStream_t st) {
   const int64_t b = (X && Y) ? P.cfg0.rm_rows / 2 : P.cfg0.rm_rows;
   const int64_t p = (P.m + b - 1) / b;
-  return launch_rowmul(P.esz, P.cfg0, X, M1, Y, M2, P.m, (int)P.n, b, p, out, status, st) == cudaSuccess
+  return launch_rowmul(P.cfg0, X, M1, Y, M2, P.m, (int)P.n, b, p, out, status, st) == cudaSuccess
              ? TSQR_OK
              : TSQR_ERR_CUDA;
 }
@@ -197,7 +209,8 @@ tsqr_status copy_r(double* R, int64_t ldr, const double* src, int64_t n, cudaStr
 
 tsqr_status plan_for(int op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* o, size_t work_bytes,
                      const void* work, Plan* P) {
-  int rc = make_plan(m, n, esz_of(dtype), o ? o->block_rows : 0, o ? o->tree_fanout : 0, P);
+  const int prec = (o && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? o->prec : 0;
+  int rc = make_plan(m, n, esz_of(dtype), o ? o->block_rows : 0, o ? o->tree_fanout : 0, P, prec);
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   if (!work || !aligned16(work) || work_bytes < op_bytes(*P, op)) return TSQR_ERR_WORKSPACE;
   return TSQR_OK;
@@ -234,8 +247,9 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
   if (esz == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
+  const int prec = (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? opts->prec : 0;
   Plan P;
-  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P);
+  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec);
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   const int L = static_cast<int>(P.levels.size());
   switch (op) {
@@ -267,8 +281,9 @@ tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
   if (op < TSQR_OP_DIRECT || op > TSQR_OP_BACKWARD) return TSQR_ERR_ARG;
+  const int prec = (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? opts->prec : 0;
   Plan P;
-  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P);
+  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec);
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   *bytes = op_bytes(P, op);
   return TSQR_OK;
@@ -284,7 +299,8 @@ tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_
   const int esz = esz_of(dtype);
   if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
   Plan P;
-  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P);
+  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P,
+                     opts ? opts->prec : 0);
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   if (!work || work_bytes < P.bytes || !aligned16(work)) return TSQR_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

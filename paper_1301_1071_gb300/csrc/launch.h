@@ -8,17 +8,18 @@
 
 namespace tsqr {
 
-// Step 1 / tree level: p CTAs, one per row block of b rows.
-cudaError_t launch_local_qr(int esz, const KernelCfg& k, const void* A, int64_t m, int n, int64_t b,
+// Step 1 / tree level: p CTAs, one per row block of b rows (k.kind selects
+// the storage/compute types).
+cudaError_t launch_local_qr( const KernelCfg& k, const void* A, int64_t m, int n, int64_t b,
                             int64_t p, void* Y, double* Rst, double* Tst, int32_t* status,
                             cudaStream_t st);
 // Step 3 / tree down-pass: p CTAs.
-cudaError_t launch_form_q(int esz, const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b,
+cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b,
                           int64_t p, const double* T, const double* C, int64_t cblocks, void* Q,
                           int32_t* status, cudaStream_t st);
 
 // out_r = X_r M1 + Y_r M2 over p blocks of b rows (X or Y may be NULL).
-cudaError_t launch_rowmul(int esz, const KernelCfg& k, const void* X, const double* M1, const void* Y,
+cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, const void* Y,
                           const double* M2, int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,
                           cudaStream_t st);
 // Partial Grams X^T Y (grid partials of n x n binary64), then their fixed-order sum into G.

@@ -18,12 +18,14 @@ constexpr int kNumTiles = 4;
 static const TileChoice kTiles64[kNumTiles] = {{12, 320}, {8, 448}, {4, 640}, {8, 640}};
 static const TileChoice kTiles32[kNumTiles] = {{24, 320}, {16, 448}, {8, 640}, {16, 640}};
 
-bool choose_cfg(int esz, int n, KernelCfg* out) {
+bool choose_cfg(int kind, int n, KernelCfg* out) {
   if (n < 1 || n > TSQR_NMAX) return false;
+  const int esz = kind == kKindF32 ? 4 : 8;
   const int CS = (n + kNpc - 1) / kNpc;
   const int NPAD = CS * kNpc;
-  const TileChoice* tiles = esz == 8 ? kTiles64 : kTiles32;
+  const TileChoice* tiles = kind == kKindF32 ? kTiles32 : kTiles64;
   KernelCfg best;
+  best.kind = kind;
   for (int ti = 0; ti < kNumTiles; ++ti) {
     const int R = tiles[ti].R;
     for (int NRG = tiles[ti].maxt / (32 * CS); NRG >= 1; --NRG) {
@@ -71,13 +73,15 @@ size_t op_bytes(const Plan& P, int op) {
   return (op == TSQR_OP_CHOLQR || op == TSQR_OP_BACKWARD) ? P.bytes_gram : P.bytes;
 }
 
-int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan) {
+int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec) {
   if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  if (prec != TSQR_PREC_NATIVE && (prec != TSQR_PREC_DF64 || esz != 8)) return TSQR_ERR_ARG;
   Plan P;
   P.m = m;
   P.n = n;
   P.esz = esz;
-  if (!choose_cfg(esz, (int)n, &P.cfg0) || !choose_cfg(8, (int)n, &P.cfg64)) return TSQR_ERR_SHAPE;
+  const int kind0 = esz == 4 ? kKindF32 : (prec == TSQR_PREC_DF64 ? kKindDF64 : kKindF64);
+  if (!choose_cfg(kind0, (int)n, &P.cfg0) || !choose_cfg(kKindF64, (int)n, &P.cfg64)) return TSQR_ERR_SHAPE;
   int64_t b0 = block_rows > 0 ? block_rows : P.cfg0.B;
   if (b0 < n || b0 > P.cfg0.B) return TSQR_ERR_SHAPE;
   // tree node = f stacked R factors, f >= 2

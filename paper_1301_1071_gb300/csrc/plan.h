@@ -13,7 +13,11 @@ constexpr int kNpc = 5;                // columns per thread (register tile widt
 constexpr size_t kSmemMax = 232448;    // 227 KB dynamic shared memory per CTA
 constexpr size_t kHeaderBytes = 256;   // status word + padding at the start of work
 
+// Kernel kind of a tall pass: storage / compute types.
+enum KernelKind { kKindF64 = 0, kKindF32 = 1, kKindDF64 = 2 };
+
 struct KernelCfg {
+  int kind = kKindF64;
   int npc = kNpc;
   int R = 0;    // rows per thread
   int CS = 0;   // column slices (warps per row group)
@@ -27,8 +31,8 @@ struct KernelCfg {
   size_t smem_rm = 0;
 };
 
-// Picks the register tile for storage/compute size `esz` (8 or 4) and n.
-bool choose_cfg(int esz, int n, KernelCfg* out);
+// Picks the register tile of kernel kind `kind` for n.
+bool choose_cfg(int kind, int n, KernelCfg* out);
 
 struct Level {
   int64_t rows = 0;  // rows of this level's input matrix
@@ -59,6 +63,6 @@ constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM
 size_t op_bytes(const Plan& P, int op);
 
 // Builds the plan; returns 0 or a tsqr_status code.
-int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan);
+int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec = 0);
 
 }  // namespace tsqr

@@ -19,7 +19,10 @@
 // H = I - tau v v^T; a zero column gives tau = 0 (H = I).
 #pragma once
 
+#include <type_traits>
+
 #include "device.cuh"
+#include "df64.cuh"
 #include "layout.cuh"
 
 namespace tsqr {
@@ -88,6 +91,33 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
     for (int c = 0; c < NPC; ++c) {
       const int k = cs + c * CS;
       a[q][c] = (r < rows && k < n) ? static_cast<T>(stage[r * n + k]) : T(0);
+    }
+  }
+  // Double-float compute: scale the block by a power of two (exact) so that
+  // its largest entry is ~1 and products of small entries stay in binary32
+  // range.  Y and T are invariant under the scaling; R is unscaled on output.
+  int scale_exp = 0;
+  if constexpr (std::is_same<T, df64>::value) {
+    float mx = 0.0f;
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+      for (int c = 0; c < NPC; ++c) mx = fmaxf(mx, fabsf(a[q][c].hi));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float* wmax = reinterpret_cast<float*>(red);
+    if (lane == 0) wmax[warp] = mx;
+    __syncthreads();
+    float bm = 0.0f;
+    for (int w = 0; w < NW; ++w) bm = fmaxf(bm, wmax[w]);
+    if (bm > 0.0f && isfinite(bm)) {
+      int e;
+      frexpf(bm, &e);
+      scale_exp = e;  // bm = f * 2^e, f in [0.5, 1)
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int c = 0; c < NPC; ++c) a[q][c] = scale2(a[q][c], -scale_exp);
     }
   }
   __syncthreads();  // stage is reused for the Gram matrix from here on
@@ -230,7 +260,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         const int k = cs + c * CS;
         if (k < n)
           Rst[static_cast<int64_t>(blockIdx.x) * n * n + r * n + k] =
-              (k >= r && r < rows) ? static_cast<double>(a[q][c]) : 0.0;
+              (k >= r && r < rows) ? ldexp(static_cast<double>(a[q][c]), scale_exp) : 0.0;
       }
     }
   }

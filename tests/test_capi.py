@@ -46,7 +46,7 @@ def test_status_strings(lib):
 class Opts(ctypes.Structure):
     _fields_ = [("block_rows", ctypes.c_int64), ("tree_fanout", ctypes.c_int32),
                 ("sync", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _ws(lib, op, m, n, dtype, block_rows=0, fanout=0):
@@ -54,7 +54,7 @@ def _ws(lib, op, m, n, dtype, block_rows=0, fanout=0):
     f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Opts),
                   ctypes.POINTER(ctypes.c_size_t)]
     f.restype = ctypes.c_int
-    o = Opts(block_rows, fanout, 0, None)
+    o = Opts(block_rows, fanout, 0, None, 0, 0)
     out = ctypes.c_size_t(0)
     st = f(op, m, n, dtype, ctypes.byref(o), ctypes.byref(out))
     return st, out.value
