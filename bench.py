@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip comparators / fwd+bwd / cpu baseline")
     ap.add_argument("--m", type=int, default=0, help="override the row count (profiling a smaller case)")
+    ap.add_argument("--prec", default="native", choices=["native", "df64"],
+                    help="arithmetic of Steps 1 and 3 for FP64 data")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.m:
@@ -242,14 +244,14 @@ def main():
     A = torch.from_numpy(A_host).to(dev)
     Q = torch.empty_like(A)
     R = torch.empty(n, n, dtype=torch.float64, device=dev)
-    work = torch.empty(T.workspace_size(T.OP_DIRECT, m, n, A.dtype, w["block_rows"]), dtype=torch.uint8,
-                       device=dev)
-    bench_kw = dict(block_rows=w["block_rows"], work=work, out=(Q, R), check=False)
+    work = torch.empty(T.workspace_size(T.OP_DIRECT, m, n, A.dtype, w["block_rows"], prec=args.prec),
+                       dtype=torch.uint8, device=dev)
+    bench_kw = dict(block_rows=w["block_rows"], work=work, out=(Q, R), check=False, prec=args.prec)
 
     for _ in range(args.warmup):
         T.direct(A, **bench_kw)
     torch.cuda.synchronize()
-    T.direct(A, block_rows=w["block_rows"], work=work, out=(Q, R), check=True)  # raises on a device error
+    T.direct(A, block_rows=w["block_rows"], work=work, out=(Q, R), check=True, prec=args.prec)  # raises on error
 
     # ---- device-resident timed region
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
@@ -332,11 +334,14 @@ def main():
     e2e = {"value": replica_throughput(m, k_e2e, ws, e2e_ms), "unit": "rows/s",
            "h2d_bytes_per_step": m * n * elem, "d2h_bytes_per_step": m * n * elem + n * n * 8}
 
-    launches = T.launch_count(T.OP_DIRECT, m, n, A.dtype, w["block_rows"]) * args.steps
+    launches = T.launch_count(T.OP_DIRECT, m, n, A.dtype, w["block_rows"], prec=args.prec) * args.steps
     line = {
         "metric": METRIC, "value": rows_s, "unit": "rows/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if elem == 8 else "f32", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": ("df64 (binary64 data, pairs of binary32 in Steps 1 and 3, binary64 tree)" if args.prec == "df64"
+                  else ("f64" if elem == 8 else "f32")),
+        "data": "synthetic",
         "config": {"workload": w["name"], "m": m, "n": n, "block_rows": w["block_rows"] or "auto",
                    "l2": "inputs (1.6 GB) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
         "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm_peak,
@@ -348,7 +353,7 @@ def main():
     }
 
     if not args.no_extras and rank == 0:
-        line["extras"] = extras(T, torch, A, n, m, dev)
+        line["extras"] = extras(T, torch, A, n, m, dev, other_prec="native" if args.prec == "df64" else "df64")
     if not args.no_extras and rank == 0:
         line["cpu_baseline"] = cpu_baseline(A_host)
     if rank == 0:
@@ -358,8 +363,9 @@ def main():
     return 0
 
 
-def extras(T, torch, A, n, m, dev, steps=3):
-    """fwd+bwd and the unstable comparators on the same matrix."""
+def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
+    """fwd+bwd, the other precision mode, and the unstable comparators on the
+    same matrix."""
     out = {}
 
     def timed(fn):
@@ -391,6 +397,11 @@ def extras(T, torch, A, n, m, dev, steps=3):
     ms = timed(fb)
     out["fwd_bwd"] = {"rows_s": m / (ms * 1e-3), "ms": ms,
                       "hbm_gbs_algorithmic": 9 * m * n * A.element_size() / (ms * 1e-3) / 1e9}
+    if A.dtype == torch.float64:
+        Qp, Rp = T.direct(A, prec=other_prec)
+        ms = timed(lambda: T.direct(A, check=False, prec=other_prec))
+        out[f"direct_{other_prec}"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Qp),
+                                       "hbm_gbs_algorithmic": 4 * m * n * 8 / (ms * 1e-3) / 1e9}
     for name, fn in [("cholqr", lambda: T.cholqr(A, refine=0, check=False)),
                      ("cholqr_ir", lambda: T.cholqr(A, refine=1, check=False)),
                      ("indirect_ir", lambda: T.indirect_refine(A, refine=1, check=False))]:
