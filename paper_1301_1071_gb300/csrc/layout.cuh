@@ -16,30 +16,29 @@ TSQR_HD constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a *
 
 // Shared-memory layout of k_local_qr (identical on host and device).
 struct LocalQrSmem {
-  size_t stage, red, xcol, piv, ssum, dk, tau, scal, bar, total;
+  size_t stage, red, xcol, piv, tau, bar, total;
   TSQR_HD LocalQrSmem(int B, int n, int NW, int NPAD, size_t ssz, size_t tsz) {
     size_t o = 0;
     stage = o; o = align_up(o + (size_t)B * n * ssz, 16);
-    // the stage buffer must also hold the n x n Gram / T matrix during the loop
-    size_t gram_bytes = (size_t)n * n * tsz;
+    // after the register load the stage holds the n x n Gram matrix (compute
+    // type) and the T factor (binary64 for double-float, else compute type)
+    size_t gram_bytes = align_up((size_t)n * n * tsz, 16) + (size_t)n * n * (tsz > 8 ? tsz : 8);
     if ((size_t)B * n * ssz < gram_bytes) o = align_up(stage + gram_bytes, 16);
-    red = o; o = align_up(o + (size_t)NW * 32 * tsz, 16);
-    xcol = o; o = align_up(o + 2 * (size_t)B * tsz, 16);  // double-buffered pivot column
-    piv = o; o = align_up(o + (size_t)NPAD * tsz, 16);
-    ssum = o; o = align_up(o + (size_t)NPAD * tsz, 16);
-    dk = o; o = align_up(o + (size_t)NPAD * tsz, 16);
+    red = o; o = align_up(o + 2 * (size_t)NW * 32 * tsz, 16);  // double-buffered partials
+    xcol = o; o = align_up(o + 2 * (size_t)B * tsz, 16);      // double-buffered pivot column
+    piv = o; o = align_up(o + 2 * (size_t)NPAD * tsz, 16);    // double-buffered pivot row
     tau = o; o = align_up(o + (size_t)NPAD * tsz, 16);
-    scal = o; o = align_up(o + 8 * tsz, 16);
     bar = o; o = align_up(o + 16, 16);
     total = o;
   }
 };
 
 struct FormQSmem {
-  size_t stage, wm, bar, total;
+  size_t stage, xm, wm, bar, total;
   TSQR_HD FormQSmem(int B, int n, int NPAD, size_t ssz, size_t tsz) {
     size_t o = 0;
     stage = o; o = align_up(o + (size_t)B * n * ssz, 16);
+    xm = o; o = align_up(o + (size_t)n * NPAD * tsz, 16);
     wm = o; o = align_up(o + (size_t)n * NPAD * tsz, 16);
     bar = o; o = align_up(o + 16, 16);
     total = o;

@@ -18,7 +18,10 @@ constexpr int kNumTiles = 4;
 static const TileChoice kTiles64[kNumTiles] = {{12, 320}, {8, 448}, {4, 640}, {8, 640}};
 static const TileChoice kTiles32[kNumTiles] = {{24, 320}, {16, 448}, {8, 640}, {16, 640}};
 
-bool choose_cfg(int kind, int n, KernelCfg* out) {
+// Picks the register tile and row-group count.  want_b > 0: the smallest
+// capacity B >= want_b (ties: the taller register tile); want_b == 0: the
+// default policy below.
+bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int min_b) {
   if (n < 1 || n > TSQR_NMAX) return false;
   const int esz = kind == kKindF32 ? 4 : 8;
   const int CS = (n + kNpc - 1) / kNpc;
@@ -31,7 +34,7 @@ bool choose_cfg(int kind, int n, KernelCfg* out) {
     for (int NRG = tiles[ti].maxt / (32 * CS); NRG >= 1; --NRG) {
       const int B = 32 * NRG * R;
       const int NT = 32 * CS * NRG;
-      if (B < n) break;
+      if (B < n || B < min_b) break;
       size_t a = LocalQrSmem(B, n, NT / 32, NPAD, esz, esz).total;
       if (a > kSmemMax) continue;
       int fq_rows = B;  // k_form_q stages its block in chunks of fq_rows rows
@@ -41,12 +44,24 @@ bool choose_cfg(int kind, int n, KernelCfg* out) {
       int rm_rows = B;  // k_rowmul also stages two n x NPAD matrices: shrink its stage
       while (rm_rows > 32 && RowMulSmem(rm_rows, n, NPAD, esz, esz).total > kSmemMax) rm_rows -= 32;
       if (RowMulSmem(rm_rows, n, NPAD, esz, esz).total > kSmemMax) continue;
-      if (B > best.B) {  // largest row block wins; ties keep the earlier tile
+      bool take;
+      if (want_b > 0) {
+        take = B >= want_b && (best.B == 0 || B < best.B || (B == best.B && R > best.R));
+      } else if (policy == kPolicyLargest) {
+        take = B > best.B;  // largest row block wins; ties keep the earlier tile
+      } else {
+        // Step 1: the tallest register tile within 320 threads (>= 168
+        // registers per thread, no forced spills), then the largest block;
+        // wider CTAs only when n needs them
+        const bool narrow = NT <= 320, best_narrow = best.NT > 0 && best.NT <= 320;
+        take = best.B == 0 || (narrow && !best_narrow) ||
+               (narrow == best_narrow && (R > best.R || (R == best.R && B > best.B)));
+      }
+      if (take) {
         best.npc = kNpc; best.R = R; best.CS = CS; best.NRG = NRG; best.NT = NT; best.B = B;
         best.smem_qr = a; best.smem_fq = f; best.tile = ti; best.fq_rows = fq_rows;
         best.rm_rows = rm_rows; best.smem_rm = RowMulSmem(rm_rows, n, NPAD, esz, esz).total;
       }
-      break;
     }
   }
   if (best.B == 0) return false;
@@ -81,7 +96,9 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   P.n = n;
   P.esz = esz;
   const int kind0 = esz == 4 ? kKindF32 : (prec == TSQR_PREC_DF64 ? kKindDF64 : kKindF64);
-  if (!choose_cfg(kind0, (int)n, &P.cfg0) || !choose_cfg(kKindF64, (int)n, &P.cfg64)) return TSQR_ERR_SHAPE;
+  if (!choose_cfg(kind0, (int)n, &P.cfg0, block_rows, kPolicyStep1) ||
+      !choose_cfg(kKindF64, (int)n, &P.cfg64, 0, kPolicyStep1, 2 * (int)n))
+    return TSQR_ERR_SHAPE;
   int64_t b0 = block_rows > 0 ? block_rows : P.cfg0.B;
   if (b0 < n || b0 > P.cfg0.B) return TSQR_ERR_SHAPE;
   // tree node = f stacked R factors, f >= 2

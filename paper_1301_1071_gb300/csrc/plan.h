@@ -31,8 +31,14 @@ struct KernelCfg {
   size_t smem_rm = 0;
 };
 
-// Picks the register tile of kernel kind `kind` for n.
-bool choose_cfg(int kind, int n, KernelCfg* out);
+// Default tile policies: kPolicyStep1 favours tall register tiles in narrow
+// CTAs (used for Step 1 and, with at least 2n rows so that a node merges two
+// or more R factors, for the tree); kPolicyLargest takes the largest block.
+enum { kPolicyStep1 = 0, kPolicyLargest = 1 };
+
+// Picks the register tile of kernel kind `kind` for n (want_b > 0: the
+// smallest per-CTA capacity that holds want_b rows; else `policy`).
+bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b = 0, int policy = kPolicyStep1, int min_b = 0);
 
 struct Level {
   int64_t rows = 0;  // rows of this level's input matrix

@@ -35,6 +35,137 @@ __device__ __forceinline__ float dev_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dev_copysign(double a, double b) { return copysign(a, b); }
 __device__ __forceinline__ float dev_copysign(float a, float b) { return copysignf(a, b); }
 
+// Storage <-> compute conversions.  Double-float compute converts binary64
+// with integer operations (split_scaled / to_double) so that no binary64
+// arithmetic is spent on data movement; `shift` scales by 2^-shift (exact).
+template <class T, class S>
+__device__ __forceinline__ T to_compute(S x, int shift) {
+  if constexpr (std::is_same<T, df64>::value) {
+    return split_scaled(x, shift);
+  } else {
+    (void)shift;
+    return static_cast<T>(x);
+  }
+}
+template <class S, class T>
+__device__ __forceinline__ S to_storage(T v) {
+  if constexpr (std::is_same<T, df64>::value) {
+    return to_double(v);
+  } else {
+    return static_cast<S>(v);
+  }
+}
+// Householder scalars of one column from S_j = ||x||^2 and alpha = x_1:
+// beta = -copysign(sqrt(S_j), alpha), scal = 1/(alpha - beta), ib = 1/beta,
+// tau = (beta - alpha)/beta; a zero column gives the identity (tau = 0).
+template <class T>
+struct Reflector {
+  T beta, scal, ib, tau;
+  bool ident;
+};
+// binary64 reciprocal by Newton's iteration y <- y + y (1 - x y) from a
+// binary32 seed (2^-24 -> 2^-48 -> below one ulp after two steps); outside
+// the binary32 range the IEEE division is used.  Four dependent FMAs instead
+// of a full division sequence on the slow binary64 unit.
+__device__ __forceinline__ double recip_of(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
+  double y = static_cast<double>(1.0f / static_cast<float>(x));
+  y = fma(fma(-x, y, 1.0), y, y);
+  y = fma(fma(-x, y, 1.0), y, y);
+  return y;
+}
+__device__ __forceinline__ float recip_of(float x) { return 1.0f / x; }
+// double-float reciprocal and square root without binary64 arithmetic, from
+// a correctly rounded binary32 estimate and an exactly formed residual (a
+// TwoSum of its two leading parts plus the TwoProduct error terms), so that
+// only the final rounding to the pair remains (~2^-49 relative).
+__device__ __forceinline__ df64 recip_of(df64 x) {
+  // 1/x = y0 / (1 - e), e = 1 - x y0 = 1 - (p + pe) - (q + qe), |e| <= 2^-22:
+  // y0 (1 + e + e^2).  pe is as large as e itself, so e is summed with TwoSums.
+  const float y0 = 1.0f / x.hi;
+  const float p = x.hi * y0, pe = fmaf(x.hi, y0, -p);  // x.hi y0 = p + pe
+  const float q = x.lo * y0, qe = fmaf(x.lo, y0, -q);  // x.lo y0 = q + qe
+  const df64 d2 = two_sum(1.0f - p, -pe);              // 1 - p is exact
+  const df64 d3 = two_sum(d2.hi, -q);
+  const df64 e = fast_two_sum(d3.hi, (d2.lo + d3.lo) - qe);
+  const float r = y0 * e.hi, re = fmaf(y0, e.hi, -r);
+  const float small = fmaf(y0, fmaf(e.hi, e.hi, e.lo), re);
+  df64 y = fast_two_sum(y0, r);
+  y.lo += small;
+  return fast_two_sum(y.hi, y.lo);
+}
+__device__ __forceinline__ double sqrt_of(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_of(float x) { return sqrtf(x); }
+__device__ __forceinline__ df64 sqrt_of(df64 x) {
+  // s0 = sqrt(x.hi); r = x - s0^2 = (x.hi - p) - pe + x.lo summed with TwoSums;
+  // sqrt(x) = s0 + c - c^2/(2 s0), c = r / (2 s0) carried as two words
+  const float s0 = sqrtf(x.hi);
+  if (s0 == 0.0f) return df64(0.0f, 0.0f);
+  const float p = s0 * s0, pe = fmaf(s0, s0, -p);
+  const df64 d2 = two_sum(x.hi - p, -pe);  // x.hi - p is exact
+  const df64 d3 = two_sum(d2.hi, x.lo);
+  const float rl = d2.lo + d3.lo;
+  const float t = 2.0f * s0, h = 0.5f / s0;
+  const float c0 = d3.hi * h;
+  const float c1 = fmaf(fmaf(-c0, t, d3.hi) + rl, h, c0);      // r / (2 s0), rounded
+  const float res = fmaf(-c1, t, d3.hi) + rl;                    // r - c1 (2 s0)
+  const float clo = fmaf(res, h, (-c1 * c1) * h);                // the rest of c - c^2/(2 s0)
+  df64 y = fast_two_sum(s0, c1);
+  y.lo += clo;
+  return fast_two_sum(y.hi, y.lo);
+}
+template <class T>
+__device__ __forceinline__ Reflector<T> make_reflector(T Sj, T alpha) {
+  Reflector<T> f;
+  const T sigma = sqrt_of(Sj);
+  if (sigma == T(0)) {
+    f.beta = alpha; f.scal = T(0); f.ib = T(0); f.tau = T(0); f.ident = true;
+  } else {
+    f.beta = -dev_copysign(sigma, alpha);
+    f.scal = recip_of(alpha - f.beta);
+    f.ib = recip_of(f.beta);
+    f.tau = (f.beta - alpha) * f.ib;
+    f.ident = false;
+  }
+  return f;
+}
+template <class T>
+__device__ __forceinline__ T shfl_bcast(T v) {
+  if constexpr (std::is_same<T, df64>::value) {
+    return df64(__shfl_sync(0xffffffffu, v.hi, 0), __shfl_sync(0xffffffffu, v.lo, 0));
+  } else {
+    return __shfl_sync(0xffffffffu, v, 0);
+  }
+}
+
+// Trailing update of the thread's tile for column j, with the first trailing
+// local column C0 known at compile time: a[q][c] -= d[c] x_q for c >= C0.
+// The warp owning column j (local index C0 - 1) stores v_j = x scal below the
+// pivot; the warp owning column j + 1 (local index C0) publishes it.
+template <int C0, int NPC, int R, class T>
+__device__ __forceinline__ void tile_update(T (&a)[R][NPC], const T (&d)[NPC], const T* xcur, T* xnext, int j,
+                                            int rbase, int RS, bool own_j, bool own_next, T scal) {
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int r = rbase + q * RS;
+    const T xq = (r >= j) ? xcur[r] : T(0);
+#pragma unroll
+    for (int c = C0; c < NPC; ++c) a[q][c] = fma(-d[c], xq, a[q][c]);
+    if constexpr (C0 >= 1) {
+      if (own_j) a[q][C0 - 1] = (r > j) ? xq * scal : a[q][C0 - 1];
+    }
+    if constexpr (C0 < NPC) {
+      if (own_next) xnext[r] = a[q][C0];
+    }
+  }
+}
+
+// Y between Step 1 and Step 3 is kept in the compute format when that has the
+// storage's size (double-float pairs in place of binary64): no conversion.
+template <class S, class T>
+using YStore = typename std::conditional<std::is_same<T, df64>::value, df64, S>::type;
+
 // ---------------------------------------------------------------------------
 // Step 1: local Householder QR of one row block per CTA.
 //   A    : m x n row-major (storage S); block i = rows [i*b, min(i*b+b, m)).
@@ -57,14 +188,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   S* stage = reinterpret_cast<S*>(smem + L.stage);
   T* gram = reinterpret_cast<T*>(smem + L.stage);  // reused during the loop
   T* red = reinterpret_cast<T*>(smem + L.red);
-  // pivot column, double-buffered by the parity of j: in phase C the warps
-  // owning column j+1 publish it while other column slices still read x_j
+  // pivot column, pivot row and the partial sums are double-buffered by the
+  // parity of j: while slow warps still read step j's values, fast ones
+  // publish step j+1's, so one barrier per phase suffices
   T* xbuf = reinterpret_cast<T*>(smem + L.xcol);
   T* piv = reinterpret_cast<T*>(smem + L.piv);
-  T* ssum = reinterpret_cast<T*>(smem + L.ssum);
-  T* dk = reinterpret_cast<T*>(smem + L.dk);
   T* taus = reinterpret_cast<T*>(smem + L.tau);
-  T* sc = reinterpret_cast<T*>(smem + L.scal);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -77,12 +206,40 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
     mbar_init(bar, 1);
     fence_mbar_init();
   }
-  for (int k = tid; k < NPAD; k += NT) dk[k] = T(0);
   __syncthreads();
   uint32_t parity = 0;
   if (!cta_load_bulk(stage, A + row0 * n, static_cast<int64_t>(rows) * n, bar, parity, status)) return;
   __syncthreads();
 
+  // Double-float compute: scale the block by a power of two (exact) chosen
+  // from the largest binary64 exponent, so that its entries are below 1 and
+  // products of small entries stay in binary32 range.  Y and T are invariant
+  // under the scaling; R is unscaled on output.
+  int scale_exp = 0;
+  if constexpr (std::is_same<T, df64>::value) {
+    int emax = 0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int r = rg * 32 + lane + q * RS;
+#pragma unroll
+      for (int c = 0; c < NPC; ++c) {
+        const int k = cs + c * CS;
+        if (r < rows && k < n) {
+          const int ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(
+                                              static_cast<double>(stage[r * n + k]))) >> 52) & 0x7ff);
+          emax = ex != 0x7ff && ex > emax ? ex : emax;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    int* wmax = reinterpret_cast<int*>(red);
+    if (lane == 0) wmax[warp] = emax;
+    __syncthreads();
+    int bm = 0;
+    for (int w = 0; w < NW; ++w) bm = max(bm, wmax[w]);
+    scale_exp = bm > 0 ? bm - 1022 : 0;  // max |a| * 2^-scale_exp < 1
+  }
   T a[R][NPC];
 #pragma unroll
   for (int q = 0; q < R; ++q) {
@@ -90,34 +247,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
 #pragma unroll
     for (int c = 0; c < NPC; ++c) {
       const int k = cs + c * CS;
-      a[q][c] = (r < rows && k < n) ? static_cast<T>(stage[r * n + k]) : T(0);
-    }
-  }
-  // Double-float compute: scale the block by a power of two (exact) so that
-  // its largest entry is ~1 and products of small entries stay in binary32
-  // range.  Y and T are invariant under the scaling; R is unscaled on output.
-  int scale_exp = 0;
-  if constexpr (std::is_same<T, df64>::value) {
-    float mx = 0.0f;
-#pragma unroll
-    for (int q = 0; q < R; ++q)
-#pragma unroll
-      for (int c = 0; c < NPC; ++c) mx = fmaxf(mx, fabsf(a[q][c].hi));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    float* wmax = reinterpret_cast<float*>(red);
-    if (lane == 0) wmax[warp] = mx;
-    __syncthreads();
-    float bm = 0.0f;
-    for (int w = 0; w < NW; ++w) bm = fmaxf(bm, wmax[w]);
-    if (bm > 0.0f && isfinite(bm)) {
-      int e;
-      frexpf(bm, &e);
-      scale_exp = e;  // bm = f * 2^e, f in [0.5, 1)
-#pragma unroll
-      for (int q = 0; q < R; ++q)
-#pragma unroll
-        for (int c = 0; c < NPC; ++c) a[q][c] = scale2(a[q][c], -scale_exp);
+      a[q][c] = (r < rows && k < n) ? to_compute<T>(stage[r * n + k], scale_exp) : T(0);
     }
   }
   __syncthreads();  // stage is reused for the Gram matrix from here on
@@ -133,119 +263,114 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   }
   __syncthreads();
 
+  const int rbase = rg * 32 + lane;
   for (int j = 0; j < n; ++j) {
-    const T* xcol = xbuf + (j & 1) * B;   // x_j
-    T* xnext = xbuf + ((j + 1) & 1) * B;  // x_{j+1}
-    // ---- phase A: s = x^T A over the thread's active rows, CTA reduction
-    T s[NPC];
-#pragma unroll
-    for (int c = 0; c < NPC; ++c) s[c] = T(0);
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int r = rg * 32 + lane + q * RS;
-      const T xq = (r >= j) ? xcol[r] : T(0);
-#pragma unroll
-      for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
-    }
-    TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, red + warp * 32);
-    __syncthreads();
+    const int jb = j & 1;
+    const T* xcur = xbuf + jb * B;          // x_j (column j, current values)
+    T* xnext = xbuf + (jb ^ 1) * B;         // x_{j+1}
+    const T* pcur = piv + jb * NPAD;        // row j
+    T* pnext = piv + (jb ^ 1) * NPAD;       // row j+1
+    T* rcur = red + jb * NW * 32;           // partial sums of this step
 
-    // ---- phase B: warp 0 combines, forms the reflector and the update coefficients
-    if (warp == 0) {
-      for (int k = lane; k < n; k += 32) {
-        const int kcs = k % CS, kc = k / CS;
-        T acc = T(0);
-        for (int g = 0; g < NRG; ++g) acc += red[(g * CS + kcs) * 32 + kc];
-        ssum[k] = acc;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        const T alpha = piv[j];
-        const T sigma = dev_sqrt(ssum[j]);
-        T beta, amb, scal, ib, tau;
-        if (sigma == T(0)) {
-          beta = alpha; amb = T(0); scal = T(0); ib = T(0); tau = T(0);
-        } else {
-          beta = -dev_copysign(sigma, alpha);
-          amb = alpha - beta;
-          scal = T(1) / amb;
-          ib = T(1) / beta;
-          tau = (beta - alpha) * ib;
-        }
-        sc[0] = beta; sc[1] = amb; sc[2] = scal; sc[3] = ib;
-        sc[4] = (sigma == T(0)) ? T(1) : T(0);  // identity reflector
-        taus[j] = tau;
-      }
-      __syncwarp();
-      const T beta = sc[0], scal = sc[2], ib = sc[3];
-      for (int k = lane; k < NPAD; k += 32) {
-        if (k > j && k < n) {
-          dk[k] = (piv[k] - ssum[k] * ib) * scal;
-        } else if (k < j) {
-          gram[k * n + j] = scal * (ssum[k] - beta * piv[k]);
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---- phase C: trailing update, store v_j, pivot row = R row j,
-    //      publish pivot column/row j+1
+    // ---- phase A: s = x_j^T A over the thread's rows (rows < j give 0), CTA partials
     {
-      const T beta = sc[0], scal = sc[2], ib = sc[3];
-      const bool ident = sc[4] != T(0);
-      // first local column index with global column > j (warp-uniform)
-      const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;
-      const bool own_j = (cs == j % CS);
-      const int cj = j / CS;
-      T d[NPC];
+      T s[NPC];
+      if constexpr (std::is_same<T, df64>::value) {
+        df64_acc acc[NPC];
 #pragma unroll
-      for (int c = 0; c < NPC; ++c) d[c] = (c >= c0) ? dk[cs + c * CS] : T(0);
+        for (int q = 0; q < R; ++q) {
+          const int r = rbase + q * RS;
+          const T xq = (r >= j) ? xcur[r] : T(0);
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) acc[c].add_prod(xq, a[q][c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NPC; ++c) s[c] = acc[c].value();
+      } else {
+#pragma unroll
+        for (int c = 0; c < NPC; ++c) s[c] = T(0);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int r = rbase + q * RS;
+          const T xq = (r >= j) ? xcur[r] : T(0);
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
+        }
+      }
+      TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
+    }
+    __syncthreads();
+
+    // ---- phase B (every warp): the reflector and this thread's update coefficients
+    Reflector<T> f;
+    if (lane == 0) {
+      T Sj = T(0);
+      for (int g = 0; g < NRG; ++g) Sj += rcur[(g * CS + j % CS) * 32 + j / CS];
+      f = make_reflector(Sj, pcur[j]);
+    }
+    f.beta = shfl_bcast(f.beta);
+    f.scal = shfl_bcast(f.scal);
+    f.ib = shfl_bcast(f.ib);
+    f.tau = shfl_bcast(f.tau);
+    f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
+    if (warp == 0) {
+      if (lane == 0) taus[j] = f.tau;
+      for (int kk = lane; kk < j; kk += 32) {  // Gram entries v_k^T v_j for T
+        T Sk = T(0);
+        for (int g = 0; g < NRG; ++g) Sk += rcur[(g * CS + kk % CS) * 32 + kk / CS];
+        gram[kk * n + j] = f.scal * (Sk - f.beta * pcur[kk]);
+      }
+    }
+    T d[NPC];
+#pragma unroll
+    for (int c = 0; c < NPC; ++c) {
+      const int col = cs + c * CS;
+      T Sc = T(0);
+      for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + c];
+      d[c] = (col > j && col < n) ? (pcur[col] - Sc * f.ib) * f.scal : T(0);
+    }
+
+    // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
+    const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
+    const bool own_j = (cs == j % CS);
+    const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
+    switch (c0) {
+      case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
+      case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
+      case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
+      case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
+      case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
+      default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
+    }
+    // the thread holding row j (one per column slice) writes R's row j
+    if (!f.ident && (j - rbase) >= 0 && (j - rbase) % RS == 0) {
+      const int qj = (j - rbase) / RS;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int r = rg * 32 + lane + q * RS;
-        if (r >= j) {
-          const T xq = xcol[r];
-          if (r > j) {
-#pragma unroll
-            for (int c = 0; c < NPC; ++c)
-              if (c >= c0) a[q][c] = fma(-d[c], xq, a[q][c]);
-            if (own_j) {
-#pragma unroll
-              for (int c = 0; c < NPC; ++c)
-                if (c == cj) a[q][c] = xq * scal;
-            }
-          } else if (!ident) {  // pivot row: R_jj = beta, R_jk = (x^T a_k) / beta
-#pragma unroll
-            for (int c = 0; c < NPC; ++c) {
-              if (c >= c0 && cs + c * CS < n) a[q][c] = ssum[cs + c * CS] * ib;
-              if (own_j && c == cj) a[q][c] = beta;
-            }
-          }
-        }
-      }
-      if (j + 1 < n) {
-        const int jn = j + 1;
-        if (cs == jn % CS) {
-          const int cn = jn / CS;
+        if (q == qj) {
 #pragma unroll
           for (int c = 0; c < NPC; ++c) {
-            if (c == cn) {
-#pragma unroll
-              for (int q = 0; q < R; ++q) xnext[rg * 32 + lane + q * RS] = a[q][c];
-            }
-          }
-        }
-        const int qp = jn / RS, wp = jn % RS;
-        if (rg == wp / 32 && lane == wp % 32) {
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            if (q == qp) {
-#pragma unroll
-              for (int c = 0; c < NPC; ++c) piv[cs + c * CS] = a[q][c];
+            const int col = cs + c * CS;
+            if (col > j && col < n) {
+              T Sc = T(0);
+              for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + c];
+              a[q][c] = Sc * f.ib;
+            } else if (col == j) {
+              a[q][c] = f.beta;
             }
           }
         }
       }
+    }
+    // the thread holding row j+1 publishes it (after this step's update)
+    if (j + 1 < n && (j + 1 - rbase) >= 0 && (j + 1 - rbase) % RS == 0) {
+      const int qn = (j + 1 - rbase) / RS;
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        if (q == qn) {
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
+        }
     }
     __syncthreads();
   }
@@ -260,46 +385,48 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         const int k = cs + c * CS;
         if (k < n)
           Rst[static_cast<int64_t>(blockIdx.x) * n * n + r * n + k] =
-              (k >= r && r < rows) ? ldexp(static_cast<double>(a[q][c]), scale_exp) : 0.0;
+              (k >= r && r < rows) ? (scale_exp ? ldexp(static_cast<double>(a[q][c]), scale_exp)
+                                                 : static_cast<double>(a[q][c]))
+                                   : 0.0;
       }
     }
   }
 
   if (Y == nullptr) return;  // R-only mode (indirect TSQR)
 
-  // ---- T_i from the Gram entries (in place, column by column), warp 0
+  // ---- T_i from the Gram entries: T(j,j) = tau_j,
+  //      T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j)   (i < j)
+  // column by column on warp 0 (lane = row), in binary64 for double-float
+  // compute (short dependency chains), into a buffer after the Gram matrix
+  using TT = typename std::conditional<std::is_same<T, df64>::value, double, T>::type;
+  TT* tw = reinterpret_cast<TT*>(smem + L.stage + align_up(static_cast<size_t>(n) * n * sizeof(T), 16));
   if (warp == 0) {
     for (int j = 0; j < n; ++j) {
-      T tv[4];  // n <= 128 rows of T per column: 4 per lane
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int i = lane + 32 * t;
-        T acc = T(0);
-        if (i < j) {
-          for (int l = i; l < j; ++l) {
-            const T til = (l == i) ? taus[i] : gram[i * n + l];
-            acc = fma(til, gram[l * n + j], acc);
-          }
+      const TT tj = static_cast<TT>(taus[j]);
+      for (int i = lane; i < j; i += 32) {
+        TT a0 = static_cast<TT>(taus[i]) * static_cast<TT>(gram[i * n + j]);
+        TT a1 = TT(0);
+        int l = i + 1;
+        for (; l + 1 < j; l += 2) {
+          a0 = fma(tw[i * n + l], static_cast<TT>(gram[l * n + j]), a0);
+          a1 = fma(tw[i * n + l + 1], static_cast<TT>(gram[(l + 1) * n + j]), a1);
         }
-        tv[t] = -taus[j] * acc;
-      }
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int i = lane + 32 * t;
-        if (i < j) gram[i * n + j] = tv[t];
+        if (l < j) a0 = fma(tw[i * n + l], static_cast<TT>(gram[l * n + j]), a0);
+        tw[i * n + j] = -tj * (a0 + a1);
       }
       __syncwarp();
     }
     double* Tout = Tst + static_cast<int64_t>(blockIdx.x) * n * n;
     for (int idx = lane; idx < n * n; idx += 32) {
-      const int i = idx / n, k = idx % n;
-      Tout[idx] = (k > i) ? static_cast<double>(gram[idx]) : (k == i ? static_cast<double>(taus[i]) : 0.0);
+      const int i = idx / n, kk = idx % n;
+      Tout[idx] = (kk > i) ? static_cast<double>(tw[idx]) : (kk == i ? static_cast<double>(taus[i]) : 0.0);
     }
   }
   __syncthreads();
 
-  // ---- Y_i back through shared memory, bulk store
+  // ---- Y_i back through shared memory, bulk store (compute format for df64)
+  using YS = YStore<S, T>;
+  YS* ystage = reinterpret_cast<YS*>(stage);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int r = rg * 32 + lane + q * RS;
@@ -307,13 +434,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
 #pragma unroll
       for (int c = 0; c < NPC; ++c) {
         const int k = cs + c * CS;
-        if (k < n) stage[r * n + k] = static_cast<S>(a[q][c]);
+        if (k < n) {
+          if constexpr (std::is_same<YS, T>::value) ystage[r * n + k] = a[q][c];
+          else ystage[r * n + k] = static_cast<YS>(a[q][c]);
+        }
       }
     }
   }
   fence_proxy_async_smem();
   __syncthreads();
-  cta_store_bulk(Y + row0 * n, stage, static_cast<int64_t>(rows) * n);
+  cta_store_bulk(reinterpret_cast<YS*>(Y) + row0 * n, ystage, static_cast<int64_t>(rows) * n);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,6 +461,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
   const int NPAD = NPC * CS;
   const FormQSmem L(srows, n, NPAD, sizeof(S), sizeof(T));
   S* stage = reinterpret_cast<S*>(smem + L.stage);
+  T* Xm = reinterpret_cast<T*>(smem + L.xm);
   T* Wm = reinterpret_cast<T*>(smem + L.wm);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
 
@@ -340,7 +471,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
   const int RS = 32 * NRG;
   const int ntop = rows < n ? rows : n;
-  const S* Yb = Yg + row0 * n;
+  using YS = YStore<S, T>;
+  const YS* Yb = reinterpret_cast<const YS*>(Yg) + row0 * n;
+  YS* ystage = reinterpret_cast<YS*>(stage);
 
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -351,25 +484,25 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
   const double* Cb = Cg + cb * n * n;
 
   // X = Y_top^T C  (Y_top unit lower triangular, rows < ntop, read from
-  // global memory before any row of this block is overwritten), into Wm
+  // global memory before any row of this block is overwritten)
   for (int idx = tid; idx < n * NPAD; idx += NT) {
     const int k = idx / NPAD, c = idx % NPAD;
     T acc = T(0);
     if (c < n && k < ntop) {
-      acc = static_cast<T>(Cb[k * n + c]);
+      acc = to_compute<T>(Cb[k * n + c], 0);
       for (int r = k + 1; r < ntop; ++r)
-        acc = fma(static_cast<T>(Yb[r * n + k]), static_cast<T>(Cb[r * n + c]), acc);
+        acc = fma(static_cast<T>(Yb[r * n + k]), to_compute<T>(Cb[r * n + c], 0), acc);
     }
-    Wm[idx] = acc;
+    Xm[idx] = acc;
   }
   __syncthreads();
-  // W = T X in place, one thread per column: row k of W only needs rows >= k of X
-  for (int c = tid; c < n; c += NT) {
-    for (int k = 0; k < n; ++k) {
-      T acc = T(0);
-      for (int i = k; i < n; ++i) acc = fma(static_cast<T>(Tb[k * n + i]), Wm[i * NPAD + c], acc);
-      Wm[k * NPAD + c] = acc;
-    }
+  // W = T X (T upper triangular), one entry per thread
+  for (int idx = tid; idx < n * NPAD; idx += NT) {
+    const int k = idx / NPAD, c = idx % NPAD;
+    T acc = T(0);
+    if (c < n)
+      for (int i = k; i < n; ++i) acc = fma(to_compute<T>(Tb[k * n + i], 0), Xm[i * NPAD + c], acc);
+    Wm[idx] = acc;
   }
   __syncthreads();
 
@@ -377,7 +510,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
   uint32_t parity = 0;
   for (int c0 = 0; c0 < rows; c0 += srows) {
     const int crows = rows - c0 < srows ? rows - c0 : srows;
-    if (!cta_load_bulk(stage, Yb + static_cast<int64_t>(c0) * n, static_cast<int64_t>(crows) * n, bar, parity,
+    if (!cta_load_bulk(ystage, Yb + static_cast<int64_t>(c0) * n, static_cast<int64_t>(crows) * n, bar, parity,
                        status))
       return;
     T acc[R][NPC];
@@ -387,7 +520,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
 #pragma unroll
       for (int c = 0; c < NPC; ++c) {
         const int k = cs + c * CS;
-        acc[q][c] = (r < ntop && k < n) ? static_cast<T>(Cb[r * n + k]) : T(0);
+        acc[q][c] = (r < ntop && k < n) ? to_compute<T>(Cb[r * n + k], 0) : T(0);
       }
     }
     for (int k = 0; k < n; ++k) {
@@ -399,7 +532,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
         const int rl = rg * 32 + lane + q * RS;  // row within the chunk
         const int r = c0 + rl;
         T y = T(0);
-        if (rl < crows) y = (k < r) ? static_cast<T>(stage[rl * n + k]) : (k == r ? T(1) : T(0));
+        if (rl < crows) y = (k < r) ? static_cast<T>(ystage[rl * n + k]) : (k == r ? T(1) : T(0));
 #pragma unroll
         for (int c = 0; c < NPC; ++c) acc[q][c] = fma(-y, w[c], acc[q][c]);
       }
@@ -412,7 +545,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
 #pragma unroll
         for (int c = 0; c < NPC; ++c) {
           const int k = cs + c * CS;
-          if (k < n) stage[rl * n + k] = static_cast<S>(acc[q][c]);
+          if (k < n) stage[rl * n + k] = to_storage<S>(acc[q][c]);
         }
       }
     }
