@@ -167,6 +167,33 @@ tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const 
                           void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
 
 /*
+ * Direct TSQR without a caller-provided workspace (the paper has no
+ * counterpart; this is a deployment convenience).  Same computation,
+ * arguments and outputs as tsqr_direct, but the workspace is a fixed array of
+ * TSQR_STATIC_WORK_BYTES in device memory owned by the library, so the call
+ * allocates nothing.  It is meant for callers that cannot allocate device
+ * memory themselves: a host framework that owns all device memory and forbids
+ * other allocations, a latency-critical caller that cannot pay for the
+ * implicit device synchronisation of cudaMalloc/cudaFree, or plain C code
+ * without a device allocator.
+ *  - Limit: the problem's tsqr_workspace_size(TSQR_OP_DIRECT, ...) must not
+ *    exceed TSQR_STATIC_WORK_BYTES (16 MiB; e.g. about 1.2 million rows at
+ *    n = 25 in FP64); larger problems get TSQR_ERR_WORKSPACE before any launch.
+ *  - Every GPU that loads the library holds the array until the process exits.
+ *  - The first call on each device (with that device current) looks up the
+ *    array's device address; make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (different
+ *    streams, host threads or processes' concurrent kernels on the same
+ *    device) race and give undefined results.  Order them on one stream.
+ *  - The status word lives in the array and is cleared at every call; pass
+ *    opts->sync = 1 to get a data-dependent error as the return value.
+ */
+#define TSQR_STATIC_WORK_BYTES (16u * 1024u * 1024u)
+tsqr_status tsqr_direct_static(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                               void* Q, int64_t ldq, double* R, int64_t ldr,
+                               const tsqr_opts* opts, void* stream);
+
+/*
  * Number of kernel launches one call of `op` makes for this shape and opts
  * (refine_steps applies to TSQR_OP_CHOLQR / TSQR_OP_INDIRECT).  Host-only.
  */

@@ -21,7 +21,7 @@ import threading
 
 import torch
 
-__all__ = ["direct", "svd", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
+__all__ = ["direct", "direct_static", "svd", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
            "workspace_size", "launch_count", "library_path", "load", "STATUS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -69,6 +69,7 @@ def load():
         sigs = {
             "tsqr_workspace_size": [I32, I64, I64, I32, OP, ctypes.POINTER(SZ)],
             "tsqr_direct": [P, I64, I64, I64, I32, P, I64, P, I64, P, SZ, OP, P],
+            "tsqr_direct_static": [P, I64, I64, I64, I32, P, I64, P, I64, OP, P],
             "tsqr_svd": [P, I64, I64, I64, I32, P, I64, P, P, I64, P, SZ, OP, P],
             "cholqr": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
             "tsqr_indirect_refine": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
@@ -183,6 +184,22 @@ def direct(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Te
                          ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_direct")
     _status(work, "tsqr_direct", check)
+    return Q, R
+
+
+def direct_static(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, prec: str = "native"):
+    """Direct TSQR on the library's fixed device scratch (no workspace is
+    allocated for the call; problems needing more than 16 MiB of workspace
+    are rejected).  Returns (Q, R); synchronises to report device errors."""
+    m, n = _check_tall(A)
+    A = A.contiguous()
+    lib = load()
+    Q = torch.empty_like(A)
+    R = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    o = _opts(block_rows, fanout, sync=True, prec=prec)
+    st = lib.tsqr_direct_static(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, ctypes.byref(o),
+                                _stream(A.device))
+    _raise(st, "tsqr_direct_static")
     return Q, R
 
 
