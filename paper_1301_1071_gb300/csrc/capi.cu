@@ -134,12 +134,14 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   if (launch_local_qr(P.cfg0, A, P.m, n, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
+  if (launch_build_t(T(0), l0.p, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
   // Step 2 (Alg. 2): the stack of level l-1 is the tall input of level l.
   for (size_t l = 1; l < L; ++l) {
     const Level& lv = P.levels[l];
     if (launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, S(l - 1), S(l), T(l), status, st) !=
         cudaSuccess)
       return TSQR_ERR_CUDA;
+    if (launch_build_t(T(l), lv.p, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
   }
   if (launch_sign_fix(S(L - 1), n, R, ldr, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
   if (extra(ctop) != TSQR_OK) return TSQR_ERR_CUDA;
@@ -253,8 +255,8 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   const int L = static_cast<int>(P.levels.size());
   switch (op) {
-    case TSQR_OP_DIRECT: *launches = 2 * L + 1; break;        // L up, sign fix, L down
-    case TSQR_OP_SVD: *launches = 2 * L + 2; break;           // + Jacobi SVD
+    case TSQR_OP_DIRECT: *launches = 3 * L + 1; break;        // L up (+ T build), sign fix, L down
+    case TSQR_OP_SVD: *launches = 3 * L + 2; break;           // + Jacobi SVD
     case TSQR_OP_CHOLQR: *launches = 4 * (1 + refine_steps) + refine_steps; break;  // gram, reduce, chol, rowmul (+ combine)
     case TSQR_OP_INDIRECT: *launches = (L + 3) * (1 + refine_steps) + refine_steps; break;
     case TSQR_OP_BACKWARD: *launches = 4; break;              // gram, reduce, prep, rowmul

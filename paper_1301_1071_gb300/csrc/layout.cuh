@@ -20,9 +20,8 @@ struct LocalQrSmem {
   TSQR_HD LocalQrSmem(int B, int n, int NW, int NPAD, size_t ssz, size_t tsz) {
     size_t o = 0;
     stage = o; o = align_up(o + (size_t)B * n * ssz, 16);
-    // after the register load the stage holds the n x n Gram matrix (compute
-    // type) and the T factor (binary64 for double-float, else compute type)
-    size_t gram_bytes = align_up((size_t)n * n * tsz, 16) + (size_t)n * n * (tsz > 8 ? tsz : 8);
+    // after the register load the stage holds the n x n Gram matrix
+    size_t gram_bytes = (size_t)n * n * tsz;
     if ((size_t)B * n * ssz < gram_bytes) o = align_up(stage + gram_bytes, 16);
     red = o; o = align_up(o + 2 * (size_t)NW * 32 * tsz, 16);  // double-buffered partials
     xcol = o; o = align_up(o + 2 * (size_t)B * tsz, 16);      // double-buffered pivot column

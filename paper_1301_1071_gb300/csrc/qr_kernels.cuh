@@ -131,6 +131,14 @@ __device__ __forceinline__ Reflector<T> make_reflector(T Sj, T alpha) {
   return f;
 }
 template <class T>
+__device__ __forceinline__ T shfl_from(T v, int src) {
+  if constexpr (std::is_same<T, df64>::value) {
+    return df64(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+  } else {
+    return __shfl_sync(0xffffffffu, v, src);
+  }
+}
+template <class T>
 __device__ __forceinline__ T shfl_bcast(T v) {
   if constexpr (std::is_same<T, df64>::value) {
     return df64(__shfl_sync(0xffffffffu, v.hi, 0), __shfl_sync(0xffffffffu, v.lo, 0));
@@ -172,7 +180,8 @@ using YStore = typename std::conditional<std::is_same<T, df64>::value, df64, S>:
 //   Y    : output, same shape; may alias A (the block is staged first).  NULL
 //          = R-only mode (no Y, no T).
 //   Rst  : p blocks of n x n binary64 (R_i, upper triangular, raw signs).
-//   Tst  : p blocks of n x n binary64 (T_i, upper triangular), or NULL.
+//   Tst  : p blocks of n x n binary64 receiving tau_j on the diagonal and the
+//          Gram entries v_i^T v_j above it (k_build_t then forms T_i), or NULL.
 // Launch: blockDim = 32*CS*NRG <= MAXT, gridDim = p, dynamic smem = LocalQrSmem.
 // ---------------------------------------------------------------------------
 template <class S, class T, int NPC, int R, int MAXT>
@@ -321,13 +330,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         gram[kk * n + j] = f.scal * (Sk - f.beta * pcur[kk]);
       }
     }
+    // update coefficients of this warp's columns: lane c forms column c's
+    // d_c = (a_jk - S_k / beta) / (alpha - beta), then all lanes take it
     T d[NPC];
+    {
+      T dl = T(0);
+      if (lane < NPC) {
+        const int col = cs + lane * CS;
+        if (col > j && col < n) {
+          T Sc = T(0);
+          for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
+          dl = (pcur[col] - Sc * f.ib) * f.scal;
+        }
+      }
 #pragma unroll
-    for (int c = 0; c < NPC; ++c) {
-      const int col = cs + c * CS;
-      T Sc = T(0);
-      for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + c];
-      d[c] = (col > j && col < n) ? (pcur[col] - Sc * f.ib) * f.scal : T(0);
+      for (int c = 0; c < NPC; ++c) d[c] = shfl_from(dl, c);
     }
 
     // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
@@ -394,32 +411,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
 
   if (Y == nullptr) return;  // R-only mode (indirect TSQR)
 
-  // ---- T_i from the Gram entries: T(j,j) = tau_j,
-  //      T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j)   (i < j)
-  // column by column on warp 0 (lane = row), in binary64 for double-float
-  // compute (short dependency chains), into a buffer after the Gram matrix
-  using TT = typename std::conditional<std::is_same<T, df64>::value, double, T>::type;
-  TT* tw = reinterpret_cast<TT*>(smem + L.stage + align_up(static_cast<size_t>(n) * n * sizeof(T), 16));
+  // ---- the Gram entries v_i^T v_j (i < j) and tau_j of the compact-WY form,
+  //      binary64, into the T slot; k_build_t turns them into T_i
   if (warp == 0) {
-    for (int j = 0; j < n; ++j) {
-      const TT tj = static_cast<TT>(taus[j]);
-      for (int i = lane; i < j; i += 32) {
-        TT a0 = static_cast<TT>(taus[i]) * static_cast<TT>(gram[i * n + j]);
-        TT a1 = TT(0);
-        int l = i + 1;
-        for (; l + 1 < j; l += 2) {
-          a0 = fma(tw[i * n + l], static_cast<TT>(gram[l * n + j]), a0);
-          a1 = fma(tw[i * n + l + 1], static_cast<TT>(gram[(l + 1) * n + j]), a1);
-        }
-        if (l < j) a0 = fma(tw[i * n + l], static_cast<TT>(gram[l * n + j]), a0);
-        tw[i * n + j] = -tj * (a0 + a1);
-      }
-      __syncwarp();
-    }
     double* Tout = Tst + static_cast<int64_t>(blockIdx.x) * n * n;
     for (int idx = lane; idx < n * n; idx += 32) {
       const int i = idx / n, kk = idx % n;
-      Tout[idx] = (kk > i) ? static_cast<double>(tw[idx]) : (kk == i ? static_cast<double>(taus[i]) : 0.0);
+      Tout[idx] = (kk > i) ? static_cast<double>(gram[idx]) : (kk == i ? static_cast<double>(taus[i]) : 0.0);
     }
   }
   __syncthreads();

@@ -350,6 +350,50 @@ cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop,
   return cudaGetLastError();
 }
 
+// Compact-WY T factors of p row blocks, in place (one warp per block): the
+// slot holds tau_j on the diagonal and the Gram entries G(i,j) = v_i^T v_j
+// above it; T(j,j) = tau_j and T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j),
+// column by column (H_1 ... H_k = I - Y T Y^T).
+__global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t blk = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (blk >= p) return;
+  double* t = Tst + blk * n * n;
+  for (int j = 1; j < n; ++j) {
+    const double tj = t[j * n + j];
+    double v[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = lane + 32 * s;
+      double a0 = 0.0, a1 = 0.0;
+      if (i < j) {
+        a0 = t[i * n + i] * t[i * n + j];  // T(i,i) = tau_i times G(i,j)
+        int l = i + 1;
+        for (; l + 1 < j; l += 2) {
+          a0 = fma(t[i * n + l], t[l * n + j], a0);
+          a1 = fma(t[i * n + l + 1], t[(l + 1) * n + j], a1);
+        }
+        if (l < j) a0 = fma(t[i * n + l], t[l * n + j], a0);
+      }
+      v[s] = -tj * (a0 + a1);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = lane + 32 * s;
+      if (i < j) t[i * n + j] = v[s];
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_build_t(double* Tst, int64_t p, int n, cudaStream_t st) {
+  const int warps = 8;
+  const int64_t grid = (p + warps - 1) / warps;
+  k_build_t<<<static_cast<unsigned>(grid), 32 * warps, 0, st>>>(Tst, p, n);
+  return cudaGetLastError();
+}
+
 // G = sum over the nparts partials, in index order (one thread per entry).
 __global__ void k_gram_reduce(const double* __restrict__ part, int nparts, int n, double* __restrict__ G,
                               int32_t* status) {
