@@ -162,6 +162,17 @@ __device__ __forceinline__ T shfl_xor(T v, int o) {
 // `limit` is the exclusive end of the indices owned by the current subtree:
 // the padding slot of an odd-length half must not be written, because its
 // index belongs to the sibling subtree.
+// Named CTA barrier `id` (1..15; 0 is __syncthreads) over `nthreads`
+// threads (a multiple of 32): producers arrive without waiting, consumers
+// wait until all `nthreads` have arrived.  Writes made by a producer before
+// its arrive are visible to the consumers after their sync.
+__device__ __forceinline__ void named_bar_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 template <int V, int O>
 struct TransposeReduce {
   template <class T>
@@ -185,10 +196,11 @@ struct TransposeReduce {
         T keep = up ? hi : lo;
         t[i] = keep + shfl_xor(send, O);
       }
-      if (up)
-        TransposeReduce<H, O / 2>::run(t, lane, base + H, limit, dst);
-      else
-        TransposeReduce<H, O / 2>::run(t, lane, base, (base + H < limit) ? base + H : limit, dst);
+      // one call with selected arguments: no divergent branch, so every
+      // lane reaches the same shuffles
+      const int nbase = up ? base + H : base;
+      const int nlimit = up ? limit : ((base + H < limit) ? base + H : limit);
+      TransposeReduce<H, O / 2>::run(t, lane, nbase, nlimit, dst);
     }
   }
 };

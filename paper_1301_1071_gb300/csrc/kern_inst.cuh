@@ -1,5 +1,5 @@
 // kern_inst.cuh -- instantiates the TSQR kernels for one (storage, compute)
-// type pair and four register tiles (R_i rows per thread, at most T_i threads
+// type pair and five register tiles (R_i rows per thread, at most T_i threads
 // per CTA so that registers x threads <= 64K); included once per dtype
 // translation unit.  KernelCfg::tile selects the tile.
 #pragma once
@@ -42,6 +42,7 @@ cudaError_t TSQR_LOCAL_QR_NAME(const KernelCfg& k, const void* A, int64_t m, int
     case 1: return local_qr_R<TSQR_R1, TSQR_T1>(k, a, m, n, b, p, y, Rst, Tst, status, st);
     case 2: return local_qr_R<TSQR_R2, TSQR_T2>(k, a, m, n, b, p, y, Rst, Tst, status, st);
     case 3: return local_qr_R<TSQR_R3, TSQR_T3>(k, a, m, n, b, p, y, Rst, Tst, status, st);
+    case 4: return local_qr_R<TSQR_R4, TSQR_T4>(k, a, m, n, b, p, y, Rst, Tst, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -56,10 +57,12 @@ cudaError_t TSQR_FORM_Q_NAME(const KernelCfg& k, const void* Y, int64_t m, int n
     case 1: return form_q_R<TSQR_R1, TSQR_T1>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
     case 2: return form_q_R<TSQR_R2, TSQR_T2>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
     case 3: return form_q_R<TSQR_R3, TSQR_T3>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
+    case 4: return form_q_R<TSQR_R4, TSQR_T4>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
+#ifdef TSQR_ROWMUL_NAME
 template <int R, int MAXT>
 static cudaError_t rowmul_R(const KernelCfg& k, const TSQR_S* X, const double* M1, const TSQR_S* Y,
                             const double* M2, int64_t m, int n, int64_t b, int64_t p, TSQR_S* out,
@@ -84,6 +87,7 @@ cudaError_t TSQR_ROWMUL_NAME(const KernelCfg& k, const void* X, const double* M1
     case 1: return rowmul_R<TSQR_R1, TSQR_T1>(k, x, M1, y, M2, m, n, b, p, o, status, st);
     case 2: return rowmul_R<TSQR_R2, TSQR_T2>(k, x, M1, y, M2, m, n, b, p, o, status, st);
     case 3: return rowmul_R<TSQR_R3, TSQR_T3>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 4: return rowmul_R<TSQR_R4, TSQR_T4>(k, x, M1, y, M2, m, n, b, p, o, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -98,5 +102,7 @@ cudaError_t TSQR_GRAM_NAME(const void* X, const void* Y, int64_t m, int n, int c
                              status);
   return cudaGetLastError();
 }
+
+#endif  // TSQR_ROWMUL_NAME
 
 }  // namespace tsqr

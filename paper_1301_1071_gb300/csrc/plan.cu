@@ -11,12 +11,21 @@ namespace tsqr {
 
 static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 
-// Register-tile heights and their thread bounds (must match kern_f64.cu /
-// kern_f32.cu): registers x threads stay within the 64K register file.
-struct TileChoice { int R, maxt; };
-constexpr int kNumTiles = 4;
-static const TileChoice kTiles64[kNumTiles] = {{12, 320}, {8, 448}, {4, 640}, {8, 640}};
-static const TileChoice kTiles32[kNumTiles] = {{24, 320}, {16, 448}, {8, 640}, {16, 640}};
+// Register-tile heights and their thread bounds (must match kern_f64.cu,
+// kern_df64.cu and kern_f32.cu).  Each SM sub-partition holds 16K registers
+// and a CTA of MAXT threads puts ceil(MAXT/128) warps on each, so the
+// per-thread limit is 255 / 168 / 128 / 96 registers at MAXT = 256 / 384 /
+// 512 / 640; R x 5 values (x2 registers for 8-byte and double-float values)
+// leave about 60 registers for the rest of the kernel, with no spills.
+// The last tile exceeds that budget (its registers spill); it is taken only
+// when no other tile holds the rows asked for (binary64 tree nodes of two
+// R factors at n > 64).
+struct TileChoice { int R, maxt; bool spills; };
+constexpr int kNumTiles = 5;
+static const TileChoice kTiles64[kNumTiles] = {
+    {16, 256, false}, {10, 384, false}, {6, 512, false}, {4, 640, false}, {8, 640, true}};
+static const TileChoice kTiles32[kNumTiles] = {
+    {32, 256, false}, {20, 384, false}, {12, 512, false}, {8, 640, false}, {16, 640, true}};
 
 // Picks the register tile and row-group count.  want_b > 0: the smallest
 // capacity B >= want_b (ties: the taller register tile); want_b == 0: the
@@ -29,7 +38,9 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
   const TileChoice* tiles = kind == kKindF32 ? kTiles32 : kTiles64;
   KernelCfg best;
   best.kind = kind;
+  for (int pass = 0; pass < 2 && best.B == 0; ++pass)  // pass 1 admits the spilling tile
   for (int ti = 0; ti < kNumTiles; ++ti) {
+    if (tiles[ti].spills != (pass == 1)) continue;
     const int R = tiles[ti].R;
     for (int NRG = tiles[ti].maxt / (32 * CS); NRG >= 1; --NRG) {
       const int B = 32 * NRG * R;
@@ -50,12 +61,9 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
       } else if (policy == kPolicyLargest) {
         take = B > best.B;  // largest row block wins; ties keep the earlier tile
       } else {
-        // Step 1: the tallest register tile within 320 threads (>= 168
-        // registers per thread, no forced spills), then the largest block;
-        // wider CTAs only when n needs them
-        const bool narrow = NT <= 320, best_narrow = best.NT > 0 && best.NT <= 320;
-        take = best.B == 0 || (narrow && !best_narrow) ||
-               (narrow == best_narrow && (R > best.R || (R == best.R && B > best.B)));
+        // Step 1: the largest block (the fixed per-column cost of the
+        // Householder loop is spread over more rows); ties: fewer threads
+        take = best.B == 0 || B > best.B || (B == best.B && NT < best.NT);
       }
       if (take) {
         best.npc = kNpc; best.R = R; best.CS = CS; best.NRG = NRG; best.NT = NT; best.B = B;

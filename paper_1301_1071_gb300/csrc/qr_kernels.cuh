@@ -149,22 +149,32 @@ __device__ __forceinline__ T shfl_bcast(T v) {
 
 // Trailing update of the thread's tile for column j, with the first trailing
 // local column C0 known at compile time: a[q][c] -= d[c] x_q for c >= C0.
-// The warp owning column j (local index C0 - 1) stores v_j = x scal below the
-// pivot; the warp owning column j + 1 (local index C0) publishes it.
+// The thread's rows are rbase + 32 q (q < R); the published pivot column x_j
+// is zero above row j, so the update needs no row test.  The warp owning
+// column j (local index C0 - 1) stores v_j = x scal below the pivot; the warp
+// owning column j + 1 (local index C0) publishes it, zeroed above row j + 1.
 template <int C0, int NPC, int R, class T>
 __device__ __forceinline__ void tile_update(T (&a)[R][NPC], const T (&d)[NPC], const T* xcur, T* xnext, int j,
-                                            int rbase, int RS, bool own_j, bool own_next, T scal) {
+                                            int rbase, bool own_j, bool own_next, T scal) {
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int r = rbase + q * RS;
-    const T xq = (r >= j) ? xcur[r] : T(0);
+    const T xq = xcur[rbase + 32 * q];
 #pragma unroll
     for (int c = C0; c < NPC; ++c) a[q][c] = fma(-d[c], xq, a[q][c]);
-    if constexpr (C0 >= 1) {
-      if (own_j) a[q][C0 - 1] = (r > j) ? xq * scal : a[q][C0 - 1];
+  }
+  if constexpr (C0 >= 1) {
+    if (own_j) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int r = rbase + 32 * q;
+        if (r > j) a[q][C0 - 1] = xcur[r] * scal;
+      }
     }
-    if constexpr (C0 < NPC) {
-      if (own_next) xnext[r] = a[q][C0];
+  }
+  if constexpr (C0 < NPC) {
+    if (own_next) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) xnext[rbase + 32 * q] = (rbase + 32 * q > j) ? a[q][C0] : T(0);
     }
   }
 }
@@ -188,6 +198,8 @@ template <class S, class T, int NPC, int R, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, int64_t m, int n, int b, int CS, int NRG,
                            S* Y, double* __restrict__ Rst, double* __restrict__ Tst,
                            int32_t* status) {
+  static_assert(R >= 4, "rows < 128 must lie in row group 0");
+  constexpr int QH = 4;  // register rows that can hold rows < n (n <= 128)
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   const int NW = NT >> 5;
@@ -203,13 +215,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   T* xbuf = reinterpret_cast<T*>(smem + L.xcol);
   T* piv = reinterpret_cast<T*>(smem + L.piv);
   T* taus = reinterpret_cast<T*>(smem + L.tau);
+  T* refl = reinterpret_cast<T*>(smem + L.refl);  // beta, scal, 1/beta, tau, identity flag
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int cs = warp % CS, rg = warp / CS;
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * b;
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
-  const int RS = 32 * NRG;  // row stride between a thread's rows
+  // thread rows: row group rg holds rows [32 R rg, 32 R (rg + 1)); lane l of
+  // it holds rows 32 R rg + l + 32 q, so every row offset is a constant
+  const int rbase = rg * 32 * R + lane;
 
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -227,18 +242,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   int scale_exp = 0;
   if constexpr (std::is_same<T, df64>::value) {
     int emax = 0;
+    const S* rp = stage + rbase * n + cs;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      const int r = rg * 32 + lane + q * RS;
+      const int r = rbase + 32 * q;
 #pragma unroll
       for (int c = 0; c < NPC; ++c) {
         const int k = cs + c * CS;
         if (r < rows && k < n) {
           const int ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(
-                                              static_cast<double>(stage[r * n + k]))) >> 52) & 0x7ff);
+                                              static_cast<double>(rp[c * CS]))) >> 52) & 0x7ff);
           emax = ex != 0x7ff && ex > emax ? ex : emax;
         }
       }
+      rp += 32 * n;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -250,13 +267,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
     scale_exp = bm > 0 ? bm - 1022 : 0;  // max |a| * 2^-scale_exp < 1
   }
   T a[R][NPC];
+  {
+    // row pointer advanced by 32 rows per step: no per-row address registers
+    // (with R x NPC addresses live the register tile would spill)
+    const S* rp = stage + rbase * n + cs;
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int r = rg * 32 + lane + q * RS;
+    for (int q = 0; q < R; ++q) {
+      const int r = rbase + 32 * q;
 #pragma unroll
-    for (int c = 0; c < NPC; ++c) {
-      const int k = cs + c * CS;
-      a[q][c] = (r < rows && k < n) ? to_compute<T>(stage[r * n + k], scale_exp) : T(0);
+      for (int c = 0; c < NPC; ++c) {
+        const int k = cs + c * CS;
+        a[q][c] = (r < rows && k < n) ? to_compute<T>(rp[c * CS], scale_exp) : T(0);
+      }
+      rp += 32 * n;
     }
   }
   __syncthreads();  // stage is reused for the Gram matrix from here on
@@ -264,7 +287,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   // publish pivot column 0 and pivot row 0
   if (cs == 0) {
 #pragma unroll
-    for (int q = 0; q < R; ++q) xbuf[rg * 32 + lane + q * RS] = a[q][0];
+    for (int q = 0; q < R; ++q) xbuf[rbase + 32 * q] = a[q][0];
   }
   if (rg == 0 && lane == 0) {
 #pragma unroll
@@ -272,7 +295,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   }
   __syncthreads();
 
-  const int rbase = rg * 32 + lane;
   for (int j = 0; j < n; ++j) {
     const int jb = j & 1;
     const T* xcur = xbuf + jb * B;          // x_j (column j, current values)
@@ -288,8 +310,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         df64_acc acc[NPC];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          const int r = rbase + q * RS;
-          const T xq = (r >= j) ? xcur[r] : T(0);
+          const T xq = xcur[rbase + 32 * q];  // zero above row j
 #pragma unroll
           for (int c = 0; c < NPC; ++c) acc[c].add_prod(xq, a[q][c]);
         }
@@ -300,8 +321,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         for (int c = 0; c < NPC; ++c) s[c] = T(0);
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-          const int r = rbase + q * RS;
-          const T xq = (r >= j) ? xcur[r] : T(0);
+          const T xq = xcur[rbase + 32 * q];  // zero above row j
 #pragma unroll
           for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
         }
@@ -310,41 +330,69 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
     }
     __syncthreads();
 
-    // ---- phase B (every warp): the reflector and this thread's update coefficients
-    Reflector<T> f;
-    if (lane == 0) {
-      T Sj = T(0);
-      for (int g = 0; g < NRG; ++g) Sj += rcur[(g * CS + j % CS) * 32 + j / CS];
-      f = make_reflector(Sj, pcur[j]);
+    // ---- phase B: lane c < NPC of every warp sums the partials of its column
+    //      c; warp 0 forms the reflector and publishes its scalars (producer
+    //      side of named barrier 1, the other warps wait on it), so the scalar
+    //      sequence runs once per CTA; then lane c forms R's r_jk = S_k / beta
+    //      (r_jj = beta) and d_c = (a_jk - r_jk) / (alpha - beta), which every
+    //      lane takes by shuffle
+    T Sc = T(0), pc = T(0);
+    const int mycol = cs + lane * CS;
+    if (lane < NPC && mycol < n) {
+      for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
+      pc = pcur[mycol];
     }
-    f.beta = shfl_bcast(f.beta);
-    f.scal = shfl_bcast(f.scal);
-    f.ib = shfl_bcast(f.ib);
-    f.tau = shfl_bcast(f.tau);
-    f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
+    Reflector<T> f;
     if (warp == 0) {
-      if (lane == 0) taus[j] = f.tau;
-      for (int kk = lane; kk < j; kk += 32) {  // Gram entries v_k^T v_j for T
+      if (lane == 0) {
+        T Sj = T(0);
+        for (int g = 0; g < NRG; ++g) Sj += rcur[(g * CS + j % CS) * 32 + j / CS];
+        f = make_reflector(Sj, pcur[j]);
+        refl[0] = f.beta;
+        refl[1] = f.scal;
+        refl[2] = f.ib;
+        refl[3] = f.tau;
+        refl[4] = f.ident ? T(1) : T(0);
+        taus[j] = f.tau;
+      }
+      __syncwarp();
+      named_bar_arrive(1, NT);
+      f.beta = shfl_bcast(f.beta);
+      f.scal = shfl_bcast(f.scal);
+      f.ib = shfl_bcast(f.ib);
+      f.tau = shfl_bcast(f.tau);
+      f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
+    } else {
+      named_bar_sync(1, NT);
+      f.beta = refl[0];
+      f.scal = refl[1];
+      f.ib = refl[2];
+      f.tau = refl[3];
+      f.ident = refl[4] != T(0);
+    }
+    if (warp == NW - 1) {  // Gram entries v_k^T v_j of the compact-WY T (off warp 0's path)
+      for (int kk = lane; kk < j; kk += 32) {
         T Sk = T(0);
         for (int g = 0; g < NRG; ++g) Sk += rcur[(g * CS + kk % CS) * 32 + kk / CS];
         gram[kk * n + j] = f.scal * (Sk - f.beta * pcur[kk]);
       }
     }
-    // update coefficients of this warp's columns: lane c forms column c's
-    // d_c = (a_jk - S_k / beta) / (alpha - beta), then all lanes take it
-    T d[NPC];
+    T d[NPC], rj[NPC];
     {
-      T dl = T(0);
+      T dl = T(0), rl = T(0);
       if (lane < NPC) {
-        const int col = cs + lane * CS;
-        if (col > j && col < n) {
-          T Sc = T(0);
-          for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
-          dl = (pcur[col] - Sc * f.ib) * f.scal;
+        if (mycol > j && mycol < n) {
+          rl = Sc * f.ib;
+          dl = (pc - rl) * f.scal;
+        } else if (mycol == j) {
+          rl = f.beta;
         }
       }
 #pragma unroll
-      for (int c = 0; c < NPC; ++c) d[c] = shfl_from(dl, c);
+      for (int c = 0; c < NPC; ++c) {
+        d[c] = shfl_from(dl, c);
+        rj[c] = shfl_from(rl, c);
+      }
     }
 
     // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
@@ -352,39 +400,31 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
     const bool own_j = (cs == j % CS);
     const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
     switch (c0) {
-      case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
-      case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
-      case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
-      case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
-      case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
-      default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, RS, own_j, own_next, f.scal); break;
+      case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+      case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+      case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+      case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+      case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+      default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
     }
-    // the thread holding row j (one per column slice) writes R's row j
-    if (!f.ident && (j - rbase) >= 0 && (j - rbase) % RS == 0) {
-      const int qj = (j - rbase) / RS;
+    // rows j and j+1 (< n <= 128) are register rows q < 4 of row group 0:
+    // the thread holding row j writes R's row j, the one holding row j+1
+    // publishes it (after this step's update)
+    if (!f.ident) {
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        if (q == qj) {
+      for (int q = 0; q < QH; ++q)
+        if (rbase + 32 * q == j) {
 #pragma unroll
           for (int c = 0; c < NPC; ++c) {
             const int col = cs + c * CS;
-            if (col > j && col < n) {
-              T Sc = T(0);
-              for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + c];
-              a[q][c] = Sc * f.ib;
-            } else if (col == j) {
-              a[q][c] = f.beta;
-            }
+            if (col >= j && col < n) a[q][c] = rj[c];
           }
         }
-      }
     }
-    // the thread holding row j+1 publishes it (after this step's update)
-    if (j + 1 < n && (j + 1 - rbase) >= 0 && (j + 1 - rbase) % RS == 0) {
-      const int qn = (j + 1 - rbase) / RS;
+    if (j + 1 < n) {
 #pragma unroll
-      for (int q = 0; q < R; ++q)
-        if (q == qn) {
+      for (int q = 0; q < QH; ++q)
+        if (rbase + 32 * q == j + 1) {
 #pragma unroll
           for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
         }
@@ -394,8 +434,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
 
   // ---- R_i (raw signs) for rows < n
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int r = rg * 32 + lane + q * RS;
+  for (int q = 0; q < QH; ++q) {
+    const int r = rbase + 32 * q;
     if (r < n) {
 #pragma unroll
       for (int c = 0; c < NPC; ++c) {
@@ -427,7 +467,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   YS* ystage = reinterpret_cast<YS*>(stage);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int r = rg * 32 + lane + q * RS;
+    const int r = rbase + 32 * q;
     if (r < rows) {
 #pragma unroll
       for (int c = 0; c < NPC; ++c) {
@@ -467,8 +507,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
   const int cs = warp % CS, rg = warp / CS;
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * b;
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
-  const int RS = 32 * NRG;
+  const int rbase = rg * 32 * R + lane;  // thread rows rbase + 32 q, as in k_local_qr
   const int ntop = rows < n ? rows : n;
+  (void)NRG;
   using YS = YStore<S, T>;
   const YS* Yb = reinterpret_cast<const YS*>(Yg) + row0 * n;
   YS* ystage = reinterpret_cast<YS*>(stage);
@@ -514,7 +555,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
     T acc[R][NPC];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      const int r = c0 + rg * 32 + lane + q * RS;  // row within the block
+      const int r = c0 + rbase + 32 * q;  // row within the block
 #pragma unroll
       for (int c = 0; c < NPC; ++c) {
         const int k = cs + c * CS;
@@ -527,7 +568,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
       for (int c = 0; c < NPC; ++c) w[c] = Wm[k * NPAD + cs + c * CS];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int rl = rg * 32 + lane + q * RS;  // row within the chunk
+        const int rl = rbase + 32 * q;  // row within the chunk
         const int r = c0 + rl;
         T y = T(0);
         if (rl < crows) y = (k < r) ? static_cast<T>(ystage[rl * n + k]) : (k == r ? T(1) : T(0));
@@ -538,7 +579,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
     __syncthreads();  // every read of this chunk in shared memory is done
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      const int rl = rg * 32 + lane + q * RS;
+      const int rl = rbase + 32 * q;
       if (rl < crows) {
 #pragma unroll
         for (int c = 0; c < NPC; ++c) {

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(MAXT, 1)
   const int cs = warp % CS, rg = warp / CS;
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * b;
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
-  const int RS = 32 * NRG;
+  const int rbase = rg * 32 * R + lane;  // thread rows rbase + 32 q, as in k_local_qr
+  (void)NRG;
 
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -163,10 +164,12 @@ __global__ void __launch_bounds__(MAXT, 1)
       T w[NPC];
 #pragma unroll
       for (int c = 0; c < NPC; ++c) w[c] = m1[k * NPAD + cs + c * CS];
+      const S* xp = sx + rbase * n + k;  // advanced by 32 rows per step
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int r = rg * 32 + lane + q * RS;
-        const T xv = (r < rows) ? static_cast<T>(sx[r * n + k]) : T(0);
+        const int r = rbase + 32 * q;
+        const T xv = (r < rows) ? static_cast<T>(*xp) : T(0);
+        xp += 32 * n;
 #pragma unroll
         for (int c = 0; c < NPC; ++c) acc[q][c] = fma(xv, w[c], acc[q][c]);
       }
@@ -175,10 +178,12 @@ __global__ void __launch_bounds__(MAXT, 1)
       T w[NPC];
 #pragma unroll
       for (int c = 0; c < NPC; ++c) w[c] = m2[k * NPAD + cs + c * CS];
+      const S* yp = ys + rbase * n + k;
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int r = rg * 32 + lane + q * RS;
-        const T yv = (r < rows) ? static_cast<T>(ys[r * n + k]) : T(0);
+        const int r = rbase + 32 * q;
+        const T yv = (r < rows) ? static_cast<T>(*yp) : T(0);
+        yp += 32 * n;
 #pragma unroll
         for (int c = 0; c < NPC; ++c) acc[q][c] = fma(yv, w[c], acc[q][c]);
       }
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(MAXT, 1)
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < R; ++q) {
-    const int r = rg * 32 + lane + q * RS;
+    const int r = rbase + 32 * q;
     if (r < rows) {
 #pragma unroll
       for (int c = 0; c < NPC; ++c) {
