@@ -11,18 +11,18 @@
 
 namespace tsqr {
 
-cudaError_t launch_local_qr_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, void*, double*,
+cudaError_t launch_local_qr_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, void*, double*,
                                 double*, int32_t*, cudaStream_t);
-cudaError_t launch_local_qr_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, void*, double*,
+cudaError_t launch_local_qr_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, void*, double*,
                                 double*, int32_t*, cudaStream_t);
-cudaError_t launch_form_q_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, const double*,
+cudaError_t launch_form_q_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, const double*,
                               const double*, int64_t, void*, int32_t*, cudaStream_t);
-cudaError_t launch_form_q_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, const double*,
+cudaError_t launch_form_q_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, const double*,
                               const double*, int64_t, void*, int32_t*, cudaStream_t);
 
-cudaError_t launch_local_qr_df64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, void*, double*,
+cudaError_t launch_local_qr_df64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, void*, double*,
                                  double*, int32_t*, cudaStream_t);
-cudaError_t launch_form_q_df64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, const double*,
+cudaError_t launch_form_q_df64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, const double*,
                                const double*, int64_t, void*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f64(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
@@ -47,23 +47,23 @@ cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n,
   return launch_gram_reduce(part, g.grid, n, G, status, st);
 }
 
-cudaError_t launch_local_qr(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t p, void* Y,
-                            double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+cudaError_t launch_local_qr(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                            int64_t p, void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
   switch (k.kind) {
-    case kKindF64: return launch_local_qr_f64(k, A, m, n, b, p, Y, Rst, Tst, status, st);
-    case kKindF32: return launch_local_qr_f32(k, A, m, n, b, p, Y, Rst, Tst, status, st);
-    case kKindDF64: return launch_local_qr_df64(k, A, m, n, b, p, Y, Rst, Tst, status, st);
+    case kKindF64: return launch_local_qr_f64(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
+    case kKindF32: return launch_local_qr_f32(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
+    case kKindDF64: return launch_local_qr_df64(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t p,
-                          const double* T, const double* C, int64_t cblocks, void* Q, int32_t* status,
+cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                          int64_t p, const double* T, const double* C, int64_t cblocks, void* Q, int32_t* status,
                           cudaStream_t st) {
   switch (k.kind) {
-    case kKindF64: return launch_form_q_f64(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
-    case kKindF32: return launch_form_q_f32(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
-    case kKindDF64: return launch_form_q_df64(k, Y, m, n, b, p, T, C, cblocks, Q, status, st);
+    case kKindF64: return launch_form_q_f64(k, Y, m, n, b, bt, kt, p, T, C, cblocks, Q, status, st);
+    case kKindF32: return launch_form_q_f32(k, Y, m, n, b, bt, kt, p, T, C, cblocks, Q, status, st);
+    case kKindDF64: return launch_form_q_df64(k, Y, m, n, b, bt, kt, p, T, C, cblocks, Q, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -131,17 +131,17 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   // Step 1: local QR of every row block; Y_0 is written into Q's storage.
   const Level& l0 = P.levels[0];
   if (mark(o, 0, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  if (launch_local_qr(P.cfg0, A, P.m, n, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
+  if (launch_local_qr(P.cfg0, A, P.m, n, l0.b, l0.bt, l0.kt, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  if (launch_build_t(T(0), l0.p, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  if (launch_build_t(T(0), l0.p * l0.kt, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
   // Step 2 (Alg. 2): the stack of level l-1 is the tall input of level l.
   for (size_t l = 1; l < L; ++l) {
     const Level& lv = P.levels[l];
-    if (launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, S(l - 1), S(l), T(l), status, st) !=
-        cudaSuccess)
-      return TSQR_ERR_CUDA;
-    if (launch_build_t(T(l), lv.p, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
+    const cudaError_t e =
+        launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, S(l - 1), S(l), T(l), status, st);
+    if (e != cudaSuccess) return TSQR_ERR_CUDA;
+    if (launch_build_t(T(l), lv.p * lv.kt, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
   }
   if (launch_sign_fix(S(L - 1), n, R, ldr, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
   if (extra(ctop) != TSQR_OK) return TSQR_ERR_CUDA;
@@ -150,15 +150,15 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
     const Level& lv = P.levels[l];
     const double* C = (l == L - 1) ? ctop : S(l);
     const int64_t cb = (l == L - 1) ? 1 : lv.p;
-    if (launch_form_q(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, T(l), C, cb, S(l - 1), status, st) !=
-        cudaSuccess)
-      return TSQR_ERR_CUDA;
+    const cudaError_t e =
+        launch_form_q(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, T(l), C, cb, S(l - 1), status, st);
+    if (e != cudaSuccess) return TSQR_ERR_CUDA;
   }
   // Step 3: Q_i = Q1_i Q2_i over the Y_i held in Q.
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
   const double* C0 = (L == 1) ? ctop : S(0);
   const int64_t cb0 = (L == 1) ? 1 : l0.p;
-  if (launch_form_q(P.cfg0, Q, P.m, n, l0.b, l0.p, T(0), C0, cb0, Q, status, st) != cudaSuccess)
+  if (launch_form_q(P.cfg0, Q, P.m, n, l0.b, l0.bt, l0.kt, l0.p, T(0), C0, cb0, Q, status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   return mark(o, 3, st);
 }
@@ -173,13 +173,14 @@ tsqr_status run_r_only(const Plan& P, int esz, const void* X, double* R, void* w
   auto S = [&](size_t l) { return reinterpret_cast<double*>(at(work, P.levels[l].off_S)); };
   double* ctop = reinterpret_cast<double*>(at(work, P.off_ctop));
   const Level& l0 = P.levels[0];
-  if (launch_local_qr(P.cfg0, X, P.m, n, l0.b, l0.p, nullptr, S(0), nullptr, status, st) != cudaSuccess)
-    return TSQR_ERR_CUDA;
+  const cudaError_t e0 =
+      launch_local_qr(P.cfg0, X, P.m, n, l0.b, l0.bt, l0.kt, l0.p, nullptr, S(0), nullptr, status, st);
+  if (e0 != cudaSuccess) return TSQR_ERR_CUDA;
   for (size_t l = 1; l < L; ++l) {
     const Level& lv = P.levels[l];
-    if (launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.p, nullptr, S(l), nullptr, status, st) !=
-        cudaSuccess)
-      return TSQR_ERR_CUDA;
+    const cudaError_t e =
+        launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, nullptr, S(l), nullptr, status, st);
+    if (e != cudaSuccess) return TSQR_ERR_CUDA;
   }
   if (launch_sign_fix(S(L - 1), n, R, n, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
   return TSQR_OK;

@@ -154,14 +154,6 @@ __device__ __forceinline__ T shfl_xor(T v, int o) {
   return __shfl_xor_sync(0xffffffffu, v, o);
 }
 
-// Warp transpose-reduce.  On entry every lane holds s[0..V); on exit the sum
-// over all 32 lanes of index i is written to dst[i] for every i < V by the
-// lanes that own it (several lanes may write the same, identical value).
-// Each halving step exchanges half of the remaining values with the partner
-// lane; once one value is left the remaining offsets are plain butterflies.
-// `limit` is the exclusive end of the indices owned by the current subtree:
-// the padding slot of an odd-length half must not be written, because its
-// index belongs to the sibling subtree.
 // Named CTA barrier `id` (1..15; 0 is __syncthreads) over `nthreads`
 // threads (a multiple of 32): producers arrive without waiting, consumers
 // wait until all `nthreads` have arrived.  Writes made by a producer before
@@ -173,6 +165,14 @@ __device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Warp transpose-reduce.  On entry every lane holds s[0..V); on exit the sum
+// over all 32 lanes of index i is written to dst[i] for every i < V by the
+// lanes that own it (several lanes may write the same, identical value).
+// Each halving step exchanges half of the remaining values with the partner
+// lane; once one value is left the remaining offsets are plain butterflies.
+// `limit` is the exclusive end of the indices owned by the current subtree:
+// the padding slot of an odd-length half must not be written, because its
+// index belongs to the sibling subtree.
 template <int V, int O>
 struct TransposeReduce {
   template <class T>

@@ -11,53 +11,54 @@
 namespace tsqr {
 
 template <int R, int MAXT>
-static cudaError_t local_qr_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t p,
-                              TSQR_S* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+static cudaError_t local_qr_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                              int64_t p, TSQR_S* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
   if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
   auto fn = k_local_qr<TSQR_S, TSQR_T, kNpc, R, MAXT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_qr);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)p, k.NT, k.smem_qr, st>>>(A, m, n, (int)b, k.CS, k.NRG, Y, Rst, Tst, status);
+  fn<<<(unsigned)p, k.NT, k.smem_qr, st>>>(A, m, n, (int)b, (int)bt, kt, k.CS, k.NRG, Y, Rst, Tst, status);
   return cudaGetLastError();
 }
 
 template <int R, int MAXT>
-static cudaError_t form_q_R(const KernelCfg& k, const TSQR_S* Y, int64_t m, int n, int64_t b, int64_t p,
-                            const double* T, const double* C, int64_t cblocks, TSQR_S* Q, int32_t* status,
-                            cudaStream_t st) {
+static cudaError_t form_q_R(const KernelCfg& k, const TSQR_S* Y, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                            int64_t p, const double* T, const double* C, int64_t cblocks, TSQR_S* Q,
+                            int32_t* status, cudaStream_t st) {
   if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
   auto fn = k_form_q<TSQR_S, TSQR_T, kNpc, R, MAXT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fq);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)p, k.NT, k.smem_fq, st>>>(Y, m, n, (int)b, k.fq_rows, k.CS, k.NRG, T, C, cblocks, Q, status);
+  fn<<<(unsigned)p, k.NT, k.smem_fq, st>>>(Y, m, n, (int)b, (int)bt, kt, k.fq_rows, k.CS, k.NRG, T, C, cblocks, Q,
+                                           status);
   return cudaGetLastError();
 }
 
-cudaError_t TSQR_LOCAL_QR_NAME(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t p,
-                               void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+cudaError_t TSQR_LOCAL_QR_NAME(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                               int64_t p, void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
   const TSQR_S* a = static_cast<const TSQR_S*>(A);
   TSQR_S* y = static_cast<TSQR_S*>(Y);
   switch (k.tile) {
-    case 0: return local_qr_R<TSQR_R0, TSQR_T0>(k, a, m, n, b, p, y, Rst, Tst, status, st);
-    case 1: return local_qr_R<TSQR_R1, TSQR_T1>(k, a, m, n, b, p, y, Rst, Tst, status, st);
-    case 2: return local_qr_R<TSQR_R2, TSQR_T2>(k, a, m, n, b, p, y, Rst, Tst, status, st);
-    case 3: return local_qr_R<TSQR_R3, TSQR_T3>(k, a, m, n, b, p, y, Rst, Tst, status, st);
-    case 4: return local_qr_R<TSQR_R4, TSQR_T4>(k, a, m, n, b, p, y, Rst, Tst, status, st);
+    case 0: return local_qr_R<TSQR_R0, TSQR_T0>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 1: return local_qr_R<TSQR_R1, TSQR_T1>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 2: return local_qr_R<TSQR_R2, TSQR_T2>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 3: return local_qr_R<TSQR_R3, TSQR_T3>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 4: return local_qr_R<TSQR_R4, TSQR_T4>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t TSQR_FORM_Q_NAME(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t p,
-                             const double* T, const double* C, int64_t cblocks, void* Q, int32_t* status,
-                             cudaStream_t st) {
+cudaError_t TSQR_FORM_Q_NAME(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                             int64_t p, const double* T, const double* C, int64_t cblocks, void* Q,
+                             int32_t* status, cudaStream_t st) {
   const TSQR_S* y = static_cast<const TSQR_S*>(Y);
   TSQR_S* q = static_cast<TSQR_S*>(Q);
   switch (k.tile) {
-    case 0: return form_q_R<TSQR_R0, TSQR_T0>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
-    case 1: return form_q_R<TSQR_R1, TSQR_T1>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
-    case 2: return form_q_R<TSQR_R2, TSQR_T2>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
-    case 3: return form_q_R<TSQR_R3, TSQR_T3>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
-    case 4: return form_q_R<TSQR_R4, TSQR_T4>(k, y, m, n, b, p, T, C, cblocks, q, status, st);
+    case 0: return form_q_R<TSQR_R0, TSQR_T0>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 1: return form_q_R<TSQR_R1, TSQR_T1>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 2: return form_q_R<TSQR_R2, TSQR_T2>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 3: return form_q_R<TSQR_R3, TSQR_T3>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 4: return form_q_R<TSQR_R4, TSQR_T4>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -10,11 +10,13 @@ namespace tsqr {
 
 // Step 1 / tree level: p CTAs, one per row block of b rows (k.kind selects
 // the storage/compute types).
-cudaError_t launch_local_qr( const KernelCfg& k, const void* A, int64_t m, int n, int64_t b,
-                            int64_t p, void* Y, double* Rst, double* Tst, int32_t* status,
-                            cudaStream_t st);
+// Blocks of b rows; a block taller than the register tile (b > k.B) is
+// factored as tiles of k.B rows and then bt rows, kt tiles at most
+// (T slots per block).
+cudaError_t launch_local_qr(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                            int64_t p, void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st);
 // Step 3 / tree down-pass: p CTAs.
-cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b,
+cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t bt, int kt,
                           int64_t p, const double* T, const double* C, int64_t cblocks, void* Q,
                           int32_t* status, cudaStream_t st);
 

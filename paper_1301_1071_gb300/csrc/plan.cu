@@ -104,11 +104,32 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   P.n = n;
   P.esz = esz;
   const int kind0 = esz == 4 ? kKindF32 : (prec == TSQR_PREC_DF64 ? kKindDF64 : kKindF64);
-  if (!choose_cfg(kind0, (int)n, &P.cfg0, block_rows, kPolicyStep1) ||
+  // Step-1 tile: the largest register tile; a smaller one when the caller's
+  // blocks fit in it
+  if (!choose_cfg(kind0, (int)n, &P.cfg0, 0, kPolicyStep1) ||
       !choose_cfg(kKindF64, (int)n, &P.cfg64, 0, kPolicyStep1, 2 * (int)n))
     return TSQR_ERR_SHAPE;
-  int64_t b0 = block_rows > 0 ? block_rows : P.cfg0.B;
-  if (b0 < n || b0 > P.cfg0.B) return TSQR_ERR_SHAPE;
+  if (block_rows > 0 && block_rows <= P.cfg0.B && !choose_cfg(kind0, (int)n, &P.cfg0, block_rows, kPolicyStep1))
+    return TSQR_ERR_SHAPE;
+  const int64_t B0 = P.cfg0.B;
+  // rows per tile after the first: the register tile less the carried R,
+  // rounded down so that every tile starts on a 16-byte boundary when the
+  // block does (bulk copies)
+  int64_t al = 1;
+  while ((al * n * esz) % 16 != 0) ++al;
+  const int64_t bt = (B0 - n) / al * al;
+  if (bt < 1) return TSQR_ERR_SHAPE;
+  int64_t b0 = block_rows;
+  if (b0 <= 0) {
+    const int64_t want = m / kMinBlocks;
+    int64_t kt = want <= B0 ? 1 : 1 + (want - B0) / bt;
+    if (kt > kMaxTiles) kt = kMaxTiles;
+    b0 = B0 + (kt - 1) * bt;
+  }
+  if (b0 < n) return TSQR_ERR_SHAPE;
+  if (b0 > m) b0 = m;  // one block
+  const int64_t kt0 = b0 <= B0 ? 1 : 1 + (b0 - B0 + bt - 1) / bt;
+  if (kt0 > (1 << 20)) return TSQR_ERR_SHAPE;
   // tree node = f stacked R factors, f >= 2
   int64_t fmax = P.cfg64.B / n;
   int64_t f = fanout > 0 ? fanout : fmax;
@@ -118,12 +139,16 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   l0.rows = m;
   l0.b = b0;
   l0.p = (m + b0 - 1) / b0;
+  l0.bt = bt;
+  l0.kt = (int)kt0;
   P.levels.push_back(l0);
   while (P.levels.back().p > 1) {
     Level l;
     l.rows = P.levels.back().p * n;
     l.b = f * n;
     l.p = (l.rows + l.b - 1) / l.b;
+    l.bt = P.cfg64.B - n;  // tree nodes fit one tile (f n <= B)
+    l.kt = 1;
     P.levels.push_back(l);
   }
   size_t o = kHeaderBytes;
@@ -132,7 +157,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
     l.off_S = o;
     o = al16(o + (size_t)l.p * nn);
     l.off_T = o;
-    o = al16(o + (size_t)l.p * nn);
+    o = al16(o + (size_t)l.p * l.kt * nn);
   }
   P.off_ctop = o;
   o = al16(o + nn);

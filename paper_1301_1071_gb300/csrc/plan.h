@@ -31,9 +31,10 @@ struct KernelCfg {
   size_t smem_rm = 0;
 };
 
-// Default tile policies: kPolicyStep1 favours tall register tiles in narrow
-// CTAs (used for Step 1 and, with at least 2n rows so that a node merges two
-// or more R factors, for the tree); kPolicyLargest takes the largest block.
+// Default tile policies: kPolicyStep1 takes the largest spill-free register
+// tile (ties: fewer threads; used for Step 1 and, with at least 2n rows so
+// that a node merges two or more R factors, for the tree); kPolicyLargest
+// takes the largest block.
 enum { kPolicyStep1 = 0, kPolicyLargest = 1 };
 
 // Picks the register tile of kernel kind `kind` for n (want_b > 0: the
@@ -44,8 +45,13 @@ struct Level {
   int64_t rows = 0;  // rows of this level's input matrix
   int64_t b = 0;     // rows per block
   int64_t p = 0;     // number of blocks
+  // a block taller than the register tile (b > B) is factored as a flat
+  // tree of tiles inside one CTA: B rows, then bt rows per tile, kt tiles at
+  // most (kt T slots per block)
+  int64_t bt = 0;
+  int kt = 1;
   size_t off_S = 0;  // byte offset of the p blocks of R (n x n, binary64)
-  size_t off_T = 0;  // byte offset of the p blocks of T (n x n, binary64)
+  size_t off_T = 0;  // byte offset of the p kt T slots (n x n, binary64)
 };
 
 struct Plan {
@@ -63,12 +69,19 @@ struct Plan {
 };
 
 constexpr int kSmallSlots = 8;  // n x n binary64 matrices in each small scratch area
+// Default Step-1 block height: enough tiles per block that the stack of R
+// factors (and so the Step-2 tree) stays small, while keeping at least
+// kMinBlocks blocks (4 per SM on a 152-SM GB300) and at most kMaxTiles tiles.
+constexpr int64_t kMinBlocks = 608;
+constexpr int kMaxTiles = 64;
 constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM of a GB300)
 
 // Workspace bytes of `op` (tsqr_op) under a built plan.
 size_t op_bytes(const Plan& P, int op);
 
-// Builds the plan; returns 0 or a tsqr_status code.
+// Builds the plan; returns 0 or a tsqr_status code.  block_rows > 0 fixes
+// the Step-1 block height (any value >= n; above the register tile's B rows
+// the block is factored tile by tile); 0 chooses it.
 int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec = 0);
 
 }  // namespace tsqr

@@ -187,17 +187,25 @@ using YStore = typename std::conditional<std::is_same<T, df64>::value, df64, S>:
 // ---------------------------------------------------------------------------
 // Step 1: local Householder QR of one row block per CTA.
 //   A    : m x n row-major (storage S); block i = rows [i*b, min(i*b+b, m)).
-//   Y    : output, same shape; may alias A (the block is staged first).  NULL
+//   Y    : output, same shape; may alias A (each tile is staged first).  NULL
 //          = R-only mode (no Y, no T).
 //   Rst  : p blocks of n x n binary64 (R_i, upper triangular, raw signs).
-//   Tst  : p blocks of n x n binary64 receiving tau_j on the diagonal and the
-//          Gram entries v_i^T v_j above it (k_build_t then forms T_i), or NULL.
+//   Tst  : kt slots of n x n binary64 per block (slot i*kt + t for tile t)
+//          receiving tau_j on the diagonal and the Gram entries v_i^T v_j
+//          above it (k_build_t then forms T), or NULL.
+// A block taller than the register tile (b > B rows) is factored as a flat
+// tree inside the CTA (the sequential reduction order of Sec. II-B / Alg. 2
+// with one R carried along): tile 0 is the block's first B rows; tile t >= 1
+// stacks the running R on the next bt rows and factors [R; A_t] =
+// Q_t [R'; 0].  The rows of R below its diagonal are zero and stay exactly
+// zero, so the Householder vectors of tile t are [I; V_t] and only V_t is
+// stored (over A_t's rows of Y).
 // Launch: blockDim = 32*CS*NRG <= MAXT, gridDim = p, dynamic smem = LocalQrSmem.
 // ---------------------------------------------------------------------------
 template <class S, class T, int NPC, int R, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, int64_t m, int n, int b, int CS, int NRG,
-                           S* Y, double* __restrict__ Rst, double* __restrict__ Tst,
-                           int32_t* status) {
+__global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, int64_t m, int n, int b, int bt,
+                                                       int kt, int CS, int NRG, S* Y, double* __restrict__ Rst,
+                                                       double* __restrict__ Tst, int32_t* status) {
   static_assert(R >= 4, "rows < 128 must lie in row group 0");
   constexpr int QH = 4;  // register rows that can hold rows < n (n <= 128)
   extern __shared__ __align__(128) unsigned char smem[];
@@ -222,6 +230,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   const int cs = warp % CS, rg = warp / CS;
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * b;
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
+  const int ntiles = rows <= B ? 1 : 1 + (rows - B + bt - 1) / bt;
   // thread rows: row group rg holds rows [32 R rg, 32 R (rg + 1)); lane l of
   // it holds rows 32 R rg + l + 32 q, so every row offset is a constant
   const int rbase = rg * 32 * R + lane;
@@ -232,205 +241,265 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   }
   __syncthreads();
   uint32_t parity = 0;
-  if (!cta_load_bulk(stage, A + row0 * n, static_cast<int64_t>(rows) * n, bar, parity, status)) return;
-  __syncthreads();
-
-  // Double-float compute: scale the block by a power of two (exact) chosen
-  // from the largest binary64 exponent, so that its entries are below 1 and
-  // products of small entries stay in binary32 range.  Y and T are invariant
-  // under the scaling; R is unscaled on output.
   int scale_exp = 0;
-  if constexpr (std::is_same<T, df64>::value) {
-    int emax = 0;
-    const S* rp = stage + rbase * n + cs;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int r = rbase + 32 * q;
-#pragma unroll
-      for (int c = 0; c < NPC; ++c) {
-        const int k = cs + c * CS;
-        if (r < rows && k < n) {
-          const int ex = static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(
-                                              static_cast<double>(rp[c * CS]))) >> 52) & 0x7ff);
-          emax = ex != 0x7ff && ex > emax ? ex : emax;
-        }
-      }
-      rp += 32 * n;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    int* wmax = reinterpret_cast<int*>(red);
-    if (lane == 0) wmax[warp] = emax;
-    __syncthreads();
-    int bm = 0;
-    for (int w = 0; w < NW; ++w) bm = max(bm, wmax[w]);
-    scale_exp = bm > 0 ? bm - 1022 : 0;  // max |a| * 2^-scale_exp < 1
-  }
   T a[R][NPC];
-  {
-    // row pointer advanced by 32 rows per step: no per-row address registers
-    // (with R x NPC addresses live the register tile would spill)
-    const S* rp = stage + rbase * n + cs;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int r = rbase + 32 * q;
-#pragma unroll
-      for (int c = 0; c < NPC; ++c) {
-        const int k = cs + c * CS;
-        a[q][c] = (r < rows && k < n) ? to_compute<T>(rp[c * CS], scale_exp) : T(0);
+  for (int t = 0; t < ntiles; ++t) {
+    // tile t: data rows [tr0, tr0 + cnt) of the block in register rows
+    // [off, off + cnt); register rows < off hold the running R
+    const int tr0 = t == 0 ? 0 : B + (t - 1) * bt;
+    const int cnt = t == 0 ? (rows < B ? rows : B) : (rows - tr0 < bt ? rows - tr0 : bt);
+    const int off = t == 0 ? 0 : n;
+    if (!cta_load_bulk(stage, A + (row0 + tr0) * n, static_cast<int64_t>(cnt) * n, bar, parity, status)) return;
+
+    // Double-float compute: scale the data by a power of two (exact) chosen
+    // from the largest binary64 exponent seen so far in the block, so that
+    // entries are below 1 and products of small entries stay in binary32
+    // range; when a tile raises it, the running R is rescaled (exact).  Y and
+    // T are invariant under the scaling; R is unscaled on output.
+    if constexpr (std::is_same<T, df64>::value) {
+      int emax = 0;
+      for (int idx = tid; idx < cnt * n; idx += NT) {
+        const int ex = static_cast<int>(
+            (static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(stage[idx]))) >> 52) & 0x7ff);
+        emax = ex != 0x7ff && ex > emax ? ex : emax;
       }
-      rp += 32 * n;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      int* wmax = reinterpret_cast<int*>(red);
+      if (lane == 0) wmax[warp] = emax;
+      __syncthreads();
+      int bm = 0;
+      for (int w = 0; w < NW; ++w) bm = max(bm, wmax[w]);
+      const int se = bm > 0 ? bm - 1022 : 0;  // max |a| * 2^-se < 1
+      if (t == 0) {
+        scale_exp = se;
+      } else if (se > scale_exp) {
+#pragma unroll
+        for (int q = 0; q < QH; ++q)
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) a[q][c] = scale2(a[q][c], scale_exp - se);
+        scale_exp = se;
+      }
+      __syncthreads();  // wmax (in the partial-sum buffer) is read by all
     }
-  }
-  __syncthreads();  // stage is reused for the Gram matrix from here on
-
-  // publish pivot column 0 and pivot row 0
-  if (cs == 0) {
-#pragma unroll
-    for (int q = 0; q < R; ++q) xbuf[rbase + 32 * q] = a[q][0];
-  }
-  if (rg == 0 && lane == 0) {
-#pragma unroll
-    for (int c = 0; c < NPC; ++c) piv[cs + c * CS] = a[0][c];
-  }
-  __syncthreads();
-
-  for (int j = 0; j < n; ++j) {
-    const int jb = j & 1;
-    const T* xcur = xbuf + jb * B;          // x_j (column j, current values)
-    T* xnext = xbuf + (jb ^ 1) * B;         // x_{j+1}
-    const T* pcur = piv + jb * NPAD;        // row j
-    T* pnext = piv + (jb ^ 1) * NPAD;       // row j+1
-    T* rcur = red + jb * NW * 32;           // partial sums of this step
-
-    // ---- phase A: s = x_j^T A over the thread's rows (rows < j give 0), CTA partials
     {
-      T s[NPC];
-      if constexpr (std::is_same<T, df64>::value) {
-        df64_acc acc[NPC];
+      // row pointer advanced by 32 rows per step: no per-row address registers
+      // (with R x NPC addresses live the register tile would spill)
+      const S* rp = stage + (rbase - off) * n + cs;
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-          const T xq = xcur[rbase + 32 * q];  // zero above row j
-#pragma unroll
-          for (int c = 0; c < NPC; ++c) acc[c].add_prod(xq, a[q][c]);
-        }
-#pragma unroll
-        for (int c = 0; c < NPC; ++c) s[c] = acc[c].value();
-      } else {
-#pragma unroll
-        for (int c = 0; c < NPC; ++c) s[c] = T(0);
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-          const T xq = xcur[rbase + 32 * q];  // zero above row j
-#pragma unroll
-          for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
-        }
-      }
-      TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
-    }
-    __syncthreads();
-
-    // ---- phase B: lane c < NPC of every warp sums the partials of its column
-    //      c; warp 0 forms the reflector and publishes its scalars (producer
-    //      side of named barrier 1, the other warps wait on it), so the scalar
-    //      sequence runs once per CTA; then lane c forms R's r_jk = S_k / beta
-    //      (r_jj = beta) and d_c = (a_jk - r_jk) / (alpha - beta), which every
-    //      lane takes by shuffle
-    T Sc = T(0), pc = T(0);
-    const int mycol = cs + lane * CS;
-    if (lane < NPC && mycol < n) {
-      for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
-      pc = pcur[mycol];
-    }
-    Reflector<T> f;
-    if (warp == 0) {
-      if (lane == 0) {
-        T Sj = T(0);
-        for (int g = 0; g < NRG; ++g) Sj += rcur[(g * CS + j % CS) * 32 + j / CS];
-        f = make_reflector(Sj, pcur[j]);
-        refl[0] = f.beta;
-        refl[1] = f.scal;
-        refl[2] = f.ib;
-        refl[3] = f.tau;
-        refl[4] = f.ident ? T(1) : T(0);
-        taus[j] = f.tau;
-      }
-      __syncwarp();
-      named_bar_arrive(1, NT);
-      f.beta = shfl_bcast(f.beta);
-      f.scal = shfl_bcast(f.scal);
-      f.ib = shfl_bcast(f.ib);
-      f.tau = shfl_bcast(f.tau);
-      f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
-    } else {
-      named_bar_sync(1, NT);
-      f.beta = refl[0];
-      f.scal = refl[1];
-      f.ib = refl[2];
-      f.tau = refl[3];
-      f.ident = refl[4] != T(0);
-    }
-    if (warp == NW - 1) {  // Gram entries v_k^T v_j of the compact-WY T (off warp 0's path)
-      for (int kk = lane; kk < j; kk += 32) {
-        T Sk = T(0);
-        for (int g = 0; g < NRG; ++g) Sk += rcur[(g * CS + kk % CS) * 32 + kk / CS];
-        gram[kk * n + j] = f.scal * (Sk - f.beta * pcur[kk]);
-      }
-    }
-    T d[NPC], rj[NPC];
-    {
-      T dl = T(0), rl = T(0);
-      if (lane < NPC) {
-        if (mycol > j && mycol < n) {
-          rl = Sc * f.ib;
-          dl = (pc - rl) * f.scal;
-        } else if (mycol == j) {
-          rl = f.beta;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NPC; ++c) {
-        d[c] = shfl_from(dl, c);
-        rj[c] = shfl_from(rl, c);
-      }
-    }
-
-    // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
-    const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
-    const bool own_j = (cs == j % CS);
-    const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
-    switch (c0) {
-      case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-      case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-      case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-      case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-      case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-      default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-    }
-    // rows j and j+1 (< n <= 128) are register rows q < 4 of row group 0:
-    // the thread holding row j writes R's row j, the one holding row j+1
-    // publishes it (after this step's update)
-    if (!f.ident) {
-#pragma unroll
-      for (int q = 0; q < QH; ++q)
-        if (rbase + 32 * q == j) {
+      for (int q = 0; q < R; ++q) {
+        const int r = rbase + 32 * q - off;  // data row of the tile
+        if (q >= QH || t == 0 || r >= 0) {
 #pragma unroll
           for (int c = 0; c < NPC; ++c) {
-            const int col = cs + c * CS;
-            if (col >= j && col < n) a[q][c] = rj[c];
+            const int k = cs + c * CS;
+            a[q][c] = (r < cnt && k < n) ? to_compute<T>(rp[c * CS], scale_exp) : T(0);
           }
         }
+        rp += 32 * n;
+      }
     }
-    if (j + 1 < n) {
+    __syncthreads();  // stage is reused for the Gram matrix from here on
+
+    // publish pivot column 0 and pivot row 0
+    if (cs == 0) {
 #pragma unroll
-      for (int q = 0; q < QH; ++q)
-        if (rbase + 32 * q == j + 1) {
+      for (int q = 0; q < R; ++q) xbuf[rbase + 32 * q] = a[q][0];
+    }
+    if (rg == 0 && lane == 0) {
 #pragma unroll
-          for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
-        }
+      for (int c = 0; c < NPC; ++c) piv[cs + c * CS] = a[0][c];
     }
     __syncthreads();
-  }
+
+    for (int j = 0; j < n; ++j) {
+      const int jb = j & 1;
+      const T* xcur = xbuf + jb * B;          // x_j (column j, current values)
+      T* xnext = xbuf + (jb ^ 1) * B;         // x_{j+1}
+      const T* pcur = piv + jb * NPAD;        // row j
+      T* pnext = piv + (jb ^ 1) * NPAD;       // row j+1
+      T* rcur = red + jb * NW * 32;           // partial sums of this step
+
+      // ---- phase A: s = x_j^T A over the thread's rows (rows < j give 0), CTA partials
+      {
+        T s[NPC];
+        if constexpr (std::is_same<T, df64>::value) {
+          df64_acc acc[NPC];
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const T xq = xcur[rbase + 32 * q];  // zero above row j
+#pragma unroll
+            for (int c = 0; c < NPC; ++c) acc[c].add_prod(xq, a[q][c]);
+          }
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) s[c] = acc[c].value();
+        } else {
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) s[c] = T(0);
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            const T xq = xcur[rbase + 32 * q];  // zero above row j
+#pragma unroll
+            for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
+          }
+        }
+        TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
+      }
+      __syncthreads();
+
+      // ---- phase B: lane c < NPC of every warp sums the partials of its column
+      //      c; warp 0 forms the reflector and publishes its scalars (producer
+      //      side of named barrier 1, the other warps wait on it), so the scalar
+      //      sequence runs once per CTA; then lane c forms R's r_jk = S_k / beta
+      //      (r_jj = beta) and d_c = (a_jk - r_jk) / (alpha - beta), which every
+      //      lane takes by shuffle
+      T Sc = T(0), pc = T(0);
+      const int mycol = cs + lane * CS;
+      if (lane < NPC && mycol < n) {
+        for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
+        pc = pcur[mycol];
+      }
+      Reflector<T> f;
+      if (warp == 0) {
+        if (lane == 0) {
+          T Sj = T(0);
+          for (int g = 0; g < NRG; ++g) Sj += rcur[(g * CS + j % CS) * 32 + j / CS];
+          f = make_reflector(Sj, pcur[j]);
+          refl[0] = f.beta;
+          refl[1] = f.scal;
+          refl[2] = f.ib;
+          refl[3] = f.tau;
+          refl[4] = f.ident ? T(1) : T(0);
+          taus[j] = f.tau;
+        }
+        __syncwarp();
+        named_bar_arrive(1, NT);
+        f.beta = shfl_bcast(f.beta);
+        f.scal = shfl_bcast(f.scal);
+        f.ib = shfl_bcast(f.ib);
+        f.tau = shfl_bcast(f.tau);
+        f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
+      } else {
+        named_bar_sync(1, NT);
+        f.beta = refl[0];
+        f.scal = refl[1];
+        f.ib = refl[2];
+        f.tau = refl[3];
+        f.ident = refl[4] != T(0);
+      }
+      if (warp == NW - 1) {  // Gram entries v_k^T v_j of the compact-WY T (off warp 0's path)
+        for (int kk = lane; kk < j; kk += 32) {
+          T Sk = T(0);
+          for (int g = 0; g < NRG; ++g) Sk += rcur[(g * CS + kk % CS) * 32 + kk / CS];
+          gram[kk * n + j] = f.scal * (Sk - f.beta * pcur[kk]);
+        }
+      }
+      T d[NPC], rj[NPC];
+      {
+        T dl = T(0), rl = T(0);
+        if (lane < NPC) {
+          if (mycol > j && mycol < n) {
+            rl = Sc * f.ib;
+            dl = (pc - rl) * f.scal;
+          } else if (mycol == j) {
+            rl = f.beta;
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NPC; ++c) {
+          d[c] = shfl_from(dl, c);
+          rj[c] = shfl_from(rl, c);
+        }
+      }
+
+      // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
+      const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
+      const bool own_j = (cs == j % CS);
+      const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
+      switch (c0) {
+        case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+        case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+        case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+        case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+        case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+        default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+      }
+      // rows j and j+1 (< n <= 128) are register rows q < 4 of row group 0:
+      // the thread holding row j writes R's row j, the one holding row j+1
+      // publishes it (after this step's update)
+      if (!f.ident) {
+#pragma unroll
+        for (int q = 0; q < QH; ++q)
+          if (rbase + 32 * q == j) {
+#pragma unroll
+            for (int c = 0; c < NPC; ++c) {
+              const int col = cs + c * CS;
+              if (col >= j && col < n) a[q][c] = rj[c];
+            }
+          }
+      }
+      if (j + 1 < n) {
+#pragma unroll
+        for (int q = 0; q < QH; ++q)
+          if (rbase + 32 * q == j + 1) {
+#pragma unroll
+            for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
+          }
+      }
+      __syncthreads();
+    }
+
+    if (Y != nullptr) {
+      // ---- the Gram entries v_i^T v_j (i < j) and tau_j of the compact-WY
+      //      form, binary64, into the upper triangle of the tile's T slot (the
+      //      strictly lower part is never read); k_build_t turns them into T
+      {
+        double* Tout = Tst + (static_cast<int64_t>(blockIdx.x) * kt + t) * n * n;
+        for (int idx = tid; idx < n * n; idx += NT) {
+          const int i = idx / n, kk = idx % n;
+          if (kk >= i) Tout[idx] = static_cast<double>(kk > i ? gram[idx] : taus[i]);
+        }
+      }
+      __syncthreads();
+
+      // ---- the tile's rows of Y back through shared memory, bulk store
+      //      (compute format for df64)
+      using YS = YStore<S, T>;
+      YS* ystage = reinterpret_cast<YS*>(stage);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int r = rbase + 32 * q - off;
+        if (r >= 0 && r < cnt) {
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) {
+            const int k = cs + c * CS;
+            if (k < n) {
+              if constexpr (std::is_same<YS, T>::value) ystage[r * n + k] = a[q][c];
+              else ystage[r * n + k] = static_cast<YS>(a[q][c]);
+            }
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+      cta_store_bulk(reinterpret_cast<YS*>(Y) + (row0 + tr0) * n, ystage, static_cast<int64_t>(cnt) * n);
+    }
+    if (t + 1 < ntiles) {
+      // the running R for the next tile: clear what lies below its diagonal
+      // (tile 0's Y_top; later tiles leave exact zeros there)
+#pragma unroll
+      for (int q = 0; q < QH; ++q) {
+        const int r = rbase + 32 * q;
+#pragma unroll
+        for (int c = 0; c < NPC; ++c)
+          if (r < n && cs + c * CS < r) a[q][c] = T(0);
+      }
+      // the stage's generic-proxy writes (Gram, Y) are ordered before the next
+      // tile's bulk load, and the bulk store has read it (waited in the store)
+      fence_proxy_async_smem();
+      __syncthreads();
+    }
+  }  // tiles
 
   // ---- R_i (raw signs) for rows < n
 #pragma unroll
@@ -448,55 +517,33 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       }
     }
   }
-
-  if (Y == nullptr) return;  // R-only mode (indirect TSQR)
-
-  // ---- the Gram entries v_i^T v_j (i < j) and tau_j of the compact-WY form,
-  //      binary64, into the T slot; k_build_t turns them into T_i
-  if (warp == 0) {
-    double* Tout = Tst + static_cast<int64_t>(blockIdx.x) * n * n;
-    for (int idx = lane; idx < n * n; idx += 32) {
-      const int i = idx / n, kk = idx % n;
-      Tout[idx] = (kk > i) ? static_cast<double>(gram[idx]) : (kk == i ? static_cast<double>(taus[i]) : 0.0);
-    }
-  }
-  __syncthreads();
-
-  // ---- Y_i back through shared memory, bulk store (compute format for df64)
-  using YS = YStore<S, T>;
-  YS* ystage = reinterpret_cast<YS*>(stage);
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    const int r = rbase + 32 * q;
-    if (r < rows) {
-#pragma unroll
-      for (int c = 0; c < NPC; ++c) {
-        const int k = cs + c * CS;
-        if (k < n) {
-          if constexpr (std::is_same<YS, T>::value) ystage[r * n + k] = a[q][c];
-          else ystage[r * n + k] = static_cast<YS>(a[q][c]);
-        }
-      }
-    }
-  }
-  fence_proxy_async_smem();
-  __syncthreads();
-  cta_store_bulk(reinterpret_cast<YS*>(Y) + row0 * n, ystage, static_cast<int64_t>(rows) * n);
 }
 
 // ---------------------------------------------------------------------------
-// Step 3: Q_i = [C_i; 0] - Y_i W_i, W_i = T_i (Y_top_i^T C_i).
-//   Yg  : m x n (storage S), Y_i per block as written by k_local_qr.
-//   Tg  : p blocks of n x n binary64.  Cg: p blocks of n x n binary64 (Q2_i).
+// Step 3: Q_i = Q1_i C_i with C_i = Q2_i (n x n binary64), one CTA per row
+// block.  A block of one tile gives Q_i = [C; 0] - Y_i W, W = T (Y_top^T C).
+// A block factored as a flat tree of tiles (k_local_qr) is taken tile by
+// tile, last to first, with X = C: tile t >= 1 has Householder vectors
+// [I; V_t], so W_t = T_t X, its rows of Q are -V_t W_t and tile t-1 gets
+// X - W_t; tile 0 is the one-tile case with C = X.
+//   Yg  : m x n (storage S), as written by k_local_qr.
+//   Tg  : kt slots of n x n binary64 per block (T of each tile, upper part).
+//   Cg  : cblocks blocks of n x n binary64 (cblocks == 1: one C for all).
 //   Qg  : output m x n (storage S); may alias Yg.
+// The n x n operands stream through the stage in row chunks; each thread
+// keeps its (at most kMaxE) entries of an n x NPAD product in registers.
 // ---------------------------------------------------------------------------
+constexpr int kMaxE = 16;  // n NPAD / (32 CS NRG) = 5 n / (32 NRG) <= 16 for n <= 100
+
 template <class S, class T, int NPC, int R, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int n, int b, int srows, int CS, int NRG,
-                                                     const double* __restrict__ Tg, const double* __restrict__ Cg,
-                                                     int64_t cblocks, S* Qg, int32_t* status) {
+__global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int n, int b, int bt, int kt, int srows,
+                                                     int CS, int NRG, const double* __restrict__ Tg,
+                                                     const double* __restrict__ Cg, int64_t cblocks, S* Qg,
+                                                     int32_t* status) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   const int NPAD = NPC * CS;
+  const int B = 32 * NRG * R;
   const FormQSmem L(srows, n, NPAD, sizeof(S), sizeof(T));
   S* stage = reinterpret_cast<S*>(smem + L.stage);
   T* Xm = reinterpret_cast<T*>(smem + L.xm);
@@ -507,91 +554,145 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
   const int cs = warp % CS, rg = warp / CS;
   const int64_t row0 = static_cast<int64_t>(blockIdx.x) * b;
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
+  const int ntiles = rows <= B ? 1 : 1 + (rows - B + bt - 1) / bt;
   const int rbase = rg * 32 * R + lane;  // thread rows rbase + 32 q, as in k_local_qr
   const int ntop = rows < n ? rows : n;
-  (void)NRG;
+  const int NE = n * NPAD;
   using YS = YStore<S, T>;
   const YS* Yb = reinterpret_cast<const YS*>(Yg) + row0 * n;
   YS* ystage = reinterpret_cast<YS*>(stage);
+  T* tm = reinterpret_cast<T*>(stage);
+  // rows of an n-column matrix of 8-byte values that the stage holds
+  const int crow = static_cast<int>(static_cast<size_t>(srows) * sizeof(S) / 8);
 
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
   const int64_t cb = cblocks == 1 ? 0 : static_cast<int64_t>(blockIdx.x);
-  const double* Tb = Tg + static_cast<int64_t>(blockIdx.x) * n * n;
   const double* Cb = Cg + cb * n * n;
-
-  // X = Y_top^T C  (Y_top unit lower triangular, rows < ntop, read from
-  // global memory before any row of this block is overwritten)
-  for (int idx = tid; idx < n * NPAD; idx += NT) {
-    const int k = idx / NPAD, c = idx % NPAD;
-    T acc = T(0);
-    if (c < n && k < ntop) {
-      acc = to_compute<T>(Cb[k * n + c], 0);
-      for (int r = k + 1; r < ntop; ++r)
-        acc = fma(static_cast<T>(Yb[r * n + k]), to_compute<T>(Cb[r * n + c], 0), acc);
-    }
-    Xm[idx] = acc;
-  }
-  __syncthreads();
-  // W = T X (T upper triangular), one entry per thread
-  for (int idx = tid; idx < n * NPAD; idx += NT) {
-    const int k = idx / NPAD, c = idx % NPAD;
-    T acc = T(0);
-    if (c < n)
-      for (int i = k; i < n; ++i) acc = fma(to_compute<T>(Tb[k * n + i], 0), Xm[i * NPAD + c], acc);
-    Wm[idx] = acc;
+  for (int idx = tid; idx < NE; idx += NT) {  // X = C
+    const int kk = idx / NPAD, c = idx % NPAD;
+    Xm[idx] = c < n ? to_compute<T>(Cb[kk * n + c], 0) : T(0);
   }
   __syncthreads();
 
-  // Q rows = [C; 0] - Y W, chunk by chunk of `srows` staged rows
   uint32_t parity = 0;
-  for (int c0 = 0; c0 < rows; c0 += srows) {
-    const int crows = rows - c0 < srows ? rows - c0 : srows;
-    if (!cta_load_bulk(ystage, Yb + static_cast<int64_t>(c0) * n, static_cast<int64_t>(crows) * n, bar, parity,
-                       status))
-      return;
-    T acc[R][NPC];
+  for (int t = ntiles - 1; t >= 0; --t) {
+    const int tr0 = t == 0 ? 0 : B + (t - 1) * bt;  // first row of the tile's data in the block
+    const int cnt = t == 0 ? (rows < B ? rows : B) : (rows - tr0 < bt ? rows - tr0 : bt);
+    const double* Tb = Tg + (static_cast<int64_t>(blockIdx.x) * kt + t) * n * n;
+    T w[kMaxE];
+    const T* src = Xm;
+    if (t == 0) {
+      // Z = Y_top^T X (Y_top unit lower triangular), Y_top streamed by rows;
+      // read before any row of the block is overwritten
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int r = c0 + rbase + 32 * q;  // row within the block
+      for (int e = 0; e < kMaxE; ++e) {
+        const int idx = tid + e * NT, kk = idx / NPAD, c = idx % NPAD;
+        w[e] = (idx < NE && c < n && kk < ntop) ? Xm[idx] : T(0);
+      }
+      for (int r0 = 0; r0 < ntop; r0 += crow) {
+        const int r1 = ntop < r0 + crow ? ntop : r0 + crow;
+        for (int idx = tid; idx < (r1 - r0) * n; idx += NT) ystage[idx] = Yb[static_cast<int64_t>(r0) * n + idx];
+        __syncthreads();
 #pragma unroll
-      for (int c = 0; c < NPC; ++c) {
-        const int k = cs + c * CS;
-        acc[q][c] = (r < ntop && k < n) ? to_compute<T>(Cb[r * n + k], 0) : T(0);
+        for (int e = 0; e < kMaxE; ++e) {
+          const int idx = tid + e * NT, kk = idx / NPAD, c = idx % NPAD;
+          if (idx < NE && c < n)
+            for (int r = (r0 > kk + 1 ? r0 : kk + 1); r < r1; ++r)
+              w[e] = fma(static_cast<T>(ystage[(r - r0) * n + kk]), Xm[r * NPAD + c], w[e]);
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int e = 0; e < kMaxE; ++e)
+        if (tid + e * NT < NE) Wm[tid + e * NT] = w[e];
+      __syncthreads();
+      src = Wm;
+    }
+    // W = T src (T upper triangular), T streamed by rows: row kk of W is
+    // complete in the chunk that holds row kk of T
+#pragma unroll
+    for (int e = 0; e < kMaxE; ++e) w[e] = T(0);
+    for (int k0 = 0; k0 < n; k0 += crow) {
+      const int k1 = n < k0 + crow ? n : k0 + crow;
+      for (int idx = tid; idx < (k1 - k0) * n; idx += NT) {
+        const int i = idx / n, col = idx % n;
+        tm[idx] = col >= k0 + i ? to_compute<T>(Tb[static_cast<int64_t>(k0) * n + idx], 0) : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < kMaxE; ++e) {
+        const int idx = tid + e * NT, kk = idx / NPAD, c = idx % NPAD;
+        if (idx < NE && c < n && kk >= k0 && kk < k1)
+          for (int i = kk; i < n; ++i) w[e] = fma(tm[(kk - k0) * n + i], src[i * NPAD + c], w[e]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int e = 0; e < kMaxE; ++e) {
+      const int idx = tid + e * NT;
+      if (idx < NE) {
+        Wm[idx] = w[e];
+        if (t > 0) Xm[idx] = Xm[idx] - w[e];  // coefficient of tile t-1
       }
     }
-    for (int k = 0; k < n; ++k) {
-      T w[NPC];
-#pragma unroll
-      for (int c = 0; c < NPC; ++c) w[c] = Wm[k * NPAD + cs + c * CS];
+    __syncthreads();
+
+    // the tile's rows of Q, chunk by chunk of `srows` staged rows:
+    // tile 0: [X; 0] - Y W (unit lower Y_top); tile t >= 1: -V_t W
+    const bool top = (t == 0);
+    for (int c0 = 0; c0 < cnt; c0 += srows) {
+      const int crows = cnt - c0 < srows ? cnt - c0 : srows;
+      const int64_t g0 = row0 + tr0 + c0;  // first matrix row of the chunk
+      if (!cta_load_bulk(ystage, reinterpret_cast<const YS*>(Yg) + g0 * n, static_cast<int64_t>(crows) * n, bar,
+                         parity, status))
+        return;
+      T acc[R][NPC];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int rl = rbase + 32 * q;  // row within the chunk
-        const int r = c0 + rl;
-        T y = T(0);
-        if (rl < crows) y = (k < r) ? static_cast<T>(ystage[rl * n + k]) : (k == r ? T(1) : T(0));
-#pragma unroll
-        for (int c = 0; c < NPC; ++c) acc[q][c] = fma(-y, w[c], acc[q][c]);
-      }
-    }
-    __syncthreads();  // every read of this chunk in shared memory is done
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      const int rl = rbase + 32 * q;
-      if (rl < crows) {
+        const int r = c0 + rbase + 32 * q;  // row within the tile
 #pragma unroll
         for (int c = 0; c < NPC; ++c) {
-          const int k = cs + c * CS;
-          if (k < n) stage[rl * n + k] = to_storage<S>(acc[q][c]);
+          const int kc = cs + c * CS;
+          acc[q][c] = (top && r < ntop && kc < n) ? Xm[r * NPAD + kc] : T(0);
         }
       }
+      for (int kk = 0; kk < n; ++kk) {
+        T wk[NPC];
+#pragma unroll
+        for (int c = 0; c < NPC; ++c) wk[c] = Wm[kk * NPAD + cs + c * CS];
+        const YS* yp = ystage + rbase * n + kk;  // advanced by 32 rows per step
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          const int rl = rbase + 32 * q;  // row within the chunk
+          const int r = c0 + rl;
+          T y = T(0);
+          if (rl < crows) y = static_cast<T>(*yp);
+          if (top && kk >= r) y = (kk == r) ? T(1) : T(0);
+          yp += 32 * n;
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) acc[q][c] = fma(-y, wk[c], acc[q][c]);
+        }
+      }
+      __syncthreads();  // every read of this chunk in shared memory is done
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int rl = rbase + 32 * q;
+        if (rl < crows) {
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) {
+            const int kc = cs + c * CS;
+            if (kc < n) stage[rl * n + kc] = to_storage<S>(acc[q][c]);
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+      cta_store_bulk(Qg + g0 * n, stage, static_cast<int64_t>(crows) * n);
+      __syncthreads();  // the stage is free again (bulk store read it, tail stores done)
     }
-    fence_proxy_async_smem();
-    __syncthreads();
-    cta_store_bulk(Qg + row0 * n + static_cast<int64_t>(c0) * n, stage, static_cast<int64_t>(crows) * n);
-    __syncthreads();  // the stage is free again (bulk store read it, tail stores done)
   }
 }
 

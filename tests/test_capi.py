@@ -69,6 +69,15 @@ def test_workspace_size_host_only(lib):
     assert st2 == 0 and b2 >= 100 * 2 * 10 * 10 * 8
 
 
+def test_workspace_tiled_blocks(lib):
+    """Blocks taller than the register tile are accepted: one R per block and
+    one T per tile (binary64 R tile of 640 rows at n = 25, then 614-row tiles)."""
+    st, b = _ws(lib, 0, 200_000, 25, 0, block_rows=5000)
+    assert st == 0
+    p, kt = 40, 1 + -(-(5000 - 640) // 614)
+    assert b >= (p + p * kt) * 25 * 25 * 8
+
+
 @pytest.mark.parametrize("m,n,dt,b,f,want", [
     (10, 20, 0, 0, 0, 2),       # m < n
     (100, 0, 0, 0, 0, 2),       # n < 1

@@ -26,7 +26,8 @@ def _direct(A, **kw):
 
 
 @pytest.mark.parametrize("m,n,b,f", [(100_000, 10, 1000, 0), (4099, 25, 0, 0), (3000, 7, 64, 2),
-                                     (20_000, 50, 0, 0), (3000, 100, 0, 0), (513, 1, 0, 0)])
+                                     (20_000, 50, 0, 0), (3000, 100, 0, 0), (513, 1, 0, 0),
+                                     (203_457, 25, 5000, 0), (60_000, 50, 2999, 0)])
 def test_df64_parity_gaussian(m, n, b, f):
     A = ti.gaussian(m, n, 2000 + m + n)
     Q, R = _direct(A, block_rows=b, fanout=f)
@@ -64,6 +65,20 @@ def test_df64_tiny_and_huge_scales():
         e2, _ = oracle.orth_error(Q)
         rF, _ = oracle.residual(A * s, Q, R)
         assert e2 <= 1e-13 and rF <= 1e-13, (s, e2, rF)
+
+
+def test_df64_scale_grows_between_tiles():
+    """Tiles of one block with magnitudes 2^60 apart: the running power-of-two
+    scale rises at the large tile and the carried R is rescaled exactly."""
+    A = ti.gaussian(40_000, 12, 93)
+    A[3000:6000] *= 2.0 ** 60
+    Q, R = _direct(A, block_rows=10_000)
+    Qo, Ro = oracle.householder_qr(A)
+    kappa = np.linalg.cond(A)
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 10 * 12 * kappa * U48
+    e2, _ = oracle.orth_error(Q)
+    rF, _ = oracle.residual(A, Q, R)
+    assert e2 <= 1e-13 and rF <= 1e-13, (e2, rF)
 
 
 def test_df64_svd():

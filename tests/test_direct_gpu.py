@@ -69,6 +69,12 @@ SHAPES = [
     (20_000, 50, 0, 0),
     (12_000, 64, 0, 0),
     (3000, 100, 0, 0),
+    # blocks taller than the register tile: in-CTA flat tree of tiles
+    (203_457, 25, 5000, 0),   # 41 blocks, ragged last block of one tile
+    (150_001, 10, 12_345, 0), # last block of several tiles, last tile short
+    (60_000, 50, 2999, 0),
+    (30_000, 100, 1500, 0),   # many tiles of few rows (binary64: 28 per tile)
+    (1_000_003, 25, 0, 0),    # default block height (two tiles per block)
 ]
 
 
@@ -123,4 +129,8 @@ def test_direct_rejects_bad_arguments():
     with pytest.raises(T.TSQRError):
         T.direct(A, block_rows=5)          # block_rows < n
     with pytest.raises(T.TSQRError):
-        T.direct(A, block_rows=10**7)      # above the per-block capacity
+        T.direct(A, block_rows=-1)
+    # a block taller than the matrix is one block (factored tile by tile)
+    Q, R = T.direct(A, block_rows=10**7)
+    Qd, Rd = T.direct(A)
+    assert float((R - Rd).abs().max()) <= 1e-13 * float(Rd.abs().max())

@@ -53,6 +53,20 @@ def test_svd_parity_f64(m, n, seed):
     assert rF <= 1e-13
 
 
+def test_svd_tiled_blocks():
+    """SVD variant over blocks of several register tiles."""
+    m, n = 60_000, 20
+    A = ti.power_spectrum(m, n, 5)
+    U, S, V = _T().svd(_cuda(A), block_rows=7001)
+    U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    Uo, So, Vo = oracle.svd(A)
+    assert np.max(np.abs(S - So) / So[0]) <= 10 * n * EPS64
+    gap = np.min(np.abs(np.diff(So))) / So[0]
+    tolv = 100 * n * EPS64 / gap
+    assert np.max(np.abs(V - Vo)) <= tolv and np.max(np.abs(U - Uo)) <= tolv
+    assert oracle.orth_error(U)[0] <= 1e-13
+
+
 def test_svd_f32_storage():
     m, n = 50_000, 20
     A = ti.power_spectrum(m, n, 9).astype(np.float32)
@@ -109,6 +123,17 @@ def test_indirect_parity_well_conditioned(refine):
     A = ti.conditioned(40_000, 25, 1.0, 21)
     Q, R = _T().indirect_refine(_cuda(A), refine=refine)
     st, Qo, Ro = oracle.indirect_refine(A, refine)
+    assert st == 0
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-13
+    assert np.max(np.abs(Q - Qo)) <= 1e-13
+
+
+def test_indirect_tiled_blocks():
+    """R-only TSQR over blocks of several register tiles."""
+    A = ti.conditioned(40_000, 25, 1.0, 24)
+    Q, R = _T().indirect_refine(_cuda(A), refine=1, block_rows=9000)
+    st, Qo, Ro = oracle.indirect_refine(A, 1)
     assert st == 0
     Q, R = Q.cpu().numpy(), R.cpu().numpy()
     assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= 1e-13
