@@ -355,6 +355,10 @@ def main():
     if not args.no_extras and rank == 0:
         line["extras"] = extras(T, torch, A, n, m, dev, other_prec="native" if args.prec == "df64" else "df64")
     if not args.no_extras and rank == 0:
+        del A, Q, work
+        torch.cuda.empty_cache()
+        line["configs"] = config_extras(T, torch, dev)
+    if not args.no_extras and rank == 0:
         line["cpu_baseline"] = cpu_baseline(A_host)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -413,6 +417,115 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
         except Exception as e:  # a breakdown is a result, not a crash
             ms, err = float("nan"), f"{type(e).__name__}: {e}"
         out[name] = {"rows_s": m / (ms * 1e-3) if ms == ms else None, "ms": ms, "orth_error_2": err}
+    return out
+
+
+def config_extras(T, torch, dev, steps=3):
+    """The other benchmark configurations (synthetic, generated on the device
+    from a seeded generator): the FP32 form on 50,000,000 x 50 against the
+    FP64 form on the same matrix upcast, the SVD variant on 20,000,000 x 100
+    FP32 storage, and forward + backward on 4,000,000 x 64 in FP32 and FP64."""
+    out = {}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    def orth(Qx):
+        n = Qx.shape[1]
+        G = torch.zeros(n, n, dtype=torch.float64, device=dev)
+        for r0 in range(0, Qx.shape[0], 1 << 22):
+            blk = Qx[r0:r0 + (1 << 22)].double()
+            G += blk.T @ blk
+        G -= torch.eye(n, dtype=torch.float64, device=dev)
+        return float(torch.linalg.eigvalsh(G.cpu()).abs().max())
+
+    def resid(Ax, Qx, Rx):
+        num = den = 0.0
+        for r0 in range(0, Ax.shape[0], 1 << 22):
+            a = Ax[r0:r0 + (1 << 22)].double()
+            num += float(((a - Qx[r0:r0 + (1 << 22)].double() @ Rx) ** 2).sum())
+            den += float((a ** 2).sum())
+        return (num / den) ** 0.5
+
+    g = torch.Generator(device=dev)
+    # mixed precision: N(0,1) scaled by column factors log-spaced over [1, 1e-4]
+    try:
+        m, n = 50_000_000, 50
+        g.manual_seed(ti.SEED_MIXED)
+        c = torch.logspace(0, -4, n, dtype=torch.float64, device=dev)
+        A32 = (torch.randn(m, n, dtype=torch.float32, device=dev, generator=g) * c.float())
+        entry = {"workload": "50,000,000x50 FP32, N(0,1) x column factors 1..1e-4"}
+        Q, R = T.direct(A32)
+        ms = timed(lambda: T.direct(A32, check=False))
+        entry["fp32"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Q),
+                         "residual_F": resid(A32, Q, R),
+                         "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9}
+        del Q
+        A64 = A32.double()
+        del A32
+        Q, R = T.direct(A64)
+        ms = timed(lambda: T.direct(A64, check=False))
+        entry["fp64_upcast"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Q),
+                                "residual_F": resid(A64, Q, R),
+                                "hbm_gbs_algorithmic": 4 * m * n * 8 / (ms * 1e-3) / 1e9}
+        del Q, A64
+        out["mixed_50Mx50"] = entry
+    except Exception as e:  # reported, not fatal
+        out["mixed_50Mx50"] = {"error": f"{type(e).__name__}: {e}"}
+    torch.cuda.empty_cache()
+    # SVD variant: G diag(j^-2) V^T, FP32 storage
+    try:
+        m, n = 20_000_000, 100
+        g.manual_seed(ti.SEED_SVD)
+        V, _ = torch.linalg.qr(torch.randn(n, n, dtype=torch.float64, device=dev, generator=g))
+        sig = torch.arange(1, n + 1, dtype=torch.float64, device=dev) ** -2.0
+        M = (sig[:, None] * V.T) / m ** 0.5
+        A = torch.empty(m, n, dtype=torch.float32, device=dev)
+        for r0 in range(0, m, 1 << 22):
+            rows = min(1 << 22, m - r0)
+            A[r0:r0 + rows] = (torch.randn(rows, n, dtype=torch.float64, device=dev, generator=g) @ M).float()
+        U, S, Vo = T.svd(A)
+        ms = timed(lambda: T.svd(A, check=False))
+        out["svd_20Mx100"] = {"workload": "20,000,000x100 FP32 storage, G diag(j^-2) V^T",
+                              "rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2_U": orth(U),
+                              "max_rel_sigma_dev": float((S / sig - 1).abs().max()),
+                              "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9}
+        del U, A
+    except Exception as e:
+        out["svd_20Mx100"] = {"error": f"{type(e).__name__}: {e}"}
+    torch.cuda.empty_cache()
+    # forward + backward, 4,000,000 x 64, row blocks of 4,096
+    try:
+        m, n = 4_000_000, 64
+        entry = {"workload": "4,000,000x64 N(0,1), W_Q and W_R N(0,1), row blocks of 4,096"}
+        for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            g.manual_seed(ti.SEED_GRAD)
+            A = torch.randn(m, n, dtype=dt, device=dev, generator=g)
+            WQ = torch.randn(m, n, dtype=dt, device=dev, generator=g)
+            WR = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+
+            def fb():
+                Qx, Rx = T.direct(A, block_rows=4096, check=False)
+                T.backward(Qx, Rx, WQ, WR, check=False)
+
+            ms = timed(fb)
+            msf = timed(lambda: T.direct(A, block_rows=4096, check=False))
+            Q, R = T.direct(A, block_rows=4096)
+            entry[name] = {"fwd_bwd_rows_s": m / (ms * 1e-3), "fwd_bwd_ms": ms, "fwd_rows_s": m / (msf * 1e-3),
+                           "orth_error_2": orth(Q)}
+            del A, WQ, Q
+        out["grad_4Mx64"] = entry
+    except Exception as e:
+        out["grad_4Mx64"] = {"error": f"{type(e).__name__}: {e}"}
+    torch.cuda.empty_cache()
     return out
 
 

@@ -1,5 +1,6 @@
 // capi.cu -- the extern "C" boundary (include/tsqr.h): argument checks, the
 // plan, and the launch sequence of each computation on the caller's stream.
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <cuda_runtime.h>
@@ -71,6 +72,23 @@ cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, i
 namespace {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// SM count of the current device (the planner's default block height
+// depends on it); the GB300 value when no device answers.
+int device_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return kDefaultSMs;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();  // clear the error of a host without a device
+    return kDefaultSMs;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 
 int esz_of(int32_t dtype) { return dtype == TSQR_F64 ? 8 : (dtype == TSQR_F32 ? 4 : 0); }
 
@@ -213,7 +231,8 @@ tsqr_status copy_r(double* R, int64_t ldr, const double* src, int64_t n, cudaStr
 tsqr_status plan_for(int op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* o, size_t work_bytes,
                      const void* work, Plan* P) {
   const int prec = (o && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? o->prec : 0;
-  int rc = make_plan(m, n, esz_of(dtype), o ? o->block_rows : 0, o ? o->tree_fanout : 0, P, prec);
+  int rc = make_plan(m, n, esz_of(dtype), o ? o->block_rows : 0, o ? o->tree_fanout : 0, P, prec,
+                     device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   if (!work || !aligned16(work) || work_bytes < op_bytes(*P, op)) return TSQR_ERR_WORKSPACE;
   return TSQR_OK;
@@ -252,7 +271,8 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
   if (s != TSQR_OK) return s;
   const int prec = (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? opts->prec : 0;
   Plan P;
-  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec);
+  int rc =
+      make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec, device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   const int L = static_cast<int>(P.levels.size());
   switch (op) {
@@ -286,7 +306,8 @@ tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
   if (op < TSQR_OP_DIRECT || op > TSQR_OP_BACKWARD) return TSQR_ERR_ARG;
   const int prec = (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? opts->prec : 0;
   Plan P;
-  int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec);
+  int rc =
+      make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec, device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   *bytes = op_bytes(P, op);
   return TSQR_OK;
@@ -303,7 +324,7 @@ tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_
   if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
   Plan P;
   int rc = make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P,
-                     opts ? opts->prec : 0);
+                     opts ? opts->prec : 0, device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   if (!work || work_bytes < P.bytes || !aligned16(work)) return TSQR_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -16,7 +16,7 @@ TSQR_HD constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a *
 
 // Shared-memory layout of k_local_qr (identical on host and device).
 struct LocalQrSmem {
-  size_t stage, red, xcol, piv, tau, refl, bar, total;
+  size_t stage, red, xcol, piv, tau, refl, nrm, bar, total;
   TSQR_HD LocalQrSmem(int B, int n, int NW, int NPAD, size_t ssz, size_t tsz) {
     size_t o = 0;
     stage = o; o = align_up(o + (size_t)B * n * ssz, 16);
@@ -28,6 +28,7 @@ struct LocalQrSmem {
     piv = o; o = align_up(o + 2 * (size_t)NPAD * tsz, 16);    // double-buffered pivot row
     tau = o; o = align_up(o + (size_t)NPAD * tsz, 16);
     refl = o; o = align_up(o + 8 * tsz, 16);                  // reflector scalars of the column
+    nrm = o; o = align_up(o + 2 * 32 * (size_t)tsz, 16);     // look-ahead norms per row group
     bar = o; o = align_up(o + 16, 16);
     total = o;
   }

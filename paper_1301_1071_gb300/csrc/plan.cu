@@ -96,7 +96,7 @@ size_t op_bytes(const Plan& P, int op) {
   return (op == TSQR_OP_CHOLQR || op == TSQR_OP_BACKWARD) ? P.bytes_gram : P.bytes;
 }
 
-int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec) {
+int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec, int sms) {
   if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
   if (prec != TSQR_PREC_NATIVE && (prec != TSQR_PREC_DF64 || esz != 8)) return TSQR_ERR_ARG;
   Plan P;
@@ -121,10 +121,18 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   if (bt < 1) return TSQR_ERR_SHAPE;
   int64_t b0 = block_rows;
   if (b0 <= 0) {
-    const int64_t want = m / kMinBlocks;
-    int64_t kt = want <= B0 ? 1 : 1 + (want - B0) / bt;
-    if (kt > kMaxTiles) kt = kMaxTiles;
-    b0 = B0 + (kt - 1) * bt;
+    if (sms < 1) sms = kDefaultSMs;
+    const int64_t kmax = kind0 == kKindDF64 ? kMaxTilesDF64 : kMaxTiles;
+    const int64_t bmax = B0 + (kmax - 1) * bt;
+    if (m <= (int64_t)kMinWaves * sms * B0) {
+      b0 = B0;
+    } else {
+      int64_t waves = (m + (int64_t)sms * bmax - 1) / ((int64_t)sms * bmax);
+      if (waves < kMinWaves) waves = kMinWaves;
+      const int64_t p = waves * sms;
+      b0 = (m + p - 1) / p;
+      b0 = (b0 + al - 1) / al * al;  // blocks start on 16-byte boundaries
+    }
   }
   if (b0 < n) return TSQR_ERR_SHAPE;
   if (b0 > m) b0 = m;  // one block

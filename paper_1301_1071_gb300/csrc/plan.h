@@ -69,11 +69,17 @@ struct Plan {
 };
 
 constexpr int kSmallSlots = 8;  // n x n binary64 matrices in each small scratch area
-// Default Step-1 block height: enough tiles per block that the stack of R
-// factors (and so the Step-2 tree) stays small, while keeping at least
-// kMinBlocks blocks (4 per SM on a 152-SM GB300) and at most kMaxTiles tiles.
-constexpr int64_t kMinBlocks = 608;
-constexpr int kMaxTiles = 64;
+// Default Step-1 block height.  Small problems: one register tile per block.
+// Otherwise the number of blocks is a whole number (at least kMinWaves) of
+// waves of one CTA per SM, so that no wave runs part-empty, with blocks as
+// tall as kMaxTiles tiles allow: tall blocks keep the stack of R factors (and
+// so the Step-2 tree) small.  The flat tree inside a block adds rounding
+// error in proportion to its tiles, so double-float compute (unit roundoff
+// 2^-48) takes fewer of them.
+constexpr int kMinWaves = 4;
+constexpr int kMaxTiles = 32;
+constexpr int kMaxTilesDF64 = 8;
+constexpr int kDefaultSMs = 152;  // GB300
 constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM of a GB300)
 
 // Workspace bytes of `op` (tsqr_op) under a built plan.
@@ -82,6 +88,8 @@ size_t op_bytes(const Plan& P, int op);
 // Builds the plan; returns 0 or a tsqr_status code.  block_rows > 0 fixes
 // the Step-1 block height (any value >= n; above the register tile's B rows
 // the block is factored tile by tile); 0 chooses it.
-int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec = 0);
+// `sms` = the device's SM count (sizes the default block height).
+int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec = 0,
+              int sms = kDefaultSMs);
 
 }  // namespace tsqr

@@ -147,15 +147,48 @@ __device__ __forceinline__ T shfl_bcast(T v) {
   }
 }
 
+// Sum over the warp (every lane gets it).
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = v + shfl_xor(v, o);
+  return v;
+}
+
+// Sum of squares of this thread's entries of column C (rows above `from`
+// excluded), summed over the warp.
+template <int C, int NPC, int R, class T>
+__device__ __forceinline__ T col_norm2(const T (&a)[R][NPC], int rbase, int from) {
+  if constexpr (std::is_same<T, df64>::value) {
+    df64_acc acc;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const T v = (rbase + 32 * q >= from) ? a[q][C] : T(0);
+      acc.add_prod(v, v);
+    }
+    return warp_sum(acc.value());
+  } else {
+    T ss = T(0);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const T v = (rbase + 32 * q >= from) ? a[q][C] : T(0);
+      ss = fma(v, v, ss);
+    }
+    return warp_sum(ss);
+  }
+}
+
 // Trailing update of the thread's tile for column j, with the first trailing
 // local column C0 known at compile time: a[q][c] -= d[c] x_q for c >= C0.
 // The thread's rows are rbase + 32 q (q < R); the published pivot column x_j
 // is zero above row j, so the update needs no row test.  The warp owning
 // column j (local index C0 - 1) stores v_j = x scal below the pivot; the warp
-// owning column j + 1 (local index C0) publishes it, zeroed above row j + 1.
+// owning column j + 1 (local index C0) publishes it, zeroed above row j + 1,
+// and its squared norm over this row group (look-ahead: the reflector of
+// column j + 1 is formed from it before column j + 1's dot products).
 template <int C0, int NPC, int R, class T>
 __device__ __forceinline__ void tile_update(T (&a)[R][NPC], const T (&d)[NPC], const T* xcur, T* xnext, int j,
-                                            int rbase, bool own_j, bool own_next, T scal) {
+                                            int rbase, bool own_j, bool own_next, T scal, T* nnext) {
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const T xq = xcur[rbase + 32 * q];
@@ -175,6 +208,8 @@ __device__ __forceinline__ void tile_update(T (&a)[R][NPC], const T (&d)[NPC], c
     if (own_next) {
 #pragma unroll
       for (int q = 0; q < R; ++q) xnext[rbase + 32 * q] = (rbase + 32 * q > j) ? a[q][C0] : T(0);
+      const T ss = col_norm2<C0, NPC, R>(a, rbase, j + 1);
+      if ((threadIdx.x & 31) == 0) *nnext = ss;
     }
   }
 }
@@ -224,6 +259,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
   T* piv = reinterpret_cast<T*>(smem + L.piv);
   T* taus = reinterpret_cast<T*>(smem + L.tau);
   T* refl = reinterpret_cast<T*>(smem + L.refl);  // beta, scal, 1/beta, tau, identity flag
+  T* nrm = reinterpret_cast<T*>(smem + L.nrm);    // look-ahead squared norms, 2 x 32
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -301,10 +337,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
     }
     __syncthreads();  // stage is reused for the Gram matrix from here on
 
-    // publish pivot column 0 and pivot row 0
+    // publish pivot column 0 (and its squared norm per row group) and pivot row 0
     if (cs == 0) {
 #pragma unroll
       for (int q = 0; q < R; ++q) xbuf[rbase + 32 * q] = a[q][0];
+      const T ss = col_norm2<0, NPC, R>(a, rbase, 0);
+      if (lane == 0) nrm[rg] = ss;
     }
     if (rg == 0 && lane == 0) {
 #pragma unroll
@@ -319,6 +357,35 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       const T* pcur = piv + jb * NPAD;        // row j
       T* pnext = piv + (jb ^ 1) * NPAD;       // row j+1
       T* rcur = red + jb * NW * 32;           // partial sums of this step
+      const T* ncur = nrm + jb * 32;          // squared norm of x_j per row group
+      T* nnext = nrm + (jb ^ 1) * 32;         // ... of x_{j+1}
+
+      // ---- the reflector of column j, from the look-ahead squared norm of x_j
+      //      and alpha = a_jj: formed by the warp of row group 0 that owns
+      //      column j, published before its dot products so that its scalar
+      //      sequence overlaps the other warps' phase A
+      Reflector<T> f;
+      const bool owner = (rg == 0) && (cs == j % CS);
+      if (owner) {
+        if (lane == 0) {
+          T Sj = T(0);
+          for (int g = 0; g < NRG; ++g) Sj += ncur[g];
+          f = make_reflector(Sj, pcur[j]);
+          refl[0] = f.beta;
+          refl[1] = f.scal;
+          refl[2] = f.ib;
+          refl[3] = f.tau;
+          refl[4] = f.ident ? T(1) : T(0);
+          taus[j] = f.tau;
+        }
+        __syncwarp();
+        if (NRG == 1) named_bar_arrive(1, NT);  // producer: the scalars are out
+        f.beta = shfl_bcast(f.beta);
+        f.scal = shfl_bcast(f.scal);
+        f.ib = shfl_bcast(f.ib);
+        f.tau = shfl_bcast(f.tau);
+        f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
+      }
 
       // ---- phase A: s = x_j^T A over the thread's rows (rows < j give 0), CTA partials
       {
@@ -345,64 +412,43 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         }
         TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
       }
-      __syncthreads();
-
-      // ---- phase B: lane c < NPC of every warp sums the partials of its column
-      //      c; warp 0 forms the reflector and publishes its scalars (producer
-      //      side of named barrier 1, the other warps wait on it), so the scalar
-      //      sequence runs once per CTA; then lane c forms R's r_jk = S_k / beta
-      //      (r_jj = beta) and d_c = (a_jk - r_jk) / (alpha - beta), which every
-      //      lane takes by shuffle
-      T Sc = T(0), pc = T(0);
-      const int mycol = cs + lane * CS;
-      if (lane < NPC && mycol < n) {
-        for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
-        pc = pcur[mycol];
-      }
-      Reflector<T> f;
-      if (warp == 0) {
-        if (lane == 0) {
-          T Sj = T(0);
-          for (int g = 0; g < NRG; ++g) Sj += rcur[(g * CS + j % CS) * 32 + j / CS];
-          f = make_reflector(Sj, pcur[j]);
-          refl[0] = f.beta;
-          refl[1] = f.scal;
-          refl[2] = f.ib;
-          refl[3] = f.tau;
-          refl[4] = f.ident ? T(1) : T(0);
-          taus[j] = f.tau;
-        }
+      // one row group: each warp's column sums are its own (a warp sync
+      // suffices) and only the reflector crosses warps; several row groups:
+      // the partial sums cross warps too
+      if (NRG == 1) {
         __syncwarp();
-        named_bar_arrive(1, NT);
-        f.beta = shfl_bcast(f.beta);
-        f.scal = shfl_bcast(f.scal);
-        f.ib = shfl_bcast(f.ib);
-        f.tau = shfl_bcast(f.tau);
-        f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
+        if (!owner) named_bar_sync(1, NT);
       } else {
-        named_bar_sync(1, NT);
+        __syncthreads();
+      }
+      if (!owner) {
         f.beta = refl[0];
         f.scal = refl[1];
         f.ib = refl[2];
         f.tau = refl[3];
         f.ident = refl[4] != T(0);
       }
-      if (warp == NW - 1) {  // Gram entries v_k^T v_j of the compact-WY T (off warp 0's path)
-        for (int kk = lane; kk < j; kk += 32) {
-          T Sk = T(0);
-          for (int g = 0; g < NRG; ++g) Sk += rcur[(g * CS + kk % CS) * 32 + kk / CS];
-          gram[kk * n + j] = f.scal * (Sk - f.beta * pcur[kk]);
-        }
-      }
+
+      // ---- phase B: lane c < NPC sums the partials of its column c over the
+      //      row groups, then forms R's r_jk = S_k / beta (r_jj = beta),
+      //      d_c = (a_jk - r_jk) / (alpha - beta) and, for k < j, the Gram
+      //      entry v_k^T v_j of the compact-WY T; every lane takes d and r_j
+      //      by shuffle
       T d[NPC], rj[NPC];
       {
         T dl = T(0), rl = T(0);
-        if (lane < NPC) {
-          if (mycol > j && mycol < n) {
+        const int mycol = cs + lane * CS;
+        if (lane < NPC && mycol < n) {
+          T Sc = T(0);
+          for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
+          const T pc = pcur[mycol];
+          if (mycol > j) {
             rl = Sc * f.ib;
             dl = (pc - rl) * f.scal;
           } else if (mycol == j) {
             rl = f.beta;
+          } else if (rg == 0) {
+            gram[mycol * n + j] = f.scal * (Sc - f.beta * pc);
           }
         }
 #pragma unroll
@@ -417,12 +463,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       const bool own_j = (cs == j % CS);
       const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
       switch (c0) {
-        case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-        case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-        case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-        case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-        case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
-        default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal); break;
+        case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+        case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+        case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+        case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+        case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+        default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
       }
       // rows j and j+1 (< n <= 128) are register rows q < 4 of row group 0:
       // the thread holding row j writes R's row j, the one holding row j+1
