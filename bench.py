@@ -35,6 +35,13 @@ import tsqr_inputs as ti  # noqa: E402
 METRIC = "direct-TSQR rows/s and HBM GB/s (fwd; fwd+bwd) at stated ||Q^TQ-I||, 1 GB300"
 HBM_PEAK_FALLBACK = 6800.0  # GB/s, used only when MEASURED_PEAKS.json is absent
 FP64_PEAK_GFLOPS = 1250.0   # nominal GB300 FP64 rate (152 SMs x ~2 DFMA/clk x 2 flop x 2.07 GHz)
+FP32_PEAK_GFLOPS = 80540.0  # nominal GB300 FP32 CUDA-core rate (152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz)
+
+# Algorithmic passes over the tall matrix (m n s bytes each) per call: read A
+# and write Y (Step 1), read Y and write Q (Step 3); Cholesky QR and indirect
+# TSQR read A twice and write Q once; refinement repeats the method; the
+# adjoint reads Q and dQ for the Gram, then Q and dQ again and writes dA.
+ALG_PASSES = {"direct": 4, "cholqr": 3, "cholqr_ir": 6, "indirect": 3, "indirect_ir": 6, "backward": 5}
 
 WORKLOADS = {
     "sweep": dict(m=8_000_000, n=25, dtype="f64", kappa=1e15, block_rows=0, seed=ti.SEED_SWEEP,
@@ -42,6 +49,8 @@ WORKLOADS = {
                        "sigma log-spaced 1..1e-15 (kappa 1e15)"),
     "small": dict(m=100_000, n=10, dtype="f64", kappa=None, block_rows=1000, seed=ti.SEED_SMALL,
                   name="100,000x10 FP64 i.i.d. N(0,1), row blocks of 1,000"),
+    "mixed": dict(m=50_000_000, n=50, dtype="f32", kappa=None, colscale=1e-4, block_rows=0, seed=ti.SEED_MIXED,
+                  name="50,000,000x50 FP32 N(0,1) x column factors 1..1e-4"),
 }
 
 
@@ -71,9 +80,14 @@ def replica_throughput(rows_per_rank: int, steps: int, world: int, max_ms: float
 
 def make_input(w, rows=None):
     """The workload matrix, or only its first `rows` rows."""
-    if w["kappa"] is None:
-        return ti.gaussian(w["m"], w["n"], w["seed"], rows=rows)
-    return ti.conditioned(w["m"], w["n"], w["kappa"], w["seed"], rows=rows)
+    if w.get("colscale"):
+        return ti.column_scaled(w["m"] if rows is None else rows, w["n"], w["colscale"], w["seed"],
+                                dtype=np.float32 if w["dtype"] == "f32" else np.float64)
+    elif w["kappa"] is None:
+        A = ti.gaussian(w["m"], w["n"], w["seed"], rows=rows)
+    else:
+        A = ti.conditioned(w["m"], w["n"], w["kappa"], w["seed"], rows=rows)
+    return A.astype(np.float32) if w["dtype"] == "f32" else A
 
 
 def load_peaks():
@@ -160,19 +174,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(A_host: np.ndarray, target_s: float = 12.0, max_rows: int = 2_000_000):
+def cpu_baseline(A_host: np.ndarray, target_s: float = 12.0, max_rows: int = 8_000_000):
     """The oracle (plain single-threaded FP64 Householder QR with explicit Q)
     on a bounded row sample of the same matrix."""
     import oracle
     n = A_host.shape[1]
     rows = 100_000
+    sample = np.asarray(A_host[:rows], dtype=np.float64)
     t0 = time.perf_counter()
-    oracle.householder_qr(A_host[:rows])
+    oracle.householder_qr(sample)
     t = time.perf_counter() - t0
     if t < target_s / 3:
         rows = int(min(max_rows, A_host.shape[0], rows * target_s / max(t, 1e-3)))
+        sample = np.asarray(A_host[:rows], dtype=np.float64)
         t0 = time.perf_counter()
-        oracle.householder_qr(A_host[:rows])
+        oracle.householder_qr(sample)
         t = time.perf_counter() - t0
     return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle",
             "sample": f"first {rows:,} rows x {n} of the workload matrix, one thin QR (Q and R), "
@@ -185,7 +201,7 @@ def run_reference(args, w):
         return 0
     import oracle
     rows = min(w["m"], 1_000_000)
-    sample = make_input(w, rows=rows)
+    sample = np.asarray(make_input(w, rows=rows), dtype=np.float64)
     for _ in range(args.warmup):
         oracle.householder_qr(sample)
     t0 = time.perf_counter()
@@ -241,6 +257,7 @@ def main():
 
     m, n = w["m"], w["n"]
     A_host = make_input(w)
+    gb = A_host.nbytes / 1e9
     A = torch.from_numpy(A_host).to(dev)
     Q = torch.empty_like(A)
     R = torch.empty(n, n, dtype=torch.float64, device=dev)
@@ -279,33 +296,40 @@ def main():
     s1, s2, s3 = statistics.mean(st1), statistics.mean(st2), statistics.mean(st3)
     rows_s = replica_throughput(m, args.steps, ws, total_ms)
     elem = 8 if A.dtype == torch.float64 else 4
-    alg_bytes = 4 * m * n * elem
+    alg_bytes = ALG_PASSES["direct"] * m * n * elem
     gbs = alg_bytes / (ms_step * 1e-3) / 1e9
     hbm_peak, peak_src = load_peaks()
 
     # dominant kernel: Step 1 (k_local_qr) or Step 3 (k_form_q); both are
-    # binary64 FMA-bound: 2 m n^2 algorithmic flops per launch
+    # FMA-bound (binary64 unit for FP64 data, binary32 for FP32 and for
+    # double-float compute): 2 m n^2 algorithmic flops per launch
     dom, dom_ms = ("k_local_qr", s1) if s1 >= s3 else ("k_form_q", s3)
     flops = 2.0 * m * n * n
     achieved = flops / (dom_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": load_traffic(dom, args.workload),
-                "kernel": dom, "peak_source": "nominal FP64 rate (recipe table); probe measured 1196 GFLOP/s",
+    if elem == 8 and args.prec == "native":
+        peak, alu_src = FP64_PEAK_GFLOPS, "nominal FP64 rate (recipe table); probe measured 1196 GFLOP/s"
+    else:
+        peak, alu_src = FP32_PEAK_GFLOPS, "nominal FP32 CUDA-core rate; probe measured 74.8 TFLOP/s"
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                "frac": achieved / peak, "traffic": load_traffic(dom, args.workload),
+                "kernel": dom, "peak_source": alu_src,
                 "hbm_view": {"achieved_gbs": 2 * m * n * elem / (dom_ms * 1e-3) / 1e9, "peak_gbs": hbm_peak,
                              "frac": 2 * m * n * elem / (dom_ms * 1e-3) / 1e9 / hbm_peak,
                              "peak_source": peak_src}}
 
     # ---- accuracy at the stated kappa (library check with torch, FP64)
     with torch.no_grad():
-        G = Q.T @ Q
-        G -= torch.eye(n, dtype=G.dtype, device=dev)
-        orth2 = float(torch.linalg.eigvalsh(G.cpu()).abs().max())
+        G = torch.zeros(n, n, dtype=torch.float64, device=dev)
         res = 0.0
         an = 0.0
         for r0 in range(0, m, 1 << 21):
-            blk = A[r0:r0 + (1 << 21)]
-            res += float(((blk - Q[r0:r0 + (1 << 21)] @ R) ** 2).sum())
+            qb = Q[r0:r0 + (1 << 21)].double()
+            blk = A[r0:r0 + (1 << 21)].double()
+            G += qb.T @ qb
+            res += float(((blk - qb @ R) ** 2).sum())
             an += float((blk ** 2).sum())
+        G -= torch.eye(n, dtype=G.dtype, device=dev)
+        orth2 = float(torch.linalg.eigvalsh(G.cpu()).abs().max())
         resF = (res / an) ** 0.5
 
     # ---- end to end: pinned host A -> device, factor, Q and R back to the host
@@ -343,7 +367,8 @@ def main():
                   else ("f64" if elem == 8 else "f32")),
         "data": "synthetic",
         "config": {"workload": w["name"], "m": m, "n": n, "block_rows": w["block_rows"] or "auto",
-                   "l2": "inputs (1.6 GB) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
+                   "l2": f"inputs ({gb:.1f} GB) larger than L2; no flush" if gb > 0.2
+                   else "inputs smaller than L2", "parallelism": f"replicas x{ws}"},
         "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm_peak,
         "orth_error_2": orth2, "residual_F": resF,
         "step_ms": {"step1_local_qr": s1, "step2_tree": s2, "step3_form_q": s3},
@@ -400,7 +425,8 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
 
     ms = timed(fb)
     out["fwd_bwd"] = {"rows_s": m / (ms * 1e-3), "ms": ms,
-                      "hbm_gbs_algorithmic": 9 * m * n * A.element_size() / (ms * 1e-3) / 1e9}
+                      "hbm_gbs_algorithmic": (ALG_PASSES["direct"] + ALG_PASSES["backward"]) * m * n *
+                      A.element_size() / (ms * 1e-3) / 1e9}
     if A.dtype == torch.float64:
         Qp, Rp = T.direct(A, prec=other_prec)
         ms = timed(lambda: T.direct(A, check=False, prec=other_prec))
@@ -416,7 +442,9 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
             err = orth(Qx)
         except Exception as e:  # a breakdown is a result, not a crash
             ms, err = float("nan"), f"{type(e).__name__}: {e}"
-        out[name] = {"rows_s": m / (ms * 1e-3) if ms == ms else None, "ms": ms, "orth_error_2": err}
+        out[name] = {"rows_s": m / (ms * 1e-3) if ms == ms else None, "ms": ms, "orth_error_2": err,
+                     "hbm_gbs_algorithmic": (ALG_PASSES[name] * m * n * A.element_size() / (ms * 1e-3) / 1e9
+                                             if ms == ms else None)}
     return out
 
 
