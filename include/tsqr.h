@@ -64,15 +64,20 @@ typedef enum tsqr_status {
 
 typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
 
-/* Arithmetic of the tall passes (Step 1 and Step 3) for TSQR_F64 data.
- * NATIVE: IEEE binary64 throughout.
- * DF64:   binary64 storage, double-float arithmetic (pairs of binary32,
- *         ~48-bit significand) in Step 1 and Step 3, each row block scaled by
- *         a power of two (exact); the Step-2 tree, the SVD of R and all n x n
- *         work stay binary64.  Targets ||Q^TQ - I|| and the residual at the
- *         1e-13 level for kappa up to ~1e15.  Only tsqr_direct and tsqr_svd
- *         honour it; TSQR_F32 data require NATIVE. */
-typedef enum tsqr_prec { TSQR_PREC_NATIVE = 0, TSQR_PREC_DF64 = 1 } tsqr_prec;
+/* Arithmetic of the tall passes (Step 1 and Step 3).  Only tsqr_direct and
+ * tsqr_svd honour it; the Step-2 tree, the SVD of R and all n x n work are
+ * binary64 in every mode.
+ * NATIVE: the data's type (binary64 for TSQR_F64, binary32 with binary32
+ *         accumulation for TSQR_F32).
+ * DF64:   TSQR_F64 data only.  Binary64 storage, double-float arithmetic
+ *         (pairs of binary32, ~48-bit significand) in Step 1 and Step 3, each
+ *         row block scaled by a power of two (exact).  Targets ||Q^TQ - I||
+ *         and the residual at the 1e-13 level for kappa up to ~1e15.
+ * TF32X3: TSQR_F32 data only.  Step 1 as NATIVE; the Step-3 product
+ *         Y_i W_i runs on the tensor cores as 3xTF32 split precision
+ *         (Y = Yh + Yl, W = Wh + Wl rounded to TF32; Y W ~ Yh Wh + Yh Wl +
+ *         Yl Wh, binary32 accumulation) for n <= 64 (NATIVE Step 3 above). */
+typedef enum tsqr_prec { TSQR_PREC_NATIVE = 0, TSQR_PREC_DF64 = 1, TSQR_PREC_TF32X3 = 2 } tsqr_prec;
 
 /* Which computation a workspace is sized for. */
 typedef enum tsqr_op {
@@ -84,8 +89,9 @@ typedef enum tsqr_op {
 } tsqr_op;
 
 typedef struct tsqr_opts {
-  int64_t block_rows; /* rows per Step-1 row block; 0 = automatic.  Must be >= n
-                         and no larger than the kernel's per-block capacity. */
+  int64_t block_rows; /* rows per Step-1 row block; 0 = automatic.  Must be >= n.
+                         A block taller than one CTA's register tile is factored
+                         by that CTA tile by tile (a flat reduction tree). */
   int32_t tree_fanout; /* R factors merged per Step-2 tree node; 0 = automatic (>= 2) */
   int32_t sync;        /* 1 = synchronise the stream and return the device status */
   /* Optional stage timing (tsqr_direct, tsqr_svd): NULL, or 4 cudaEvent_t

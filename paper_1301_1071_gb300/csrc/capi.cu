@@ -95,7 +95,7 @@ int esz_of(int32_t dtype) { return dtype == TSQR_F64 ? 8 : (dtype == TSQR_F32 ? 
 tsqr_status check_opts(const tsqr_opts* o) {
   if (!o) return TSQR_OK;
   if (o->reserved != 0) return TSQR_ERR_ARG;
-  if (o->prec != TSQR_PREC_NATIVE && o->prec != TSQR_PREC_DF64) return TSQR_ERR_ARG;
+  if (o->prec != TSQR_PREC_NATIVE && o->prec != TSQR_PREC_DF64 && o->prec != TSQR_PREC_TF32X3) return TSQR_ERR_ARG;
   if (o->block_rows < 0 || o->tree_fanout < 0 || o->tree_fanout == 1) return TSQR_ERR_ARG;
   return TSQR_OK;
 }
@@ -176,8 +176,11 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
   const double* C0 = (L == 1) ? ctop : S(0);
   const int64_t cb0 = (L == 1) ? 1 : l0.p;
-  if (launch_form_q(P.cfg0, Q, P.m, n, l0.b, l0.bt, l0.kt, l0.p, T(0), C0, cb0, Q, status, st) != cudaSuccess)
-    return TSQR_ERR_CUDA;
+  const cudaError_t e3 =
+      P.tc3 ? launch_form_q_tc(static_cast<float*>(Q), P.m, n, l0.b, P.cfg0.B, l0.bt, l0.kt, l0.p, T(0), C0, cb0,
+                               status, st)
+            : launch_form_q(P.cfg0, Q, P.m, n, l0.b, l0.bt, l0.kt, l0.p, T(0), C0, cb0, Q, status, st);
+  if (e3 != cudaSuccess) return TSQR_ERR_CUDA;
   return mark(o, 3, st);
 }
 

@@ -6,6 +6,7 @@
 #include "../../include/tsqr.h"
 #include "launch.h"
 #include "layout.cuh"
+#include "tc_kernels.cuh"
 
 namespace tsqr {
 
@@ -98,7 +99,8 @@ size_t op_bytes(const Plan& P, int op) {
 
 int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec, int sms) {
   if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
-  if (prec != TSQR_PREC_NATIVE && (prec != TSQR_PREC_DF64 || esz != 8)) return TSQR_ERR_ARG;
+  if (prec != TSQR_PREC_NATIVE && !(prec == TSQR_PREC_DF64 && esz == 8) && !(prec == TSQR_PREC_TF32X3 && esz == 4))
+    return TSQR_ERR_ARG;
   Plan P;
   P.m = m;
   P.n = n;
@@ -143,6 +145,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   int64_t f = fanout > 0 ? fanout : fmax;
   if (f < 2 || f > fmax) return TSQR_ERR_SHAPE;
 
+  P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcMaxN;
   Level l0;
   l0.rows = m;
   l0.b = b0;

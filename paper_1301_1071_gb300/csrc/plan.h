@@ -59,6 +59,7 @@ struct Plan {
   int esz = 8;           // element size of the tall matrices
   KernelCfg cfg0;        // Step-1 kernel config (dtype of A)
   KernelCfg cfg64;       // tree kernel config (binary64)
+  bool tc3 = false;      // Step 3 on the tensor cores (3xTF32, binary32 data, n <= 64)
   std::vector<Level> levels;  // levels[0] = Step 1; levels[1..] = tree
   size_t off_ctop = 0;   // n x n binary64 top coefficient (sign matrix, or D U_R)
   size_t off_small = 0;  // scratch for small n x n work (SVD, Cholesky, ...)

@@ -1,0 +1,88 @@
+"""Parity of the 3xTF32 tensor-core Step 3 (TSQR_PREC_TF32X3, FP32 data).
+
+Step 1 and the tree are those of the FP32 form; the Step-3 product Y_i W_i
+runs on the tensor cores (tcgen05, kind::tf32) with Y and W split into TF32
+high and low parts (three products, binary32 accumulation).  Bars: the FP32
+form's (||Q^TQ - I||_2 <= 1e-5, ||A - QR||_F/||A||_F <= 1e-5, R and Q within
+10 n kappa 2^-23 of the FP64 oracle on the upcast input).  n > 64 falls back
+to the binary32 FMA path and must give the same bars.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import tsqr_inputs as ti
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS32 = 2.0 ** -23
+
+
+def _run(A, **kw):
+    import paper_1301_1071_gb300 as T
+    Q, R = T.direct(torch.tensor(A, device="cuda"), prec="tf32x3", **kw)
+    torch.cuda.synchronize()
+    return Q.double().cpu().numpy(), R.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,b,f", [
+    (100_000, 10, 1000, 0),
+    (4099, 25, 0, 0),          # ragged last block
+    (700, 25, 0, 0),           # one block
+    (3000, 7, 64, 2),          # deep binary tree
+    (513, 1, 0, 0),            # n = 1
+    (37, 37, 0, 0),            # square
+    (20_000, 50, 0, 0),
+    (60_000, 50, 2999, 0),     # blocks of several register tiles
+    (12_000, 64, 0, 0),        # largest n on the tensor-core path
+    (3000, 100, 0, 0),         # above it: binary32 FMA fallback
+])
+def test_tf32x3_parity(m, n, b, f):
+    A = ti.gaussian(m, n, 3000 + m + n).astype(np.float32)
+    Q, R = _run(A, block_rows=b, fanout=f)
+    A64 = A.astype(np.float64)
+    Qo, Ro = oracle.householder_qr(A64)
+    kappa = np.linalg.cond(A64)
+    tol = 10 * n * kappa * EPS32
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) >= 0.0)
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= tol
+    assert np.max(np.abs(Q - Qo)) <= max(tol, 10 * n * EPS32)
+    e2, _ = oracle.orth_error(Q)
+    rF, _ = oracle.residual(A64, Q, R)
+    assert e2 <= 1e-5 and rF <= 1e-5, (e2, rF)
+
+
+def test_tf32x3_column_scaled():
+    """The mixed-precision workload's spectrum (column factors 1..1e-4)."""
+    A = ti.column_scaled(200_000, 50, 1e-4, ti.SEED_MIXED).astype(np.float32)
+    Q, R = _run(A)
+    e2, _ = oracle.orth_error(Q)
+    rF, _ = oracle.residual(A.astype(np.float64), Q, R)
+    assert e2 <= 1e-5 and rF <= 1e-5, (e2, rF)
+
+
+def test_tf32x3_matches_fp32_form():
+    """Same Step 1 and tree: the two Step-3 products agree to FP32 rounding."""
+    import paper_1301_1071_gb300 as T
+    A = torch.tensor(ti.gaussian(50_000, 40, 31).astype(np.float32), device="cuda")
+    Qt, Rt = T.direct(A, prec="tf32x3")
+    Qn, Rn = T.direct(A)
+    assert float((Rt - Rn).abs().max()) == 0.0  # Step 1 and the tree are shared
+    assert float((Qt - Qn).abs().max()) <= 1e-5
+
+
+def test_tf32x3_svd():
+    import paper_1301_1071_gb300 as T
+    A = ti.power_spectrum(50_000, 20, 9).astype(np.float32)
+    U, S, V = T.svd(torch.tensor(A, device="cuda"), prec="tf32x3")
+    _, So, _ = oracle.svd(A.astype(np.float64))
+    assert np.max(np.abs(S.cpu().numpy() - So) / So[0]) <= 1e-5
+    e2, _ = oracle.orth_error(U.double().cpu().numpy())
+    assert e2 <= 1e-5
+
+
+def test_tf32x3_rejected_for_f64():
+    import paper_1301_1071_gb300 as T
+    with pytest.raises(T.TSQRError):
+        T.direct(torch.randn(1000, 8, dtype=torch.float64, device="cuda"), prec="tf32x3")
