@@ -231,8 +231,8 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip comparators / fwd+bwd / cpu baseline")
     ap.add_argument("--m", type=int, default=0, help="override the row count (profiling a smaller case)")
-    ap.add_argument("--prec", default="native", choices=["native", "df64"],
-                    help="arithmetic of Steps 1 and 3 for FP64 data")
+    ap.add_argument("--prec", default="native", choices=["native", "df64", "tf32x3"],
+                    help="arithmetic of Steps 1 and 3 (df64: FP64 data; tf32x3: FP32 data)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.m:
@@ -364,6 +364,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": ("df64 (binary64 data, pairs of binary32 in Steps 1 and 3, binary64 tree)" if args.prec == "df64"
+                  else "f32 (Step 3 product as 3xTF32 on the tensor cores)" if args.prec == "tf32x3"
                   else ("f64" if elem == 8 else "f32")),
         "data": "synthetic",
         "config": {"workload": w["name"], "m": m, "n": n, "block_rows": w["block_rows"] or "auto",
@@ -378,7 +379,8 @@ def main():
     }
 
     if not args.no_extras and rank == 0:
-        line["extras"] = extras(T, torch, A, n, m, dev, other_prec="native" if args.prec == "df64" else "df64")
+        other = ("native" if args.prec != "native" else ("df64" if elem == 8 else "tf32x3"))
+        line["extras"] = extras(T, torch, A, n, m, dev, other_prec=other)
     if not args.no_extras and rank == 0:
         del A, Q, work
         torch.cuda.empty_cache()
@@ -409,9 +411,12 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
         return a.elapsed_time(b) / steps
 
     def orth(Qx):
-        G = Qx.T @ Qx
+        G = torch.zeros(n, n, dtype=torch.float64, device=dev)
+        for r0 in range(0, Qx.shape[0], 1 << 22):
+            blk = Qx[r0:r0 + (1 << 22)].double()
+            G += blk.T @ blk
         G -= torch.eye(n, dtype=G.dtype, device=dev)
-        return float(torch.linalg.eigvalsh(G.double().cpu()).abs().max())
+        return float(torch.linalg.eigvalsh(G.cpu()).abs().max())
 
     g = torch.Generator(device=dev)
     g.manual_seed(ti.SEED_GRAD)
@@ -427,11 +432,11 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
     out["fwd_bwd"] = {"rows_s": m / (ms * 1e-3), "ms": ms,
                       "hbm_gbs_algorithmic": (ALG_PASSES["direct"] + ALG_PASSES["backward"]) * m * n *
                       A.element_size() / (ms * 1e-3) / 1e9}
-    if A.dtype == torch.float64:
-        Qp, Rp = T.direct(A, prec=other_prec)
-        ms = timed(lambda: T.direct(A, check=False, prec=other_prec))
-        out[f"direct_{other_prec}"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Qp),
-                                       "hbm_gbs_algorithmic": 4 * m * n * 8 / (ms * 1e-3) / 1e9}
+    Qp, Rp = T.direct(A, prec=other_prec)
+    ms = timed(lambda: T.direct(A, check=False, prec=other_prec))
+    out[f"direct_{other_prec}"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Qp),
+                                   "hbm_gbs_algorithmic": ALG_PASSES["direct"] * m * n * A.element_size() /
+                                   (ms * 1e-3) / 1e9}
     for name, fn in [("cholqr", lambda: T.cholqr(A, refine=0, check=False)),
                      ("cholqr_ir", lambda: T.cholqr(A, refine=1, check=False)),
                      ("indirect_ir", lambda: T.indirect_refine(A, refine=1, check=False))]:

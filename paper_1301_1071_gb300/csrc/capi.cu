@@ -152,14 +152,14 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   if (launch_local_qr(P.cfg0, A, P.m, n, l0.b, l0.bt, l0.kt, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  if (launch_build_t(T(0), l0.p * l0.kt, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  if (launch_build_t(T(0), l0.p * l0.kt, n, P.esz == 4, st) != cudaSuccess) return TSQR_ERR_CUDA;
   // Step 2 (Alg. 2): the stack of level l-1 is the tall input of level l.
   for (size_t l = 1; l < L; ++l) {
     const Level& lv = P.levels[l];
     const cudaError_t e =
         launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, S(l - 1), S(l), T(l), status, st);
     if (e != cudaSuccess) return TSQR_ERR_CUDA;
-    if (launch_build_t(T(l), lv.p * lv.kt, n, st) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (launch_build_t(T(l), lv.p * lv.kt, n, false, st) != cudaSuccess) return TSQR_ERR_CUDA;
   }
   if (launch_sign_fix(S(L - 1), n, R, ldr, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
   if (extra(ctop) != TSQR_OK) return TSQR_ERR_CUDA;

@@ -124,7 +124,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   int64_t b0 = block_rows;
   if (b0 <= 0) {
     if (sms < 1) sms = kDefaultSMs;
-    const int64_t kmax = kind0 == kKindDF64 ? kMaxTilesDF64 : kMaxTiles;
+    const int64_t kmax = kind0 == kKindDF64 ? kMaxTilesDF64 : (kind0 == kKindF32 ? kMaxTilesF32 : kMaxTiles);
     const int64_t bmax = B0 + (kmax - 1) * bt;
     if (m <= (int64_t)kMinWaves * sms * B0) {
       b0 = B0;

@@ -78,7 +78,8 @@ constexpr int kSmallSlots = 8;  // n x n binary64 matrices in each small scratch
 // error in proportion to its tiles, so double-float compute (unit roundoff
 // 2^-48) takes fewer of them.
 constexpr int kMinWaves = 4;
-constexpr int kMaxTiles = 32;
+constexpr int kMaxTiles = 32;       // binary64 data
+constexpr int kMaxTilesF32 = 128;   // binary32 data: its binary64 tree is costly, its rounding unit large
 constexpr int kMaxTilesDF64 = 8;
 constexpr int kDefaultSMs = 152;  // GB300
 constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM of a GB300)

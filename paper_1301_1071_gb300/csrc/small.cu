@@ -353,27 +353,40 @@ cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop,
 // Compact-WY T factors of p row blocks, in place (one warp per block): the
 // slot holds tau_j on the diagonal and the Gram entries G(i,j) = v_i^T v_j
 // above it; T(j,j) = tau_j and T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j),
-// column by column (H_1 ... H_k = I - Y T Y^T).
+// column by column (H_1 ... H_k = I - Y T Y^T).  Each warp stages its slot in
+// shared memory at row stride n + 1 (lane i walks row i: at most two-way bank
+// conflicts), runs the recursion there in type F and writes the upper
+// triangle back (binary64 slots; F = binary32 for the row blocks of binary32
+// data, whose Gram entries are binary32 values).
+template <class F>
 __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
-  const int lane = threadIdx.x & 31;
-  const int64_t blk = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (blk >= p) return;
-  double* t = Tst + blk * n * n;
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  F* tsm = reinterpret_cast<F*>(tsm_raw);
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int ld = n + 1;
+  F* t = tsm + static_cast<size_t>(wl) * n * ld;
+  const int64_t blk = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wl;
+  if (blk >= p) return;  // warp-level work only: no CTA barrier below
+  double* g = Tst + blk * n * n;
+  for (int i = 0; i < n; ++i)
+    for (int c = i + lane; c < n; c += 32) t[i * ld + c] = static_cast<F>(g[i * n + c]);
+  __syncwarp();
   for (int j = 1; j < n; ++j) {
-    const double tj = t[j * n + j];
-    double v[4];
+    const F tj = t[j * ld + j];
+    F v[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int i = lane + 32 * s;
-      double a0 = 0.0, a1 = 0.0;
+      F a0 = F(0), a1 = F(0);
       if (i < j) {
-        a0 = t[i * n + i] * t[i * n + j];  // T(i,i) = tau_i times G(i,j)
+        const F* ti = t + i * ld;
+        a0 = ti[i] * ti[j];  // T(i,i) = tau_i times G(i,j)
         int l = i + 1;
         for (; l + 1 < j; l += 2) {
-          a0 = fma(t[i * n + l], t[l * n + j], a0);
-          a1 = fma(t[i * n + l + 1], t[(l + 1) * n + j], a1);
+          a0 = fma(ti[l], t[l * ld + j], a0);
+          a1 = fma(ti[l + 1], t[(l + 1) * ld + j], a1);
         }
-        if (l < j) a0 = fma(t[i * n + l], t[l * n + j], a0);
+        if (l < j) a0 = fma(ti[l], t[l * ld + j], a0);
       }
       v[s] = -tj * (a0 + a1);
     }
@@ -381,16 +394,31 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const int i = lane + 32 * s;
-      if (i < j) t[i * n + j] = v[s];
+      if (i < j) t[i * ld + j] = v[s];
     }
     __syncwarp();
   }
+  for (int i = 0; i < n; ++i)
+    for (int c = i + lane; c < n; c += 32) g[i * n + c] = static_cast<double>(t[i * ld + c]);
 }
 
-cudaError_t launch_build_t(double* Tst, int64_t p, int n, cudaStream_t st) {
-  const int warps = 8;
+cudaError_t launch_build_t(double* Tst, int64_t p, int n, bool binary32, cudaStream_t st) {
+  // as many warps (<= 8) as n (n + 1) staged values each fit in 200 KB
+  const size_t per_warp = static_cast<size_t>(n) * (n + 1) * (binary32 ? sizeof(float) : sizeof(double));
+  int warps = static_cast<int>((200u * 1024u) / per_warp);
+  warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
+  const size_t smem = static_cast<size_t>(warps) * per_warp;
   const int64_t grid = (p + warps - 1) / warps;
-  k_build_t<<<static_cast<unsigned>(grid), 32 * warps, 0, st>>>(Tst, p, n);
+  cudaError_t e;
+  if (binary32) {
+    e = cudaFuncSetAttribute(k_build_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_build_t<float><<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(Tst, p, n);
+  } else {
+    e = cudaFuncSetAttribute(k_build_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_build_t<double><<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(Tst, p, n);
+  }
   return cudaGetLastError();
 }
 

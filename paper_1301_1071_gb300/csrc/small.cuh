@@ -27,7 +27,7 @@ cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop,
                               int64_t ldv, int32_t* status, cudaStream_t st);
 
 // In place: p blocks of (tau on the diagonal, Gram v_i^T v_j above) -> T_i.
-cudaError_t launch_build_t(double* Tst, int64_t p, int n, cudaStream_t st);
+cudaError_t launch_build_t(double* Tst, int64_t p, int n, bool binary32, cudaStream_t st);
 // G = sum of the nparts n x n partials in index order (deterministic).
 cudaError_t launch_gram_reduce(const double* part, int nparts, int n, double* G, int32_t* status,
                                cudaStream_t st);

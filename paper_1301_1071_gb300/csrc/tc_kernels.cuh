@@ -7,10 +7,11 @@
 // One CTA per row block (as k_form_q): the tiles of the block are taken last
 // to first with X = C (see k_form_q); W of each tile is formed on the CUDA
 // cores in binary32, split into the B operands, and the tile's rows are
-// processed in chunks of 128 rows: A operands from global memory (split on
-// the fly), one MMA chain per chunk (K/8 steps x 3 products), completion on an
-// mbarrier, accumulators read back with tcgen05.ld, Q = [X; 0] - D (tile 0)
-// or -D written over Y through a shared-memory stage.
+// processed in chunks of 128 rows: each chunk arrives by bulk copy (TMA) into
+// one of two Y buffers while the previous chunk is processed, is split into
+// the A operands, multiplied by one MMA chain (K/8 steps x 3 products) that
+// completes on an mbarrier, read back from tensor memory with tcgen05.ld, and
+// Q = [X; 0] - D (tile 0) or -D is written over Y through the same buffer.
 //
 // Operand layout: no swizzle, K-major: core matrices of 8 rows x 16 bytes
 // (4 TF32 values); element (r, k) at ((r/8) * K/4 + k/4) * 128 + (r%8) * 16 +
@@ -36,8 +37,12 @@ TSQR_HD constexpr int tc_cols(int n) { return tc_n(n) <= 32 ? 32 : (tc_n(n) <= 6
 
 // Shared-memory layout of k_form_q_tc.  The A buffers double as the stage of
 // the n x n operands in the prologue and of the Q rows in the epilogue.
+// Y chunks are double-buffered: the bulk copy of the next chunk runs while
+// the current one is converted, multiplied and written back.  A Y buffer
+// holds 128 rows at row stride n (bulk copy) and later the Q rows at the odd
+// stride n + 1 (conflict-free epilogue).
 struct FormQTcSmem {
-  size_t a_hi, a_lo, b_hi, b_lo, xm, wm, bar, tslot, total;
+  size_t a_hi, a_lo, b_hi, b_lo, xm, wm, ybuf0, ybuf1, bar, lbar, tslot, total;
   TSQR_HD FormQTcSmem(int n) {
     const size_t K = tc_k(n), N = tc_n(n);
     size_t o = 0;
@@ -47,7 +52,10 @@ struct FormQTcSmem {
     b_lo = o; o = align_up(o + N * K * 4, 128);
     xm = o; o = align_up(o + (size_t)n * n * 4, 16);
     wm = o; o = align_up(o + (size_t)n * n * 4, 16);
+    ybuf0 = o; o = align_up(o + (size_t)kTcM * (n + 1) * 4, 128);
+    ybuf1 = o; o = align_up(o + (size_t)kTcM * (n + 1) * 4, 128);
     bar = o; o = align_up(o + 8, 8);
+    lbar = o; o = align_up(o + 16, 8);
     tslot = o; o = align_up(o + 8, 16);
     total = o;
   }
@@ -98,7 +106,7 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 //   Tg : kt slots of n x n binary64 per block (upper triangle).
 //   Cg : cblocks blocks of n x n binary64 (cblocks == 1: one C for all).
 // Launch: gridDim = p, blockDim = kTcThreads, dynamic smem = FormQTcSmem(n).
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_form_q_tc(float* Yg, int64_t m, int n, int b, int B, int bt, int kt, const double* __restrict__ Tg,
                 const double* __restrict__ Cg, int64_t cblocks, int32_t* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -109,8 +117,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   float* b_lo = reinterpret_cast<float*>(smem + L.b_lo);
   float* xm = reinterpret_cast<float*>(smem + L.xm);
   float* wm = reinterpret_cast<float*>(smem + L.wm);
-  float* stage = a_hi;  // n x n operands (prologue) and Q rows (epilogue); spans a_hi and a_lo
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
+  float* stage = a_hi;  // n x n operands of the prologue; spans a_hi and a_lo
+  float* ybuf[2] = {reinterpret_cast<float*>(smem + L.ybuf0), reinterpret_cast<float*>(smem + L.ybuf1)};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);    // MMA completion
+  uint64_t* lbar = reinterpret_cast<uint64_t*>(smem + L.lbar);  // Y chunk arrival, one per buffer
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -126,6 +136,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(lbar, 1);
+    mbar_init(lbar + 1, 1);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -136,146 +148,240 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   }
   const int64_t cb = cblocks == 1 ? 0 : static_cast<int64_t>(blockIdx.x);
   for (int idx = tid; idx < nn; idx += kTcThreads) xm[idx] = static_cast<float>(Cg[cb * nn + idx]);  // X = C
+  // this thread's entries of an n x n product: idx = tid + e kTcThreads = kk n + c
+  int ekk[kTcMaxE], ec[kTcMaxE];
+  {
+    int kk = tid / n, c = tid % n;
+    const int dk = kTcThreads / n, dc = kTcThreads % n;
+#pragma unroll
+    for (int e = 0; e < kTcMaxE; ++e) {
+      ekk[e] = kk;
+      ec[e] = c;
+      kk += dk;
+      c += dc;
+      if (c >= n) {
+        c -= n;
+        ++kk;
+      }
+    }
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  uint32_t parity = 0;
+  // chunk (t, c0): rows [c0, c0 + 128) of tile t; tiles are taken last to
+  // first, so the sequence starts at tile ntiles - 1
+  auto tile_rows = [&](int t, int& tr0, int& cnt) {
+    tr0 = t == 0 ? 0 : B + (t - 1) * bt;
+    cnt = t == 0 ? (rows < B ? rows : B) : (rows - tr0 < bt ? rows - tr0 : bt);
+  };
+  // Issue (thread 0) the bulk copy of the 16-byte-aligned body of chunk
+  // (t, c0) into Y buffer s; the rest is read with plain loads on arrival.
+  auto issue = [&](int t, int c0, int s) {
+    int tr0, cnt;
+    tile_rows(t, tr0, cnt);
+    const int crows = cnt - c0 < kTcM ? cnt - c0 : kTcM;
+    const float* src = Yg + (row0 + tr0 + c0) * n;
+    const uint32_t bytes = static_cast<uint32_t>(crows) * n * 4;
+    const uint32_t body = (reinterpret_cast<uintptr_t>(src) & 15) == 0 ? (bytes & ~15u) : 0u;
+    if (tid == 0 && body > 0) {
+      mbar_arrive_expect_tx(lbar + s, body);
+      for (uint32_t off = 0; off < body; off += kBulkChunk) {
+        const uint32_t len = body - off < kBulkChunk ? body - off : kBulkChunk;
+        bulk_g2s(reinterpret_cast<char*>(ybuf[s]) + off, reinterpret_cast<const char*>(src) + off, len, lbar + s);
+      }
+    }
+    return body;
+  };
+
+  uint32_t parity = 0, lph[2] = {0u, 0u};
+  bool pend[2] = {false, false};  // a bulk copy into the buffer has not been waited for
   bool ok = true;
-  for (int t = ntiles - 1; t >= 0 && ok; --t) {
-    const int tr0 = t == 0 ? 0 : B + (t - 1) * bt;
-    const int cnt = t == 0 ? (rows < B ? rows : B) : (rows - tr0 < bt ? rows - tr0 : bt);
-    const double* Tb = Tg + (static_cast<int64_t>(blockIdx.x) * kt + t) * nn;
-    const float* src = xm;
-    float w[kTcMaxE];
-    if (t == 0) {
-      // Z = Y_top^T X (Y_top unit lower triangular, rows < ntop of the block)
-      for (int idx = tid; idx < ntop * n; idx += kTcThreads) stage[idx] = Yg[row0 * n + idx];
+  int t = ntiles - 1, c0 = 0, cur_tile = -1;
+  uint32_t body_cur = issue(t, c0, 0), body_next = 0;
+  pend[0] = body_cur > 0;
+  for (int ci = 0;; ++ci) {
+    const int s = ci & 1;
+    int tr0, cnt;
+    tile_rows(t, tr0, cnt);
+    const int crows = cnt - c0 < kTcM ? cnt - c0 : kTcM;
+    float* yq = Yg + (row0 + tr0 + c0) * n;  // first row of the chunk (Y in, Q out)
+    const bool top = (t == 0);
+    if (t != cur_tile) {
+      // ---- prologue of tile t: W, and the B operands
+      cur_tile = t;
+      const double* Tb = Tg + (static_cast<int64_t>(blockIdx.x) * kt + t) * nn;
+      const float* src = xm;
+      float w[kTcMaxE];
+      if (t == 0) {
+        // Z = Y_top^T X (Y_top unit lower triangular, rows < ntop of the block)
+        for (int idx = tid; idx < ntop * n; idx += kTcThreads) stage[idx] = Yg[row0 * n + idx];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kTcMaxE; ++e) {
+          const int kk = ekk[e], c = ec[e];
+          float acc = 0.0f;
+          if (kk < ntop) {
+            acc = xm[kk * n + c];
+            for (int r = kk + 1; r < ntop; ++r) acc = fmaf(stage[r * n + kk], xm[r * n + c], acc);
+          }
+          w[e] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kTcMaxE; ++e)
+          if (ekk[e] < n) wm[ekk[e] * n + ec[e]] = w[e];
+        __syncthreads();
+        src = wm;
+      }
+      // W = T src (T upper triangular, binary64 slot rounded to binary32)
+      for (int i = warp; i < n; i += kTcThreads / 32)
+        for (int col = lane; col < n; col += 32)
+          stage[i * n + col] = col >= i ? static_cast<float>(Tb[i * n + col]) : 0.0f;
       __syncthreads();
 #pragma unroll
       for (int e = 0; e < kTcMaxE; ++e) {
-        const int idx = tid + e * kTcThreads, kk = idx / n, c = idx % n;
+        const int kk = ekk[e], c = ec[e];
         float acc = 0.0f;
-        if (idx < nn && kk < ntop) {
-          acc = xm[idx];
-          for (int r = kk + 1; r < ntop; ++r) acc = fmaf(stage[r * n + kk], xm[r * n + c], acc);
-        }
+        if (kk < n)
+          for (int i = kk; i < n; ++i) acc = fmaf(stage[kk * n + i], src[i * n + c], acc);
         w[e] = acc;
       }
       __syncthreads();
 #pragma unroll
-      for (int e = 0; e < kTcMaxE; ++e)
-        if (tid + e * kTcThreads < nn) wm[tid + e * kTcThreads] = w[e];
-      __syncthreads();
-      src = wm;
-    }
-    // W = T src (T upper triangular, binary64 slot rounded to binary32)
-    for (int idx = tid; idx < nn; idx += kTcThreads) {
-      const int i = idx / n, col = idx % n;
-      stage[idx] = col >= i ? static_cast<float>(Tb[idx]) : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < kTcMaxE; ++e) {
-      const int idx = tid + e * kTcThreads, kk = idx / n, c = idx % n;
-      float acc = 0.0f;
-      if (idx < nn)
-        for (int i = kk; i < n; ++i) acc = fmaf(stage[kk * n + i], src[i * n + c], acc);
-      w[e] = acc;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < kTcMaxE; ++e) {
-      const int idx = tid + e * kTcThreads;
-      if (idx < nn) {
-        wm[idx] = w[e];
-        if (t > 0) xm[idx] -= w[e];  // coefficient of tile t-1
+      for (int e = 0; e < kTcMaxE; ++e) {
+        if (ekk[e] < n) {
+          const int idx = ekk[e] * n + ec[e];
+          wm[idx] = w[e];
+          if (t > 0) xm[idx] -= w[e];  // coefficient of tile t-1
+        }
       }
-    }
-    __syncthreads();
-    // B operands: element (c, k) of B^T = W[k][c], split into TF32 hi + lo;
-    // warp iteration `it` fills core matrix it (8 rows x 4 values) lane by lane
-    for (int it = warp; it < (N / 8) * KQ; it += kTcThreads / 32) {
-      const int c = (it / KQ) * 8 + (lane >> 2), k = (it % KQ) * 4 + (lane & 3);
-      const float x = (c < n && k < n) ? wm[k * n + c] : 0.0f;
-      const float h = tf32_round(x);
-      b_hi[it * 32 + lane] = h;
-      b_lo[it * 32 + lane] = tf32_round(x - h);
-    }
+      __syncthreads();
+      // B operands: element (c, k) of B^T = W[k][c], split into TF32 hi + lo;
+      // warp iteration `it` fills core matrix it (8 rows x 4 values) lane by lane
+      for (int gc = warp; gc < N / 8; gc += kTcThreads / 32)
+        for (int kq = 0; kq < KQ; ++kq) {
+          const int it = gc * KQ + kq;
+          const int c = gc * 8 + (lane >> 2), k = kq * 4 + (lane & 3);
+          const float x = (c < n && k < n) ? wm[k * n + c] : 0.0f;
+          const float h = tf32_round(x);
+          b_hi[it * 32 + lane] = h;
+          b_lo[it * 32 + lane] = tf32_round(x - h);
+        }
 
-    // the tile's rows, 128 at a time
-    const bool top = (t == 0);
-    for (int c0 = 0; c0 < cnt && ok; c0 += kTcM) {
-      const int crows = cnt - c0 < kTcM ? cnt - c0 : kTcM;
-      float* yq = Yg + (row0 + tr0 + c0) * n;  // first row of the chunk (Y in, Q out)
-      // A operands from global memory, split into TF32: warp iteration `it`
-      // fills core matrix it (rows 8 (it / KQ) .., values 4 (it % KQ) ..) with
-      // one float per lane (conflict-free stores; 16-byte row pieces read)
-      for (int it = warp; it < (kTcM / 8) * KQ; it += kTcThreads / 32) {
-        const int r = (it / KQ) * 8 + (lane >> 2), k = (it % KQ) * 4 + (lane & 3);
-        float y = 0.0f;
-        if (r < crows && k < n) {
-          y = yq[r * n + k];
-          if (top && c0 + r < n && k >= c0 + r) y = (k == c0 + r) ? 1.0f : 0.0f;  // unit lower Y_top
+    }
+    // ---- prefetch the next chunk into the other buffer (its last readers
+    //      finished before the barrier that ended the previous chunk)
+    int nt = t, nc0 = c0 + kTcM;
+    if (nc0 >= cnt) {
+      nt = t - 1;
+      nc0 = 0;
+    }
+    body_next = nt >= 0 ? issue(nt, nc0, s ^ 1) : 0u;
+    pend[s ^ 1] = body_next > 0;
+    // ---- this chunk's Y: bulk body, then the plain-load remainder
+    if (body_cur > 0) {
+      ok = mbar_wait_bounded(lbar + s, lph[s]);
+      if (ok) {
+        lph[s] ^= 1u;
+        pend[s] = false;
+      }
+    }
+    for (int e = static_cast<int>(body_cur / 4) + tid; e < crows * n; e += kTcThreads) ybuf[s][e] = yq[e];
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok) {
+      if (tid == 0) set_status(status, TSQR_ERR_TIMEOUT);
+      break;
+    }
+    // ---- A operands from the staged rows, split into TF32: warp iteration
+    //      `it` fills core matrix it (rows 8 (it / KQ) .., values 4 (it % KQ) ..)
+    //      with one value per lane
+    {
+      const float* ys = ybuf[s];
+      for (int gr = warp; gr < kTcM / 8; gr += kTcThreads / 32) {
+        const int r = gr * 8 + (lane >> 2);
+        const float* yr = ys + r * n + (lane & 3);
+        for (int kq = 0; kq < KQ; ++kq) {
+          const int it = gr * KQ + kq, k = kq * 4 + (lane & 3);
+          float y = 0.0f;
+          if (r < crows && k < n) {
+            y = yr[kq * 4];
+            if (top && c0 + r < n && k >= c0 + r) y = (k == c0 + r) ? 1.0f : 0.0f;  // unit lower Y_top
+          }
+          const float h = tf32_round(y);
+          a_hi[it * 32 + lane] = h;
+          a_lo[it * 32 + lane] = tf32_round(y - h);
         }
-        const float h = tf32_round(y);
-        a_hi[it * 32 + lane] = h;
-        a_lo[it * 32 + lane] = tf32_round(y - h);
       }
-      fence_proxy_async_smem();  // generic writes of A (and B) -> tensor-core reads
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (tid == 0) {
-        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-        for (int kb = 0; kb < K / 8; ++kb) {
-          const uint32_t ko = static_cast<uint32_t>(kb) * 256;
-          const uint64_t dah = tc_smem_desc(ah + ko, lbo, sbo), dal = tc_smem_desc(al + ko, lbo, sbo);
-          const uint64_t dbh = tc_smem_desc(bh + ko, lbo, sbo), dbl = tc_smem_desc(bl + ko, lbo, sbo);
-          tc_mma_tf32(tmem, dah, dbh, idesc, kb > 0);
-          tc_mma_tf32(tmem, dah, dbl, idesc, 1);
-          tc_mma_tf32(tmem, dal, dbh, idesc, 1);
-        }
-        tc_commit(bar);
+    }
+    fence_proxy_async_smem();  // generic writes of A (and B) -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+      for (int kb = 0; kb < K / 8; ++kb) {
+        const uint32_t ko = static_cast<uint32_t>(kb) * 256;
+        const uint64_t dah = tc_smem_desc(ah + ko, lbo, sbo), dal = tc_smem_desc(al + ko, lbo, sbo);
+        const uint64_t dbh = tc_smem_desc(bh + ko, lbo, sbo), dbl = tc_smem_desc(bl + ko, lbo, sbo);
+        tc_mma_tf32(tmem, dah, dbh, idesc, kb > 0);
+        tc_mma_tf32(tmem, dah, dbl, idesc, 1);
+        tc_mma_tf32(tmem, dal, dbh, idesc, 1);
       }
-      ok = __syncthreads_and(mbar_wait_bounded(bar, parity) ? 1 : 0) != 0;  // uniform over the CTA
-      parity ^= 1u;
-      tc_fence_after();
-      if (!ok) {
-        if (tid == 0) set_status(status, TSQR_ERR_TIMEOUT);
-        break;
-      }
-      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows of the chunk),
-      // columns [h N / 2, (h + 1) N / 2) with h = w / 4; Q rows to the stage
-      {
-        const int q = warp & 3, h = warp >> 2;
-        const int r = 32 * q + lane;
-        const int rt = c0 + r;  // row within the tile
-        for (int col0 = h * (N / 2); col0 < (h + 1) * (N / 2); col0 += 8) {
-          uint32_t v[8];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-              : "r"(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(col0)));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      tc_commit(bar);
+    }
+    ok = __syncthreads_and(mbar_wait_bounded(bar, parity) ? 1 : 0) != 0;  // uniform over the CTA
+    parity ^= 1u;
+    tc_fence_after();
+    if (!ok) {
+      if (tid == 0) set_status(status, TSQR_ERR_TIMEOUT);
+      break;
+    }
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows of the chunk),
+    //      columns [h N / 2, (h + 1) N / 2) with h = w / 4; Q rows into the
+    //      chunk's Y buffer at stride n + 1
+    {
+      float* qs = ybuf[s];
+      const int q = warp & 3, h = warp >> 2;
+      const int r = 32 * q + lane;
+      const int rt = c0 + r;  // row within the tile
+      for (int col0 = h * (N / 2); col0 < (h + 1) * (N / 2); col0 += 8) {
+        uint32_t v[8];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+            : "r"(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(col0)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int col = col0 + i;
-            if (col < n && r < crows) {
-              float x = -__uint_as_float(v[i]);
-              if (top && rt < ntop) x += xm[rt * n + col];
-              stage[r * (n + 1) + col] = x;  // odd row stride: no bank conflicts
-            }
+        for (int i = 0; i < 8; ++i) {
+          const int col = col0 + i;
+          if (col < n && r < crows) {
+            float x = -__uint_as_float(v[i]);
+            if (top && rt < ntop) x += xm[rt * n + col];
+            qs[r * (n + 1) + col] = x;
           }
         }
       }
-      tc_fence_before();
-      __syncthreads();
-      for (int idx = tid; idx < crows * n; idx += kTcThreads) yq[idx] = stage[(idx / n) * (n + 1) + idx % n];
-      __syncthreads();  // the stage (A buffers) is free for the next chunk
     }
+    tc_fence_before();
+    __syncthreads();
+    {
+      const float* qs = ybuf[s];
+      for (int r = warp; r < crows; r += kTcThreads / 32)
+        for (int col = lane; col < n; col += 32) yq[r * n + col] = qs[r * (n + 1) + col];
+    }
+    fence_proxy_async_smem();  // generic reads of this buffer before its next bulk copy
+    __syncthreads();
+    if (nt < 0) break;
+    t = nt;
+    c0 = nc0;
+    body_cur = body_next;
   }
+  // copies still in flight after an error: wait for them (bounded) before
+  // the shared memory is released
+  for (int s = 0; s < 2; ++s)
+    if (!ok && pend[s]) mbar_wait_bounded(lbar + s, lph[s]);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
