@@ -29,8 +29,10 @@ cudaError_t launch_rowmul_f64(const KernelCfg&, const void*, const double*, cons
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f32(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
-cudaError_t launch_gram_f64(const void*, const void*, int64_t, int, int, int, int, double*, int32_t*, cudaStream_t);
-cudaError_t launch_gram_f32(const void*, const void*, int64_t, int, int, int, int, double*, int32_t*, cudaStream_t);
+cudaError_t launch_gram_f64(const void*, const void*, int64_t, int, int, int, int, int, double*, int32_t*,
+                            cudaStream_t);
+cudaError_t launch_gram_f32(const void*, const void*, int64_t, int, int, int, int, int, double*, int32_t*,
+                            cudaStream_t);
 
 cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, const void* Y,
                           const double* M2, int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,
@@ -42,8 +44,8 @@ cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, c
 cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n, double* part, double* G,
                         int32_t* status, cudaStream_t st) {
   const GramGeom g = gram_geom(m, n, esz);
-  cudaError_t e = esz == 8 ? launch_gram_f64(X, Y, m, n, g.chunk, g.grid, g.nt, part, status, st)
-                           : launch_gram_f32(X, Y, m, n, g.chunk, g.grid, g.nt, part, status, st);
+  cudaError_t e = esz == 8 ? launch_gram_f64(X, Y, m, n, g.chunk, g.grid, g.nt, g.tile, part, status, st)
+                           : launch_gram_f32(X, Y, m, n, g.chunk, g.grid, g.nt, g.tile, part, status, st);
   if (e != cudaSuccess) return e;
   return launch_gram_reduce(part, g.grid, n, G, status, st);
 }
@@ -207,12 +209,15 @@ tsqr_status run_r_only(const Plan& P, int esz, const void* X, double* R, void* w
   return TSQR_OK;
 }
 
-// out = X M1 (+ Y M2) over the row blocks of the Step-1 configuration.
+// out = X M1 (+ Y M2): one input over the row blocks of the Step-1
+// configuration; two inputs with the tile sized for two staged inputs.
 tsqr_status rowmul(const Plan& P, const void* X, const double* M1, const void* Y, const double* M2, void* out,
                    int32_t* status, cudaStream_t st) {
-  const int64_t b = (X && Y) ? P.cfg0.rm_rows / 2 : P.cfg0.rm_rows;
+  const bool two = X && Y;
+  const KernelCfg& k = two ? P.cfg_rm2 : P.cfg0;
+  const int64_t b = two ? P.b_rm2 : P.cfg0.rm_rows;
   const int64_t p = (P.m + b - 1) / b;
-  return launch_rowmul(P.cfg0, X, M1, Y, M2, P.m, (int)P.n, b, p, out, status, st) == cudaSuccess
+  return launch_rowmul(k, X, M1, Y, M2, P.m, (int)P.n, b, p, out, status, st) == cudaSuccess
              ? TSQR_OK
              : TSQR_ERR_CUDA;
 }

@@ -34,7 +34,7 @@ cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n,
                         int32_t* status, cudaStream_t st);
 
 // Gram launch geometry shared by the planner and the launcher.
-struct GramGeom { int chunk, grid, nt; };
+struct GramGeom { int chunk, grid, nt, tile; };
 GramGeom gram_geom(int64_t m, int n, int esz);
 
 }  // namespace tsqr

@@ -87,8 +87,10 @@ GramGeom gram_geom(int64_t m, int n, int esz) {
   g.chunk = (int)chunk;
   const int64_t nchunks = (m + chunk - 1) / chunk;
   g.grid = (int)(nchunks < kMaxGramParts ? nchunks : kMaxGramParts);
-  const int nt4 = (n + 3) / 4;
-  int nt = (nt4 * nt4 + 31) / 32 * 32;
+  const int n4 = (n + 3) / 4, n5 = (n + 4) / 5;
+  g.tile = (n5 * n5 * 25 < n4 * n4 * 16) ? 5 : 4;  // fewer padded products
+  const int nt1 = g.tile == 5 ? n5 : n4;
+  int nt = (nt1 * nt1 + 31) / 32 * 32;
   g.nt = nt < 256 ? 256 : (nt > 1024 ? 1024 : nt);
   return g;
 }
@@ -146,6 +148,20 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   if (f < 2 || f > fmax) return TSQR_ERR_SHAPE;
 
   P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcMaxN;
+  {
+    const int kind_rm = esz == 4 ? kKindF32 : kKindF64;
+    const int NPAD = (int)((n + kNpc - 1) / kNpc) * kNpc;
+    int64_t b2 = 32;
+    while (RowMulSmem((int)(2 * (b2 + 32)), (int)n, NPAD, esz, esz).total <= kSmemMax) b2 += 32;
+    if (RowMulSmem((int)(2 * b2), (int)n, NPAD, esz, esz).total > kSmemMax) return TSQR_ERR_SHAPE;
+    // the smallest tile holding b2 rows, else (small n) the largest tile
+    if (!choose_cfg(kind_rm, (int)n, &P.cfg_rm2, b2, kPolicyStep1) &&
+        !choose_cfg(kind_rm, (int)n, &P.cfg_rm2, 0, kPolicyLargest))
+      return TSQR_ERR_SHAPE;
+    P.b_rm2 = P.cfg_rm2.B < b2 ? P.cfg_rm2.B : b2;
+    P.cfg_rm2.rm_rows = (int)(2 * P.b_rm2);
+    P.cfg_rm2.smem_rm = RowMulSmem(P.cfg_rm2.rm_rows, (int)n, NPAD, esz, esz).total;
+  }
   Level l0;
   l0.rows = m;
   l0.b = b0;

@@ -60,6 +60,10 @@ struct Plan {
   KernelCfg cfg0;        // Step-1 kernel config (dtype of A)
   KernelCfg cfg64;       // tree kernel config (binary64)
   bool tc3 = false;      // Step 3 on the tensor cores (3xTF32, binary32 data, n <= 64)
+  // k_rowmul with two inputs (the adjoint): a register tile close to the
+  // b_rm2 rows per block whose two inputs fit in shared memory together
+  KernelCfg cfg_rm2;
+  int64_t b_rm2 = 0;
   std::vector<Level> levels;  // levels[0] = Step 1; levels[1..] = tree
   size_t off_ctop = 0;   // n x n binary64 top coefficient (sign matrix, or D U_R)
   size_t off_small = 0;  // scratch for small n x n work (SVD, Cholesky, ...)

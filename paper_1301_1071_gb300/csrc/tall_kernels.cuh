@@ -15,12 +15,12 @@
 
 namespace tsqr {
 
-constexpr int kGramTile = 4;  // each thread accumulates a 4 x 4 tile of X^T Y
-
+// Each thread accumulates a TG x TG tile of X^T Y; TG (4 or 5) is chosen per
+// n to waste the fewest padded products (n = 25: 5, n = 64: 4).
 // X, Y: m x n (storage S).  Rows are processed in chunks of `chunk` rows,
 // chunks dealt to CTAs round-robin.  part: gridDim.x blocks of n x n binary64.
 // Y == X is allowed (symmetric use).  Dynamic smem: 2 * chunk * n * sizeof(S) + 16.
-template <class S>
+template <class S, int TG>
 __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t m, int n, int chunk,
                        double* __restrict__ part, int32_t* status) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -28,17 +28,17 @@ __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t
   S* sy = reinterpret_cast<S*>(smem + align_up((size_t)chunk * n * sizeof(S), 16));
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * align_up((size_t)chunk * n * sizeof(S), 16));
   const bool same = (X == Y);
-  const int nt = (n + kGramTile - 1) / kGramTile;
+  const int nt = (n + TG - 1) / TG;
   const int ntiles = nt * nt;
   const int NG = blockDim.x / ntiles > 0 ? blockDim.x / ntiles : 1;  // row groups
   const int tile = threadIdx.x % ntiles, g = threadIdx.x / ntiles;
   const bool active = threadIdx.x < ntiles * NG;
-  const int k0 = (tile / nt) * kGramTile, l0 = (tile % nt) * kGramTile;
-  double acc[kGramTile][kGramTile];
+  const int k0 = (tile / nt) * TG, l0 = (tile % nt) * TG;
+  double acc[TG][TG];
 #pragma unroll
-  for (int i = 0; i < kGramTile; ++i)
+  for (int i = 0; i < TG; ++i)
 #pragma unroll
-    for (int j = 0; j < kGramTile; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TG; ++j) acc[i][j] = 0.0;
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -57,16 +57,16 @@ __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t
     const S* ys = same ? sx : sy;
     if (active) {
       for (int r = g; r < rows; r += NG) {
-        double xv[kGramTile], yv[kGramTile];
+        double xv[TG], yv[TG];
 #pragma unroll
-        for (int i = 0; i < kGramTile; ++i) {
+        for (int i = 0; i < TG; ++i) {
           xv[i] = (k0 + i < n) ? static_cast<double>(sx[r * n + k0 + i]) : 0.0;
           yv[i] = (l0 + i < n) ? static_cast<double>(ys[r * n + l0 + i]) : 0.0;
         }
 #pragma unroll
-        for (int i = 0; i < kGramTile; ++i)
+        for (int i = 0; i < TG; ++i)
 #pragma unroll
-          for (int j = 0; j < kGramTile; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
+          for (int j = 0; j < TG; ++j) acc[i][j] = fma(xv[i], yv[j], acc[i][j]);
       }
     }
     __syncthreads();
@@ -79,9 +79,9 @@ __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t
   if (need <= have) {
     if (active) {
 #pragma unroll
-      for (int i = 0; i < kGramTile; ++i)
+      for (int i = 0; i < TG; ++i)
 #pragma unroll
-        for (int j = 0; j < kGramTile; ++j)
+        for (int j = 0; j < TG; ++j)
           if (k0 + i < n && l0 + j < n) red[(size_t)g * n * n + (k0 + i) * n + (l0 + j)] = acc[i][j];
     }
     __syncthreads();
@@ -97,9 +97,9 @@ __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t
     for (int gg = 0; gg < NG; ++gg) {
       if (active && g == gg) {
 #pragma unroll
-        for (int i = 0; i < kGramTile; ++i)
+        for (int i = 0; i < TG; ++i)
 #pragma unroll
-          for (int j = 0; j < kGramTile; ++j)
+          for (int j = 0; j < TG; ++j)
             if (k0 + i < n && l0 + j < n) P[(k0 + i) * n + (l0 + j)] += acc[i][j];
       }
       __syncthreads();

@@ -27,7 +27,7 @@
 namespace tsqr {
 
 constexpr int kTcM = 128;        // rows per MMA chunk (TMEM lanes)
-constexpr int kTcThreads = 256;  // 8 warps: warp w reads TMEM lanes 32 (w % 4) ..
+constexpr int kTcThreads = 512;  // 16 warps: warp w reads TMEM lanes 32 (w % 4) ..
 constexpr int kTcMaxN = 64;      // largest n on this path
 constexpr int kTcMaxE = (kTcMaxN * kTcMaxN + kTcThreads - 1) / kTcThreads;  // W entries per thread
 
@@ -338,15 +338,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (tid == 0) set_status(status, TSQR_ERR_TIMEOUT);
       break;
     }
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows of the chunk),
-    //      columns [h N / 2, (h + 1) N / 2) with h = w / 4; Q rows into the
-    //      chunk's Y buffer at stride n + 1
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows of the chunk)
+    //      and the h = w / 4 th group of cw columns (cw a multiple of 8: some
+    //      groups are empty for small N); Q rows into the chunk's Y buffer at
+    //      stride n + 1
     {
       float* qs = ybuf[s];
       const int q = warp & 3, h = warp >> 2;
+      const int cw = ((N / 4 + 7) / 8) * 8;
+      const int cend = (h + 1) * cw < N ? (h + 1) * cw : N;
       const int r = 32 * q + lane;
       const int rt = c0 + r;  // row within the tile
-      for (int col0 = h * (N / 2); col0 < (h + 1) * (N / 2); col0 += 8) {
+      for (int col0 = h * cw; col0 < cend; col0 += 8) {
         uint32_t v[8];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"

@@ -89,3 +89,12 @@ def test_workspace_tiled_blocks(lib):
 def test_workspace_size_rejects(lib, m, n, dt, b, f, want):
     st, _ = _ws(lib, 0, m, n, dt, b, f)
     assert st == want
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_plans_for_every_n(lib, dt):
+    """Every op has a plan (tile choice, tree, workspace) for n = 1 .. NMAX."""
+    for n in range(1, 101):
+        for op in range(5):
+            st, b = _ws(lib, op, 300_000, n, dt)
+            assert st == 0 and b > 0, (op, n, st)
