@@ -496,12 +496,13 @@ def config_extras(T, torch, dev, steps=3):
         c = torch.logspace(0, -4, n, dtype=torch.float64, device=dev)
         A32 = (torch.randn(m, n, dtype=torch.float32, device=dev, generator=g) * c.float())
         entry = {"workload": "50,000,000x50 FP32, N(0,1) x column factors 1..1e-4"}
-        Q, R = T.direct(A32)
-        ms = timed(lambda: T.direct(A32, check=False))
-        entry["fp32"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Q),
-                         "residual_F": resid(A32, Q, R),
-                         "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9}
-        del Q
+        for key, prec in (("fp32", "native"), ("fp32_tf32x3", "tf32x3")):
+            Q, R = T.direct(A32, prec=prec)
+            ms = timed(lambda: T.direct(A32, check=False, prec=prec))
+            entry[key] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Q),
+                          "residual_F": resid(A32, Q, R),
+                          "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9}
+            del Q
         A64 = A32.double()
         del A32
         Q, R = T.direct(A64)
@@ -554,6 +555,9 @@ def config_extras(T, torch, dev, steps=3):
             Q, R = T.direct(A, block_rows=4096)
             entry[name] = {"fwd_bwd_rows_s": m / (ms * 1e-3), "fwd_bwd_ms": ms, "fwd_rows_s": m / (msf * 1e-3),
                            "orth_error_2": orth(Q)}
+            if dt == torch.float32:
+                mst = timed(lambda: T.direct(A, block_rows=4096, check=False, prec="tf32x3"))
+                entry[name]["fwd_rows_s_tf32x3"] = m / (mst * 1e-3)
             del A, WQ, Q
         out["grad_4Mx64"] = entry
     except Exception as e:

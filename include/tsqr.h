@@ -183,8 +183,9 @@ tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const 
  * implicit device synchronisation of cudaMalloc/cudaFree, or plain C code
  * without a device allocator.
  *  - Limit: the problem's tsqr_workspace_size(TSQR_OP_DIRECT, ...) must not
- *    exceed TSQR_STATIC_WORK_BYTES (16 MiB; e.g. about 1.2 million rows at
- *    n = 25 in FP64); larger problems get TSQR_ERR_WORKSPACE before any launch.
+ *    exceed TSQR_STATIC_WORK_BYTES (16 MiB; e.g. about 390,000 rows at
+ *    n = 25 in FP64 with the default plan); larger problems get
+ *    TSQR_ERR_WORKSPACE before any launch.
  *  - Every GPU that loads the library holds the array until the process exits.
  *  - The first call on each device (with that device current) looks up the
  *    array's device address; make that first call before any stream capture.

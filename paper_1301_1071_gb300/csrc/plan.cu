@@ -28,6 +28,15 @@ static const TileChoice kTiles64[kNumTiles] = {
 static const TileChoice kTiles32[kNumTiles] = {
     {32, 256, false}, {20, 384, false}, {12, 512, false}, {8, 640, false}, {16, 640, true}};
 
+// Registers a thread may use under __launch_bounds__(maxt, 1): each of the
+// 4 sub-partitions holds 16K registers for ceil(maxt / 128) warps.
+static int reg_cap(int maxt) {
+  const int w = (maxt + 127) / 128;
+  int r = 16384 / (32 * w) / 8 * 8;
+  return r > 255 ? 255 : r;
+}
+constexpr size_t kSmemPerSM = 233472;  // 228 KB per SM, 1 KB of it reserved per CTA
+
 // Picks the register tile and row-group count.  want_b > 0: the smallest
 // capacity B >= want_b (ties: the taller register tile); want_b == 0: the
 // default policy below.
@@ -56,6 +65,11 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
       int rm_rows = B;  // k_rowmul also stages two n x NPAD matrices: shrink its stage
       while (rm_rows > 32 && RowMulSmem(rm_rows, n, NPAD, esz, esz).total > kSmemMax) rm_rows -= 32;
       if (RowMulSmem(rm_rows, n, NPAD, esz, esz).total > kSmemMax) continue;
+      // CTAs of k_local_qr per SM (register cap of the tile, shared memory)
+      int ctas = 65536 / (NT * reg_cap(tiles[ti].maxt));
+      const int by_smem = (int)(kSmemPerSM / (a + 1024));
+      ctas = ctas < by_smem ? ctas : by_smem;
+      ctas = ctas < 1 ? 1 : (ctas > 4 ? 4 : ctas);
       bool take;
       if (want_b > 0) {
         take = B >= want_b && (best.B == 0 || B < best.B || (B == best.B && R > best.R));
@@ -63,13 +77,16 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
         take = B > best.B;  // largest row block wins; ties keep the earlier tile
       } else {
         // Step 1: the largest block (the fixed per-column cost of the
-        // Householder loop is spread over more rows); ties: fewer threads
+        // Householder loop, and the per-tile cost of blocks of several tiles,
+        // are spread over more rows; measured better than two smaller CTAs
+        // per SM); ties: fewer threads
         take = best.B == 0 || B > best.B || (B == best.B && NT < best.NT);
       }
       if (take) {
         best.npc = kNpc; best.R = R; best.CS = CS; best.NRG = NRG; best.NT = NT; best.B = B;
         best.smem_qr = a; best.smem_fq = f; best.tile = ti; best.fq_rows = fq_rows;
         best.rm_rows = rm_rows; best.smem_rm = RowMulSmem(rm_rows, n, NPAD, esz, esz).total;
+        best.ctas = ctas;
       }
     }
   }
@@ -128,12 +145,13 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
     if (sms < 1) sms = kDefaultSMs;
     const int64_t kmax = kind0 == kKindDF64 ? kMaxTilesDF64 : (kind0 == kKindF32 ? kMaxTilesF32 : kMaxTiles);
     const int64_t bmax = B0 + (kmax - 1) * bt;
-    if (m <= (int64_t)kMinWaves * sms * B0) {
+    if (m <= (int64_t)kMinWaves * sms * P.cfg0.ctas * B0) {
       b0 = B0;
     } else {
-      int64_t waves = (m + (int64_t)sms * bmax - 1) / ((int64_t)sms * bmax);
+      const int64_t slots = (int64_t)sms * P.cfg0.ctas;  // CTAs resident at once
+      int64_t waves = (m + slots * bmax - 1) / (slots * bmax);
       if (waves < kMinWaves) waves = kMinWaves;
-      const int64_t p = waves * sms;
+      const int64_t p = waves * slots;
       b0 = (m + p - 1) / p;
       b0 = (b0 + al - 1) / al * al;  // blocks start on 16-byte boundaries
     }

@@ -29,6 +29,7 @@ struct KernelCfg {
   int fq_rows = 0;  // rows per staged chunk of k_form_q (<= B)
   int rm_rows = 0;  // staged rows per CTA of k_rowmul (<= B; halves hold two inputs)
   size_t smem_rm = 0;
+  int ctas = 1;     // CTAs of k_local_qr resident per SM (registers, shared memory)
 };
 
 // Default tile policies: kPolicyStep1 takes the largest spill-free register
