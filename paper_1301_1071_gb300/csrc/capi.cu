@@ -29,9 +29,9 @@ cudaError_t launch_rowmul_f64(const KernelCfg&, const void*, const double*, cons
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f32(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
-cudaError_t launch_gram_f64(const void*, const void*, int64_t, int, int, int, int, int, double*, int32_t*,
+cudaError_t launch_gram_f64(const void*, const void*, int64_t, int, int, int, int, int, bool, double*, int32_t*,
                             cudaStream_t);
-cudaError_t launch_gram_f32(const void*, const void*, int64_t, int, int, int, int, int, double*, int32_t*,
+cudaError_t launch_gram_f32(const void*, const void*, int64_t, int, int, int, int, int, bool, double*, int32_t*,
                             cudaStream_t);
 
 cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, const void* Y,
@@ -42,10 +42,11 @@ cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, c
 }
 
 cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n, double* part, double* G,
-                        int32_t* status, cudaStream_t st) {
+                        int32_t* status, cudaStream_t st, bool acc_storage) {
   const GramGeom g = gram_geom(m, n, esz);
-  cudaError_t e = esz == 8 ? launch_gram_f64(X, Y, m, n, g.chunk, g.grid, g.nt, g.tile, part, status, st)
-                           : launch_gram_f32(X, Y, m, n, g.chunk, g.grid, g.nt, g.tile, part, status, st);
+  cudaError_t e =
+      esz == 8 ? launch_gram_f64(X, Y, m, n, g.chunk, g.grid, g.nt, g.tile, acc_storage, part, status, st)
+               : launch_gram_f32(X, Y, m, n, g.chunk, g.grid, g.nt, g.tile, acc_storage, part, status, st);
   if (e != cudaSuccess) return e;
   return launch_gram_reduce(part, g.grid, n, G, status, st);
 }
@@ -449,7 +450,7 @@ tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const 
   double* M2 = G + 2 * nn;
   const int ni = static_cast<int>(n);
   TSQR_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
-  if (dQ) TSQR_CUDA(launch_gram(esz, dQ, Q, m, ni, part, G, status, st));  // G = dQ^T Q
+  if (dQ) TSQR_CUDA(launch_gram(esz, dQ, Q, m, ni, part, G, status, st, esz == 4));  // G = dQ^T Q
   TSQR_CUDA(launch_bwd_prep(R, dR, dQ ? G : nullptr, ni, M1, M2, status, st));
   // dA = (dQ + Q copyltu(M)) R^{-T} = dQ R^{-T} + Q (copyltu(M) R^{-T})
   TSQR_TRY(rowmul(P, dQ, M1, Q, M2, dA, status, st));

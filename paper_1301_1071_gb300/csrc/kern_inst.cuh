@@ -93,10 +93,13 @@ cudaError_t TSQR_ROWMUL_NAME(const KernelCfg& k, const void* X, const double* M1
   }
 }
 
+// acc_storage: accumulate each CTA's partial Gram in the storage type (the
+// adjoint of binary32 data); else in binary64.
 cudaError_t TSQR_GRAM_NAME(const void* X, const void* Y, int64_t m, int n, int chunk, int grid, int nt, int tile,
-                           double* part, int32_t* status, cudaStream_t st) {
+                           bool acc_storage, double* part, int32_t* status, cudaStream_t st) {
   const size_t smem = 2 * align_up((size_t)chunk * n * sizeof(TSQR_S), 16) + 16;
-  auto fn = tile == 5 ? k_gram<TSQR_S, 5> : k_gram<TSQR_S, 4>;
+  auto fn = acc_storage ? (tile == 5 ? k_gram<TSQR_S, 5, TSQR_S> : k_gram<TSQR_S, 4, TSQR_S>)
+                        : (tile == 5 ? k_gram<TSQR_S, 5, double> : k_gram<TSQR_S, 4, double>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, nt, smem, st>>>(static_cast<const TSQR_S*>(X), static_cast<const TSQR_S*>(Y), m, n, chunk, part,

@@ -30,8 +30,10 @@ cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, c
                           const double* M2, int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,
                           cudaStream_t st);
 // Partial Grams X^T Y (grid partials of n x n binary64), then their fixed-order sum into G.
+// acc_storage: per-CTA partial Grams accumulate in the storage type (binary32
+// data: the FMA pipe); the cross-CTA sum is always binary64.
 cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n, double* part, double* G,
-                        int32_t* status, cudaStream_t st);
+                        int32_t* status, cudaStream_t st, bool acc_storage = false);
 
 // Gram launch geometry shared by the planner and the launcher.
 struct GramGeom { int chunk, grid, nt, tile; };

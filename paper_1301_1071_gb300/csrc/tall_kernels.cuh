@@ -15,12 +15,14 @@
 
 namespace tsqr {
 
-// Each thread accumulates a TG x TG tile of X^T Y; TG (4 or 5) is chosen per
-// n to waste the fewest padded products (n = 25: 5, n = 64: 4).
+// Each thread accumulates a TG x TG tile of X^T Y in type A (binary64, or
+// binary32 for the adjoint of binary32 data: the per-CTA partial Grams are
+// then summed in binary64); TG (4 or 5) is chosen per n to waste the fewest
+// padded products (n = 25: 5, n = 64: 4).
 // X, Y: m x n (storage S).  Rows are processed in chunks of `chunk` rows,
 // chunks dealt to CTAs round-robin.  part: gridDim.x blocks of n x n binary64.
 // Y == X is allowed (symmetric use).  Dynamic smem: 2 * chunk * n * sizeof(S) + 16.
-template <class S, int TG>
+template <class S, int TG, class A>
 __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t m, int n, int chunk,
                        double* __restrict__ part, int32_t* status) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -34,11 +36,11 @@ __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t
   const int tile = threadIdx.x % ntiles, g = threadIdx.x / ntiles;
   const bool active = threadIdx.x < ntiles * NG;
   const int k0 = (tile / nt) * TG, l0 = (tile % nt) * TG;
-  double acc[TG][TG];
+  A acc[TG][TG];
 #pragma unroll
   for (int i = 0; i < TG; ++i)
 #pragma unroll
-    for (int j = 0; j < TG; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TG; ++j) acc[i][j] = A(0);
 
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -57,11 +59,11 @@ __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t
     const S* ys = same ? sx : sy;
     if (active) {
       for (int r = g; r < rows; r += NG) {
-        double xv[TG], yv[TG];
+        A xv[TG], yv[TG];
 #pragma unroll
         for (int i = 0; i < TG; ++i) {
-          xv[i] = (k0 + i < n) ? static_cast<double>(sx[r * n + k0 + i]) : 0.0;
-          yv[i] = (l0 + i < n) ? static_cast<double>(ys[r * n + l0 + i]) : 0.0;
+          xv[i] = (k0 + i < n) ? static_cast<A>(sx[r * n + k0 + i]) : A(0);
+          yv[i] = (l0 + i < n) ? static_cast<A>(ys[r * n + l0 + i]) : A(0);
         }
 #pragma unroll
         for (int i = 0; i < TG; ++i)
