@@ -14,7 +14,9 @@ template <int R, int MAXT>
 static cudaError_t local_qr_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
                               int64_t p, TSQR_S* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
   if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
-  auto fn = k_local_qr<TSQR_S, TSQR_T, kNpc, R, MAXT>;
+  // the look-ahead form when the tile is one row group
+  auto fn = k.NRG == 1 ? k_local_qr<TSQR_S, TSQR_T, kNpc, R, MAXT, true>
+                       : k_local_qr<TSQR_S, TSQR_T, kNpc, R, MAXT, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_qr);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)p, k.NT, k.smem_qr, st>>>(A, m, n, (int)b, (int)bt, kt, k.CS, k.NRG, Y, Rst, Tst, status);

@@ -24,10 +24,12 @@ struct LocalQrSmem {
     size_t gram_bytes = (size_t)n * n * tsz;
     if ((size_t)B * n * ssz < gram_bytes) o = align_up(stage + gram_bytes, 16);
     red = o; o = align_up(o + 2 * (size_t)NW * 32 * tsz, 16);  // double-buffered partials
-    xcol = o; o = align_up(o + 2 * (size_t)B * tsz, 16);      // double-buffered pivot column
+    // pivot column: double-buffered (several row groups) or triple-buffered
+    // (one row group, where a column's owner may run one column ahead)
+    xcol = o; o = align_up(o + 3 * (size_t)B * tsz, 16);
     piv = o; o = align_up(o + 2 * (size_t)NPAD * tsz, 16);    // double-buffered pivot row
     tau = o; o = align_up(o + (size_t)NPAD * tsz, 16);
-    refl = o; o = align_up(o + 8 * tsz, 16);                  // reflector scalars of the column
+    refl = o; o = align_up(o + 16 * tsz, 16);                 // reflector scalars, two columns
     nrm = o; o = align_up(o + 2 * 32 * (size_t)tsz, 16);     // look-ahead norms per row group
     bar = o; o = align_up(o + 16, 16);
     total = o;

@@ -178,6 +178,32 @@ __device__ __forceinline__ T col_norm2(const T (&a)[R][NPC], int rbase, int from
   }
 }
 
+// Phase A of a column: s[c] = sum over the thread's rows of x_q a[q][c]
+// (x is zero above the pivot row, so those rows add nothing).
+template <int NPC, int R, class T>
+__device__ __forceinline__ void column_dots(const T (&a)[R][NPC], const T* xcur, int rbase, T (&s)[NPC]) {
+  if constexpr (std::is_same<T, df64>::value) {
+    df64_acc acc[NPC];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const T xq = xcur[rbase + 32 * q];
+#pragma unroll
+      for (int c = 0; c < NPC; ++c) acc[c].add_prod(xq, a[q][c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NPC; ++c) s[c] = acc[c].value();
+  } else {
+#pragma unroll
+    for (int c = 0; c < NPC; ++c) s[c] = T(0);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const T xq = xcur[rbase + 32 * q];
+#pragma unroll
+      for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
+    }
+  }
+}
+
 // Trailing update of the thread's tile for column j, with the first trailing
 // local column C0 known at compile time: a[q][c] -= d[c] x_q for c >= C0.
 // The thread's rows are rbase + 32 q (q < R); the published pivot column x_j
@@ -214,6 +240,66 @@ __device__ __forceinline__ void tile_update(T (&a)[R][NPC], const T (&d)[NPC], c
   }
 }
 
+// Look-ahead form of tile_update for a tile held by one row group (every warp
+// holds all rows of its columns).  The warp owning column j + 1 updates that
+// column first, publishes x_{j+1} (zero above row j + 1), forms reflector
+// j + 1 from its squared norm and a_{j+1,j+1} (every lane, no broadcast),
+// stores the scalars in `refl_next` and arrives on the named barrier
+// `bar_next`; only then does it update its other trailing columns.  The other
+// warps can start column j + 1 while it finishes column j.
+template <int C0, int NPC, int R, class T>
+__device__ __forceinline__ void tile_update_la(T (&a)[R][NPC], const T (&d)[NPC], const T* xcur, T* xnext, int j,
+                                               int rbase, bool own_j, bool own_next, T scal, T* refl_next,
+                                               T* taus, int bar_next, int nthreads) {
+  if constexpr (C0 < NPC) {
+    if (own_next) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[q][C0] = fma(-d[C0], xcur[rbase + 32 * q], a[q][C0]);
+#pragma unroll
+      for (int q = 0; q < R; ++q) xnext[rbase + 32 * q] = (rbase + 32 * q > j) ? a[q][C0] : T(0);
+      const T ss = col_norm2<C0, NPC, R>(a, rbase, j + 1);
+      // a_{j+1,j+1}: register row (j + 1) / 32 < 4 of lane (j + 1) % 32
+      T al = T(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (rbase + 32 * q == j + 1) al = a[q][C0];
+      const Reflector<T> f = make_reflector(ss, shfl_from(al, (j + 1) & 31));
+      if ((threadIdx.x & 31) == 0) {
+        refl_next[0] = f.beta;
+        refl_next[1] = f.scal;
+        refl_next[2] = f.ib;
+        refl_next[3] = f.tau;
+        refl_next[4] = f.ident ? T(1) : T(0);
+        taus[j + 1] = f.tau;
+      }
+      __syncwarp();
+      named_bar_arrive(bar_next, nthreads);
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const T xq = xcur[rbase + 32 * q];
+#pragma unroll
+        for (int c = C0 + 1; c < NPC; ++c) a[q][c] = fma(-d[c], xq, a[q][c]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const T xq = xcur[rbase + 32 * q];
+#pragma unroll
+        for (int c = C0; c < NPC; ++c) a[q][c] = fma(-d[c], xq, a[q][c]);
+      }
+    }
+  }
+  if constexpr (C0 >= 1) {
+    if (own_j) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int r = rbase + 32 * q;
+        if (r > j) a[q][C0 - 1] = xcur[r] * scal;
+      }
+    }
+  }
+}
+
 // Y between Step 1 and Step 3 is kept in the compute format when that has the
 // storage's size (double-float pairs in place of binary64): no conversion.
 template <class S, class T>
@@ -235,9 +321,10 @@ using YStore = typename std::conditional<std::is_same<T, df64>::value, df64, S>:
 // Q_t [R'; 0].  The rows of R below its diagonal are zero and stay exactly
 // zero, so the Householder vectors of tile t are [I; V_t] and only V_t is
 // stored (over A_t's rows of Y).
+// LA (look-ahead form) is launched exactly when NRG == 1.
 // Launch: blockDim = 32*CS*NRG <= MAXT, gridDim = p, dynamic smem = LocalQrSmem.
 // ---------------------------------------------------------------------------
-template <class S, class T, int NPC, int R, int MAXT>
+template <class S, class T, int NPC, int R, int MAXT, bool LA>
 __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, int64_t m, int n, int b, int bt,
                                                        int kt, int CS, int NRG, S* Y, double* __restrict__ Rst,
                                                        double* __restrict__ Tst, int32_t* status) {
@@ -343,6 +430,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       for (int q = 0; q < R; ++q) xbuf[rbase + 32 * q] = a[q][0];
       const T ss = col_norm2<0, NPC, R>(a, rbase, 0);
       if (lane == 0) nrm[rg] = ss;
+      if (LA) {
+        // one row group: reflector 0 is formed here (the look-ahead loop
+        // below has no barrier for column 0)
+        const Reflector<T> f0 = make_reflector(ss, shfl_from(a[0][0], 0));
+        if (lane == 0) {
+          refl[0] = f0.beta;
+          refl[1] = f0.scal;
+          refl[2] = f0.ib;
+          refl[3] = f0.tau;
+          refl[4] = f0.ident ? T(1) : T(0);
+          taus[0] = f0.tau;
+        }
+      }
     }
     if (rg == 0 && lane == 0) {
 #pragma unroll
@@ -350,149 +450,229 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
     }
     __syncthreads();
 
-    for (int j = 0; j < n; ++j) {
-      const int jb = j & 1;
-      const T* xcur = xbuf + jb * B;          // x_j (column j, current values)
-      T* xnext = xbuf + (jb ^ 1) * B;         // x_{j+1}
-      const T* pcur = piv + jb * NPAD;        // row j
-      T* pnext = piv + (jb ^ 1) * NPAD;       // row j+1
-      T* rcur = red + jb * NW * 32;           // partial sums of this step
-      const T* ncur = nrm + jb * 32;          // squared norm of x_j per row group
-      T* nnext = nrm + (jb ^ 1) * 32;         // ... of x_{j+1}
+    if constexpr (LA) {
+      // ---- one row group: every warp holds all rows of its columns, so its
+      //      dot products are complete after a warp reduction and only x_j
+      //      and reflector j cross warps.  One named barrier per column
+      //      (ids 1 and 2 by the parity of j): the owner of column j arrives
+      //      once it has published them (during column j - 1), the other
+      //      warps wait.  There is no end-of-column CTA barrier, so a warp
+      //      may run one column ahead of the slowest: x_j is triple-buffered
+      //      and the reflector scalars double-buffered, so nothing is
+      //      overwritten before every warp has finished with it.
+      int jb3 = 0;  // j mod 3
+      for (int j = 0; j < n; ++j) {
+        const int jb = j & 1;
+        const int jn3 = jb3 == 2 ? 0 : jb3 + 1;
+        const T* xcur = xbuf + jb3 * B;   // x_j
+        T* xnext = xbuf + jn3 * B;        // x_{j+1}
+        const T* pcur = piv + jb * NPAD;  // row j (this warp's columns)
+        T* pnext = piv + (jb ^ 1) * NPAD;
+        T* rcur = red + jb * NW * 32;     // this warp's column sums
+        const bool owner = (cs == j % CS);
+        if (j > 0 && !owner) named_bar_sync(1 + jb, NT);
+        const T* rf = refl + jb * 8;
+        Reflector<T> f;
+        f.beta = rf[0];
+        f.scal = rf[1];
+        f.ib = rf[2];
+        f.tau = rf[3];
+        f.ident = rf[4] != T(0);
 
-      // ---- the reflector of column j, from the look-ahead squared norm of x_j
-      //      and alpha = a_jj: formed by the warp of row group 0 that owns
-      //      column j, published before its dot products so that its scalar
-      //      sequence overlaps the other warps' phase A
-      Reflector<T> f;
-      const bool owner = (rg == 0) && (cs == j % CS);
-      if (owner) {
-        if (lane == 0) {
-          T Sj = T(0);
-          for (int g = 0; g < NRG; ++g) Sj += ncur[g];
-          f = make_reflector(Sj, pcur[j]);
-          refl[0] = f.beta;
-          refl[1] = f.scal;
-          refl[2] = f.ib;
-          refl[3] = f.tau;
-          refl[4] = f.ident ? T(1) : T(0);
-          taus[j] = f.tau;
+        // phase A: s = x_j^T A for this warp's columns
+        {
+          T s[NPC];
+          column_dots(a, xcur, rbase, s);
+          TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
         }
         __syncwarp();
-        if (NRG == 1) named_bar_arrive(1, NT);  // producer: the scalars are out
-        f.beta = shfl_bcast(f.beta);
-        f.scal = shfl_bcast(f.scal);
-        f.ib = shfl_bcast(f.ib);
-        f.tau = shfl_bcast(f.tau);
-        f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
-      }
 
-      // ---- phase A: s = x_j^T A over the thread's rows (rows < j give 0), CTA partials
-      {
-        T s[NPC];
-        if constexpr (std::is_same<T, df64>::value) {
-          df64_acc acc[NPC];
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            const T xq = xcur[rbase + 32 * q];  // zero above row j
-#pragma unroll
-            for (int c = 0; c < NPC; ++c) acc[c].add_prod(xq, a[q][c]);
-          }
-#pragma unroll
-          for (int c = 0; c < NPC; ++c) s[c] = acc[c].value();
-        } else {
-#pragma unroll
-          for (int c = 0; c < NPC; ++c) s[c] = T(0);
-#pragma unroll
-          for (int q = 0; q < R; ++q) {
-            const T xq = xcur[rbase + 32 * q];  // zero above row j
-#pragma unroll
-            for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
-          }
-        }
-        TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
-      }
-      // one row group: each warp's column sums are its own (a warp sync
-      // suffices) and only the reflector crosses warps; several row groups:
-      // the partial sums cross warps too
-      if (NRG == 1) {
-        __syncwarp();
-        if (!owner) named_bar_sync(1, NT);
-      } else {
-        __syncthreads();
-      }
-      if (!owner) {
-        f.beta = refl[0];
-        f.scal = refl[1];
-        f.ib = refl[2];
-        f.tau = refl[3];
-        f.ident = refl[4] != T(0);
-      }
-
-      // ---- phase B: lane c < NPC sums the partials of its column c over the
-      //      row groups, then forms R's r_jk = S_k / beta (r_jj = beta),
-      //      d_c = (a_jk - r_jk) / (alpha - beta) and, for k < j, the Gram
-      //      entry v_k^T v_j of the compact-WY T; every lane takes d and r_j
-      //      by shuffle
-      T d[NPC], rj[NPC];
-      {
-        T dl = T(0), rl = T(0);
-        const int mycol = cs + lane * CS;
-        if (lane < NPC && mycol < n) {
-          T Sc = T(0);
-          for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
-          const T pc = pcur[mycol];
-          if (mycol > j) {
-            rl = Sc * f.ib;
-            dl = (pc - rl) * f.scal;
-          } else if (mycol == j) {
-            rl = f.beta;
-          } else if (rg == 0) {
-            gram[mycol * n + j] = f.scal * (Sc - f.beta * pc);
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < NPC; ++c) {
-          d[c] = shfl_from(dl, c);
-          rj[c] = shfl_from(rl, c);
-        }
-      }
-
-      // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
-      const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
-      const bool own_j = (cs == j % CS);
-      const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
-      switch (c0) {
-        case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-        case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-        case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-        case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-        case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-        default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-      }
-      // rows j and j+1 (< n <= 128) are register rows q < 4 of row group 0:
-      // the thread holding row j writes R's row j, the one holding row j+1
-      // publishes it (after this step's update)
-      if (!f.ident) {
-#pragma unroll
-        for (int q = 0; q < QH; ++q)
-          if (rbase + 32 * q == j) {
-#pragma unroll
-            for (int c = 0; c < NPC; ++c) {
-              const int col = cs + c * CS;
-              if (col >= j && col < n) a[q][c] = rj[c];
+        // phase B: as in the general loop, with one row group
+        T d[NPC], rj[NPC];
+        {
+          T dl = T(0), rl = T(0);
+          const int mycol = cs + lane * CS;
+          if (lane < NPC && mycol < n) {
+            const T Sc = rcur[warp * 32 + lane];
+            const T pc = pcur[mycol];
+            if (mycol > j) {
+              rl = Sc * f.ib;
+              dl = (pc - rl) * f.scal;
+            } else if (mycol == j) {
+              rl = f.beta;
+            } else {
+              gram[mycol * n + j] = f.scal * (Sc - f.beta * pc);
             }
           }
-      }
-      if (j + 1 < n) {
 #pragma unroll
-        for (int q = 0; q < QH; ++q)
-          if (rbase + 32 * q == j + 1) {
-#pragma unroll
-            for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
+          for (int c = 0; c < NPC; ++c) {
+            d[c] = shfl_from(dl, c);
+            rj[c] = shfl_from(rl, c);
           }
+        }
+
+        // phase C: trailing update with the look-ahead of column j + 1
+        const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
+        const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
+        T* rfn = refl + (jb ^ 1) * 8;
+        const int bn = 1 + (jb ^ 1);
+        switch (c0) {
+          case 0: tile_update_la<0, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
+          case 1: tile_update_la<1, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
+          case 2: tile_update_la<2, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
+          case 3: tile_update_la<3, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
+          case 4: tile_update_la<4, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
+          default: tile_update_la<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
+        }
+        if (!f.ident) {
+#pragma unroll
+          for (int q = 0; q < QH; ++q)
+            if (rbase + 32 * q == j) {
+#pragma unroll
+              for (int c = 0; c < NPC; ++c) {
+                const int col = cs + c * CS;
+                if (col >= j && col < n) a[q][c] = rj[c];
+              }
+            }
+        }
+        if (j + 1 < n) {
+#pragma unroll
+          for (int q = 0; q < QH; ++q)
+            if (rbase + 32 * q == j + 1) {
+#pragma unroll
+              for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
+            }
+        }
+        __syncwarp();
+        jb3 = jn3;
       }
-      __syncthreads();
+      __syncthreads();  // gram and taus are read CTA-wide below
+    } else {
+      for (int j = 0; j < n; ++j) {
+        const int jb = j & 1;
+        const T* xcur = xbuf + jb * B;          // x_j (column j, current values)
+        T* xnext = xbuf + (jb ^ 1) * B;         // x_{j+1}
+        const T* pcur = piv + jb * NPAD;        // row j
+        T* pnext = piv + (jb ^ 1) * NPAD;       // row j+1
+        T* rcur = red + jb * NW * 32;           // partial sums of this step
+        const T* ncur = nrm + jb * 32;          // squared norm of x_j per row group
+        T* nnext = nrm + (jb ^ 1) * 32;         // ... of x_{j+1}
+
+        // ---- the reflector of column j, from the look-ahead squared norm of x_j
+        //      and alpha = a_jj: formed by the warp of row group 0 that owns
+        //      column j, published before its dot products so that its scalar
+        //      sequence overlaps the other warps' phase A
+        Reflector<T> f;
+        const bool owner = (rg == 0) && (cs == j % CS);
+        if (owner) {
+          if (lane == 0) {
+            T Sj = T(0);
+            for (int g = 0; g < NRG; ++g) Sj += ncur[g];
+            f = make_reflector(Sj, pcur[j]);
+            refl[0] = f.beta;
+            refl[1] = f.scal;
+            refl[2] = f.ib;
+            refl[3] = f.tau;
+            refl[4] = f.ident ? T(1) : T(0);
+            taus[j] = f.tau;
+          }
+          __syncwarp();
+          if (NRG == 1) named_bar_arrive(1, NT);  // producer: the scalars are out
+          f.beta = shfl_bcast(f.beta);
+          f.scal = shfl_bcast(f.scal);
+          f.ib = shfl_bcast(f.ib);
+          f.tau = shfl_bcast(f.tau);
+          f.ident = __shfl_sync(0xffffffffu, f.ident ? 1 : 0, 0) != 0;
+        }
+
+        // ---- phase A: s = x_j^T A over the thread's rows (rows < j give 0), CTA partials
+        {
+          T s[NPC];
+          column_dots(a, xcur, rbase, s);
+          TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
+        }
+        // one row group: each warp's column sums are its own (a warp sync
+        // suffices) and only the reflector crosses warps; several row groups:
+        // the partial sums cross warps too
+        if (NRG == 1) {
+          __syncwarp();
+          if (!owner) named_bar_sync(1, NT);
+        } else {
+          __syncthreads();
+        }
+        if (!owner) {
+          f.beta = refl[0];
+          f.scal = refl[1];
+          f.ib = refl[2];
+          f.tau = refl[3];
+          f.ident = refl[4] != T(0);
+        }
+
+        // ---- phase B: lane c < NPC sums the partials of its column c over the
+        //      row groups, then forms R's r_jk = S_k / beta (r_jj = beta),
+        //      d_c = (a_jk - r_jk) / (alpha - beta) and, for k < j, the Gram
+        //      entry v_k^T v_j of the compact-WY T; every lane takes d and r_j
+        //      by shuffle
+        T d[NPC], rj[NPC];
+        {
+          T dl = T(0), rl = T(0);
+          const int mycol = cs + lane * CS;
+          if (lane < NPC && mycol < n) {
+            T Sc = T(0);
+            for (int g = 0; g < NRG; ++g) Sc += rcur[(g * CS + cs) * 32 + lane];
+            const T pc = pcur[mycol];
+            if (mycol > j) {
+              rl = Sc * f.ib;
+              dl = (pc - rl) * f.scal;
+            } else if (mycol == j) {
+              rl = f.beta;
+            } else if (rg == 0) {
+              gram[mycol * n + j] = f.scal * (Sc - f.beta * pc);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) {
+            d[c] = shfl_from(dl, c);
+            rj[c] = shfl_from(rl, c);
+          }
+        }
+
+        // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
+        const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
+        const bool own_j = (cs == j % CS);
+        const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
+        switch (c0) {
+          case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+          case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+          case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+          case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+          case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+          default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
+        }
+        // rows j and j+1 (< n <= 128) are register rows q < 4 of row group 0:
+        // the thread holding row j writes R's row j, the one holding row j+1
+        // publishes it (after this step's update)
+        if (!f.ident) {
+#pragma unroll
+          for (int q = 0; q < QH; ++q)
+            if (rbase + 32 * q == j) {
+#pragma unroll
+              for (int c = 0; c < NPC; ++c) {
+                const int col = cs + c * CS;
+                if (col >= j && col < n) a[q][c] = rj[c];
+              }
+            }
+        }
+        if (j + 1 < n) {
+#pragma unroll
+          for (int q = 0; q < QH; ++q)
+            if (rbase + 32 * q == j + 1) {
+#pragma unroll
+              for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
+            }
+        }
+        __syncthreads();
+      }
     }
 
     if (Y != nullptr) {
