@@ -31,8 +31,8 @@ static cudaError_t form_q_R(const KernelCfg& k, const TSQR_S* Y, int64_t m, int 
   auto fn = k_form_q<TSQR_S, TSQR_T, kNpc, R, MAXT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fq);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)p, k.NT, k.smem_fq, st>>>(Y, m, n, (int)b, (int)bt, kt, k.fq_rows, k.CS, k.NRG, T, C, cblocks, Q,
-                                           status);
+  fn<<<(unsigned)p, k.NT, k.smem_fq, st>>>(Y, m, n, (int)b, (int)bt, kt, k.fq_rows, k.CS, k.NRG, k.skew, T, C,
+                                           cblocks, Q, status);
   return cudaGetLastError();
 }
 
@@ -75,7 +75,7 @@ static cudaError_t rowmul_R(const KernelCfg& k, const TSQR_S* X, const double* M
   const size_t smem = k.smem_rm;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)p, k.NT, smem, st>>>(X, M1, Y, M2, m, n, (int)b, k.rm_rows, k.CS, k.NRG, out, status);
+  fn<<<(unsigned)p, k.NT, smem, st>>>(X, M1, Y, M2, m, n, (int)b, k.rm_rows, k.CS, k.NRG, k.skew, out, status);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <numeric>
 
 #include "../../include/tsqr.h"
 #include "launch.h"
@@ -87,6 +88,11 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
         best.smem_qr = a; best.smem_fq = f; best.tile = ti; best.fq_rows = fq_rows;
         best.rm_rows = rm_rows; best.smem_rm = RowMulSmem(rm_rows, n, NPAD, esz, esz).total;
         best.ctas = ctas;
+        // lanes reading one column of consecutive rows (row stride n elements)
+        // fall into gcd(n words, 32) banks' worth of conflicts; 8-way or worse
+        // is worth the rotated order (which spreads the n x NPAD coefficient
+        // reads instead)
+        best.skew = std::gcd(n * esz / 4, 32) >= 8 ? 1 : 0;
       }
     }
   }

@@ -30,6 +30,11 @@ struct KernelCfg {
   int rm_rows = 0;  // staged rows per CTA of k_rowmul (<= B; halves hold two inputs)
   size_t smem_rm = 0;
   int ctas = 1;     // CTAs of k_local_qr resident per SM (registers, shared memory)
+  // k_form_q / k_rowmul walk the columns of their staged rows in a per-lane
+  // rotated order (lane l starts at column l mod n): with a row stride of n
+  // elements the lanes of a warp (consecutive rows) otherwise hit the same
+  // shared-memory bank when n x element size is a multiple of 32 bytes
+  int skew = 0;
 };
 
 // Default tile policies: kPolicyStep1 takes the largest spill-free register

@@ -758,12 +758,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
 //   Qg  : output m x n (storage S); may alias Yg.
 // The n x n operands stream through the stage in row chunks; each thread
 // keeps its (at most kMaxE) entries of an n x NPAD product in registers.
+// skew != 0: lane l takes the columns kk of its staged rows in the order
+// l mod n, l mod n + 1, ... (cyclic), so that the lanes' reads of one step
+// spread over the banks (the sum is the same up to rounding order).
 // ---------------------------------------------------------------------------
 constexpr int kMaxE = 16;  // n NPAD / (32 CS NRG) = 5 n / (32 NRG) <= 16 for n <= 100
 
 template <class S, class T, int NPC, int R, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int n, int b, int bt, int kt, int srows,
-                                                     int CS, int NRG, const double* __restrict__ Tg,
+                                                     int CS, int NRG, int skew, const double* __restrict__ Tg,
                                                      const double* __restrict__ Cg, int64_t cblocks, S* Qg,
                                                      int32_t* status) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -885,7 +888,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
           acc[q][c] = (top && r < ntop && kc < n) ? Xm[r * NPAD + kc] : T(0);
         }
       }
-      for (int kk = 0; kk < n; ++kk) {
+      int kk = skew ? lane % n : 0;
+      for (int step = 0; step < n; ++step, kk = (kk + 1 == n) ? 0 : kk + 1) {
         T wk[NPC];
 #pragma unroll
         for (int c = 0; c < NPC; ++c) wk[c] = Wm[kk * NPAD + cs + c * CS];

@@ -116,7 +116,7 @@ __global__ void k_gram(const S* __restrict__ X, const S* __restrict__ Y, int64_t
 template <class S, class T, int NPC, int R, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1)
     k_rowmul(const S* X, const double* __restrict__ M1, const S* Yin, const double* __restrict__ M2, int64_t m,
-             int n, int b, int srows, int CS, int NRG, S* out, int32_t* status) {
+             int n, int b, int srows, int CS, int NRG, int skew, S* out, int32_t* status) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
   const int B = 32 * NRG * R;
@@ -161,7 +161,10 @@ __global__ void __launch_bounds__(MAXT, 1)
   for (int q = 0; q < R; ++q)
 #pragma unroll
     for (int c = 0; c < NPC; ++c) acc[q][c] = T(0);
-  for (int k = 0; k < n; ++k) {
+  // skew != 0: lane l takes the columns in the cyclic order starting at
+  // l mod n (bank-conflict-free reads of one column of consecutive rows)
+  int k = skew ? lane % n : 0;
+  for (int step = 0; step < n; ++step, k = (k + 1 == n) ? 0 : k + 1) {
     if (X) {
       T w[NPC];
 #pragma unroll
