@@ -76,6 +76,9 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
         take = B >= want_b && (best.B == 0 || B < best.B || (B == best.B && R > best.R));
       } else if (policy == kPolicyLargest) {
         take = B > best.B;  // largest row block wins; ties keep the earlier tile
+      } else if (policy == kPolicyInFlight) {
+        const int64_t rows = (int64_t)B * ctas, best_rows = (int64_t)best.B * best.ctas;
+        take = best.B == 0 || rows > best_rows || (rows == best_rows && ctas > best.ctas);
       } else {
         // Step 1: the largest block (the fixed per-column cost of the
         // Householder loop, and the per-tile cost of blocks of several tiles,
@@ -131,9 +134,10 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   P.n = n;
   P.esz = esz;
   const int kind0 = esz == 4 ? kKindF32 : (prec == TSQR_PREC_DF64 ? kKindDF64 : kKindF64);
-  // Step-1 tile: the largest register tile; a smaller one when the caller's
-  // blocks fit in it
-  if (!choose_cfg(kind0, (int)n, &P.cfg0, 0, kPolicyStep1) ||
+  // Step-1 tile: the most rows resident per SM (double-float: the largest
+  // tile); a smaller one when the caller's blocks fit in it
+  const int policy0 = kind0 == kKindDF64 ? kPolicyStep1 : kPolicyInFlight;
+  if (!choose_cfg(kind0, (int)n, &P.cfg0, 0, policy0) ||
       !choose_cfg(kKindF64, (int)n, &P.cfg64, 0, kPolicyStep1, 2 * (int)n))
     return TSQR_ERR_SHAPE;
   if (block_rows > 0 && block_rows <= P.cfg0.B && !choose_cfg(kind0, (int)n, &P.cfg0, block_rows, kPolicyStep1))
@@ -156,7 +160,8 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
     } else {
       const int64_t slots = (int64_t)sms * P.cfg0.ctas;  // CTAs resident at once
       int64_t waves = (m + slots * bmax - 1) / (slots * bmax);
-      if (waves < kMinWaves) waves = kMinWaves;
+      const int64_t wmin = (kMinWaves + P.cfg0.ctas - 1) / P.cfg0.ctas;  // kMinWaves blocks per SM
+      if (waves < wmin) waves = wmin;
       const int64_t p = waves * slots;
       b0 = (m + p - 1) / p;
       b0 = (b0 + al - 1) / al * al;  // blocks start on 16-byte boundaries

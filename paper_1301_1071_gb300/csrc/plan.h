@@ -38,10 +38,14 @@ struct KernelCfg {
 };
 
 // Default tile policies: kPolicyStep1 takes the largest spill-free register
-// tile (ties: fewer threads; used for Step 1 and, with at least 2n rows so
-// that a node merges two or more R factors, for the tree); kPolicyLargest
-// takes the largest block.
-enum { kPolicyStep1 = 0, kPolicyLargest = 1 };
+// tile (ties: fewer threads; used for double-float Step 1 and, with at least
+// 2n rows so that a node merges two or more R factors, for the tree);
+// kPolicyLargest takes the largest block; kPolicyInFlight takes the most rows
+// resident per SM (B x CTAs per SM), ties going to more CTAs: two CTAs of one
+// row group each (the look-ahead loop) overlap their per-column barriers and
+// reductions, which one CTA of two row groups cannot (binary64 and binary32
+// Step 1).
+enum { kPolicyStep1 = 0, kPolicyLargest = 1, kPolicyInFlight = 2 };
 
 // Picks the register tile of kernel kind `kind` for n (want_b > 0: the
 // smallest per-CTA capacity that holds want_b rows; else `policy`).
@@ -81,14 +85,15 @@ struct Plan {
 
 constexpr int kSmallSlots = 8;  // n x n binary64 matrices in each small scratch area
 // Default Step-1 block height.  Small problems: one register tile per block.
-// Otherwise the number of blocks is a whole number (at least kMinWaves) of
-// waves of one CTA per SM, so that no wave runs part-empty, with blocks as
-// tall as kMaxTiles tiles allow: tall blocks keep the stack of R factors (and
-// so the Step-2 tree) small.  The flat tree inside a block adds rounding
-// error in proportion to its tiles, so double-float compute (unit roundoff
-// 2^-48) takes fewer of them.
+// Otherwise the number of blocks is a whole number of waves (CTAs resident
+// per SM x SMs), so that no wave runs part-empty, at least kMinWaves blocks
+// per SM, with blocks as tall as kMaxTiles tiles allow: tall blocks keep the
+// stack of R factors (and so the Step-2 tree) small -- at n = 25 the 608
+// R factors of 4 blocks per SM take a two-level tree of 25-way nodes.  The
+// flat tree inside a block adds rounding error in proportion to its tiles,
+// so double-float compute (unit roundoff 2^-48) takes fewer of them.
 constexpr int kMinWaves = 4;
-constexpr int kMaxTiles = 32;       // binary64 data
+constexpr int kMaxTiles = 64;       // binary64 data
 constexpr int kMaxTilesF32 = 128;   // binary32 data: its binary64 tree is costly, its rounding unit large
 constexpr int kMaxTilesDF64 = 8;
 constexpr int kDefaultSMs = 152;  // GB300
