@@ -74,6 +74,9 @@ SHAPES = [
     (150_001, 10, 12_345, 0), # last block of several tiles, last tile short
     (60_000, 50, 2999, 0),
     (30_000, 100, 1500, 0),   # many tiles of few rows (binary64: 28 per tile)
+    (30_000, 32, 2500, 0),    # carried R fills one 32-row register slice
+    (50_000, 33, 3000, 0),    # carried R padded to two slices (rows 33..63 zero)
+    (40_000, 64, 2000, 0),
     (1_000_003, 25, 0, 0),    # default block height (two tiles per block)
 ]
 
