@@ -85,7 +85,8 @@ typedef enum tsqr_op {
   TSQR_OP_SVD = 1,
   TSQR_OP_CHOLQR = 2,
   TSQR_OP_INDIRECT = 3,
-  TSQR_OP_BACKWARD = 4
+  TSQR_OP_BACKWARD = 4,
+  TSQR_OP_DIRECT_HOST = 5 /* tsqr_direct_host: its own row-block plan (copy chunks) */
 } tsqr_op;
 
 typedef struct tsqr_opts {
@@ -199,6 +200,36 @@ tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const 
 tsqr_status tsqr_direct_static(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
                                void* Q, int64_t ldq, double* R, int64_t ldr,
                                const tsqr_opts* opts, void* stream);
+
+/*
+ * Direct TSQR from and to HOST memory (Sec. III-B, Alg. 2), with the
+ * host<->device copies overlapped with the kernels.  The same computation as
+ * tsqr_direct on the device copy of A; the row blocks are taken in chunks of
+ * whole waves of CTAs: chunk c's rows of A are copied on `copy_stream` while
+ * Step 1 of chunk c - 1 runs on `stream`; after the tree (Step 2), Step 3
+ * forms chunk c's rows of Q on `stream` while chunk c - 1's rows are copied
+ * back on `copy_stream`.
+ *  - A (read-only), Q: HOST, m x n row-major, dtype (leading dimension n).
+ *    Page-locked memory lets the copies overlap the kernels; pageable memory
+ *    works, with the copies serialised by the runtime.
+ *  - R: HOST, n x n binary64, row-major, diag(R) >= 0.
+ *  - dbuf: DEVICE, m x n elements of dtype, 16-byte aligned, caller-owned:
+ *    holds A's rows, then Y (Step 1), then Q (Step 3), in place.
+ *  - work: DEVICE workspace of tsqr_workspace_size(TSQR_OP_DIRECT_HOST, ...)
+ *    bytes (its row-block plan differs from tsqr_direct's: the default block
+ *    height makes each chunk a whole number of waves).
+ *  - stream, copy_stream: two different CUDA streams of the current device.
+ *    On return everything is enqueued and `stream` has been made to wait for
+ *    the last copy on `copy_stream`: synchronising `stream` (or opts->sync = 1,
+ *    which also returns the device status) completes the call.
+ *  - The call creates and releases 2 x chunks + 1 CUDA events (no device
+ *    memory); chunks <= 8.
+ *  - Errors: as tsqr_direct (TSQR_ERR_ARG also for a NULL pointer or equal
+ *    streams).
+ */
+tsqr_status tsqr_direct_host(const void* A, int64_t m, int64_t n, int32_t dtype, void* Q, double* R,
+                             void* dbuf, void* work, size_t work_bytes, const tsqr_opts* opts,
+                             void* stream, void* copy_stream);
 
 /*
  * Number of kernel launches one call of `op` makes for this shape and opts

@@ -7,6 +7,7 @@ There is no CPU fallback -- the functions raise if the library or a CUDA
 device is unavailable.
 
     Q, R = direct(A)                 # Sec. III-B direct TSQR (Alg. 2 tree)
+    Qh, Rh = direct_host(Ah)         # same, host buffers, copies overlapped
     U, S, V = svd(A)                 # SVD variant, U = Q U_R
     Q, R = cholqr(A, refine=0)       # Cholesky QR (+ refinement)
     Q, R = indirect_refine(A, 1)     # indirect TSQR + refinement
@@ -21,7 +22,7 @@ import threading
 
 import torch
 
-__all__ = ["direct", "direct_static", "svd", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
+__all__ = ["direct", "direct_host", "direct_static", "svd", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
            "workspace_size", "launch_count", "library_path", "load", "STATUS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -31,7 +32,7 @@ _lib = None
 
 F64, F32 = 0, 1
 PREC = {"native": 0, "df64": 1, "tf32x3": 2}
-OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD = 0, 1, 2, 3, 4
+OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD, OP_DIRECT_HOST = 0, 1, 2, 3, 4, 5
 NMAX = 100
 STATUS = {0: "TSQR_OK", 1: "TSQR_ERR_ARG", 2: "TSQR_ERR_SHAPE", 3: "TSQR_ERR_ALIGN",
           4: "TSQR_ERR_WORKSPACE", 5: "TSQR_ERR_CUDA", 6: "TSQR_ERR_NOT_SPD", 7: "TSQR_ERR_SINGULAR",
@@ -70,6 +71,7 @@ def load():
             "tsqr_workspace_size": [I32, I64, I64, I32, OP, ctypes.POINTER(SZ)],
             "tsqr_direct": [P, I64, I64, I64, I32, P, I64, P, I64, P, SZ, OP, P],
             "tsqr_direct_static": [P, I64, I64, I64, I32, P, I64, P, I64, OP, P],
+            "tsqr_direct_host": [P, I64, I64, I32, P, P, P, P, SZ, OP, P, P],
             "tsqr_svd": [P, I64, I64, I64, I32, P, I64, P, P, I64, P, SZ, OP, P],
             "cholqr": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
             "tsqr_indirect_refine": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
@@ -184,6 +186,42 @@ def direct(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Te
                          ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_direct")
     _status(work, "tsqr_direct", check)
+    return Q, R
+
+
+def direct_host(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, out: tuple | None = None,
+                dbuf: torch.Tensor | None = None, work: torch.Tensor | None = None,
+                copy_stream: torch.cuda.Stream | None = None, device=None, check: bool = True,
+                prec: str = "native"):
+    """Direct TSQR of a HOST matrix A (CPU tensor, m x n, float64/float32;
+    page-locked for the copies to overlap the kernels): returns (Q, R) on the
+    host.  The rows go to the device in chunks on ``copy_stream`` while Step 1
+    runs on the current stream, and Q comes back chunk by chunk behind Step 3
+    (tsqr_direct_host).  ``dbuf`` (device, m x n) and ``work`` may be given
+    to avoid allocations; ``out`` = (Q, R) host tensors (pinned for overlap).
+    The current stream holds the whole call when it returns."""
+    if A.is_cuda or A.dim() != 2:
+        raise ValueError("A must be a 2-D host (CPU) tensor")
+    m, n = A.shape
+    if n < 1 or n > NMAX or m < n:
+        raise ValueError(f"unsupported shape {tuple(A.shape)}: need 1 <= n <= {NMAX} and m >= n")
+    A = A.contiguous()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    lib = load()
+    if out is not None:
+        Q, R = out
+    else:
+        Q = torch.empty(m, n, dtype=A.dtype, pin_memory=True)
+        R = torch.empty(n, n, dtype=torch.float64, pin_memory=True)
+    if dbuf is None:
+        dbuf = torch.empty(m, n, dtype=A.dtype, device=dev)
+    work = _workspace(OP_DIRECT_HOST, m, n, A.dtype, dev, block_rows, fanout, work, prec)
+    cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=dev)
+    o = _opts(block_rows, fanout, prec=prec)
+    st = lib.tsqr_direct_host(_ptr(A), m, n, _dtype_code(A), _ptr(Q), _ptr(R), _ptr(dbuf), _ptr(work),
+                              work.numel(), ctypes.byref(o), _stream(dev), ctypes.c_void_p(cs.cuda_stream))
+    _raise(st, "tsqr_direct_host")
+    _status(work, "tsqr_direct_host", check)
     return Q, R
 
 

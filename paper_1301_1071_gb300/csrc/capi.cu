@@ -138,6 +138,45 @@ tsqr_status mark(const tsqr_opts* o, int i, cudaStream_t st) {
                                                                                           : TSQR_ERR_CUDA;
 }
 
+#define TSQR_TRY(x)                       \
+  do {                                    \
+    tsqr_status _s = (x);                 \
+    if (_s != TSQR_OK) return _s;         \
+  } while (0)
+#define TSQR_CUDA(x) TSQR_TRY((x) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA)
+
+// Step 2 (Alg. 2) after Step 1 has filled the level-0 stack: the tree up
+// (each level's stack is the tall input of the next), the top sign fix into
+// R, `extra` on the top coefficient, and the tree down (the Q of level l's
+// stack is the coefficient of level l - 1), leaving Step 3's coefficients.
+template <class Extra>
+tsqr_status run_tree(const Plan& P, double* R, int64_t ldr, void* work, cudaStream_t st, Extra extra) {
+  const int n = static_cast<int>(P.n);
+  int32_t* status = status_ptr(work);
+  const size_t L = P.levels.size();
+  auto S = [&](size_t l) { return reinterpret_cast<double*>(at(work, P.levels[l].off_S)); };
+  auto T = [&](size_t l) { return reinterpret_cast<double*>(at(work, P.levels[l].off_T)); };
+  double* ctop = reinterpret_cast<double*>(at(work, P.off_ctop));
+  for (size_t l = 1; l < L; ++l) {
+    const Level& lv = P.levels[l];
+    const cudaError_t e =
+        launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, S(l - 1), S(l), T(l), status, st);
+    if (e != cudaSuccess) return TSQR_ERR_CUDA;
+    if (launch_build_t(T(l), lv.p * lv.kt, n, false, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  }
+  if (launch_sign_fix(S(L - 1), n, R, ldr, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  if (extra(ctop) != TSQR_OK) return TSQR_ERR_CUDA;
+  for (size_t l = L - 1; l >= 1; --l) {
+    const Level& lv = P.levels[l];
+    const double* C = (l == L - 1) ? ctop : S(l);
+    const int64_t cb = (l == L - 1) ? 1 : lv.p;
+    const cudaError_t e =
+        launch_form_q(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, T(l), C, cb, S(l - 1), status, st);
+    if (e != cudaSuccess) return TSQR_ERR_CUDA;
+  }
+  return TSQR_OK;
+}
+
 template <class Extra>
 tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t ldr, void* work,
                        cudaStream_t st, const tsqr_opts* o, Extra extra) {
@@ -156,25 +195,7 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
     return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
   if (launch_build_t(T(0), l0.p * l0.kt, n, P.esz == 4, st) != cudaSuccess) return TSQR_ERR_CUDA;
-  // Step 2 (Alg. 2): the stack of level l-1 is the tall input of level l.
-  for (size_t l = 1; l < L; ++l) {
-    const Level& lv = P.levels[l];
-    const cudaError_t e =
-        launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, S(l - 1), S(l), T(l), status, st);
-    if (e != cudaSuccess) return TSQR_ERR_CUDA;
-    if (launch_build_t(T(l), lv.p * lv.kt, n, false, st) != cudaSuccess) return TSQR_ERR_CUDA;
-  }
-  if (launch_sign_fix(S(L - 1), n, R, ldr, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
-  if (extra(ctop) != TSQR_OK) return TSQR_ERR_CUDA;
-  // Down the tree: the Q of level l's stack is the coefficient of level l-1.
-  for (size_t l = L - 1; l >= 1; --l) {
-    const Level& lv = P.levels[l];
-    const double* C = (l == L - 1) ? ctop : S(l);
-    const int64_t cb = (l == L - 1) ? 1 : lv.p;
-    const cudaError_t e =
-        launch_form_q(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, T(l), C, cb, S(l - 1), status, st);
-    if (e != cudaSuccess) return TSQR_ERR_CUDA;
-  }
+  TSQR_TRY(run_tree(P, R, ldr, work, st, extra));
   // Step 3: Q_i = Q1_i Q2_i over the Y_i held in Q.
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
   const double* C0 = (L == 1) ? ctop : S(0);
@@ -230,12 +251,88 @@ tsqr_status copy_r(double* R, int64_t ldr, const double* src, int64_t n, cudaStr
              : TSQR_ERR_CUDA;
 }
 
-#define TSQR_TRY(x)                       \
-  do {                                    \
-    tsqr_status _s = (x);                 \
-    if (_s != TSQR_OK) return _s;         \
-  } while (0)
-#define TSQR_CUDA(x) TSQR_TRY((x) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA)
+// tsqr_direct_host on a built plan: chunk c covers row blocks
+// [c pc, (c + 1) pc).  Step 1 and Step 3 of a chunk run as one launch each
+// over that chunk's blocks (pointer offsets; the kernels index blocks from 0).
+struct HostEvents {
+  cudaEvent_t ev[2 * kMaxHostChunks + 1] = {};
+  int count = 0;
+  ~HostEvents() {
+    for (int i = 0; i < count; ++i) cudaEventDestroy(ev[i]);  // released once their work completes
+  }
+  bool make(int k) {
+    for (; count < k; ++count)
+      if (cudaEventCreateWithFlags(&ev[count], cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+  }
+};
+
+tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, double* Rh, char* dbuf, void* work,
+                            cudaStream_t st, cudaStream_t cst) {
+  const int n = static_cast<int>(P.n);
+  const size_t row_bytes = (size_t)n * P.esz;
+  const size_t nn = (size_t)n * n;
+  int32_t* status = status_ptr(work);
+  const Level& l0 = P.levels[0];
+  const size_t L = P.levels.size();
+  double* S0 = reinterpret_cast<double*>(at(work, l0.off_S));
+  double* T0 = reinterpret_cast<double*>(at(work, l0.off_T));
+  double* ctop = reinterpret_cast<double*>(at(work, P.off_ctop));
+  double* Rd = reinterpret_cast<double*>(at(work, P.off_small));
+  const int64_t pc = (l0.p + chunks - 1) / chunks;
+  HostEvents E;
+  if (!E.make(2 * chunks + 1)) return TSQR_ERR_CUDA;
+  cudaEvent_t* ev_in = E.ev;             // chunk's rows of A are on the device
+  cudaEvent_t* ev_q = E.ev + chunks;     // chunk's rows of Q are formed
+  cudaEvent_t ev_done = E.ev[2 * chunks];
+  TSQR_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  // the copy stream must not overwrite dbuf before earlier work on `stream` is done
+  TSQR_CUDA(cudaEventRecord(ev_done, st));
+  TSQR_CUDA(cudaStreamWaitEvent(cst, ev_done, 0));
+  auto chunk_rows = [&](int c, int64_t* b0, int64_t* pcnt, int64_t* r0, int64_t* rows) {
+    *b0 = c * pc;
+    *pcnt = (l0.p - *b0 < pc) ? l0.p - *b0 : pc;
+    *r0 = *b0 * l0.b;
+    const int64_t r1 = (*b0 + *pcnt) * l0.b;
+    *rows = (r1 < P.m ? r1 : P.m) - *r0;
+  };
+  // Step 1, chunk by chunk as A's rows arrive
+  for (int c = 0; c < chunks; ++c) {
+    int64_t b0, pcnt, r0, rows;
+    chunk_rows(c, &b0, &pcnt, &r0, &rows);
+    if (pcnt <= 0) continue;
+    TSQR_CUDA(cudaMemcpyAsync(dbuf + r0 * row_bytes, A + r0 * row_bytes, rows * row_bytes, cudaMemcpyHostToDevice,
+                              cst));
+    TSQR_CUDA(cudaEventRecord(ev_in[c], cst));
+    TSQR_CUDA(cudaStreamWaitEvent(st, ev_in[c], 0));
+    TSQR_CUDA(launch_local_qr(P.cfg0, dbuf + r0 * row_bytes, rows, n, l0.b, l0.bt, l0.kt, pcnt,
+                              dbuf + r0 * row_bytes, S0 + b0 * nn, T0 + b0 * l0.kt * nn, status, st));
+    TSQR_CUDA(launch_build_t(T0 + b0 * l0.kt * nn, pcnt * l0.kt, n, P.esz == 4, st));
+  }
+  // Step 2, then R back to the host
+  TSQR_TRY(run_tree(P, Rd, n, work, st, [](double*) { return TSQR_OK; }));
+  TSQR_CUDA(cudaMemcpyAsync(Rh, Rd, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // Step 3, chunk by chunk, each chunk of Q copied back behind the next
+  const double* C0 = (L == 1) ? ctop : S0;
+  for (int c = 0; c < chunks; ++c) {
+    int64_t b0, pcnt, r0, rows;
+    chunk_rows(c, &b0, &pcnt, &r0, &rows);
+    if (pcnt <= 0) continue;
+    const double* Cc = (L == 1) ? C0 : C0 + b0 * nn;
+    const int64_t cb = (L == 1) ? 1 : pcnt;
+    char* Y = dbuf + r0 * row_bytes;
+    TSQR_CUDA(P.tc3 ? launch_form_q_tc(reinterpret_cast<float*>(Y), rows, n, l0.b, P.cfg0.B, l0.bt, l0.kt, pcnt,
+                                       T0 + b0 * l0.kt * nn, Cc, cb, status, st)
+                    : launch_form_q(P.cfg0, Y, rows, n, l0.b, l0.bt, l0.kt, pcnt, T0 + b0 * l0.kt * nn, Cc, cb, Y,
+                                    status, st));
+    TSQR_CUDA(cudaEventRecord(ev_q[c], st));
+    TSQR_CUDA(cudaStreamWaitEvent(cst, ev_q[c], 0));
+    TSQR_CUDA(cudaMemcpyAsync(Qh + r0 * row_bytes, Y, rows * row_bytes, cudaMemcpyDeviceToHost, cst));
+  }
+  TSQR_CUDA(cudaEventRecord(ev_done, cst));
+  TSQR_CUDA(cudaStreamWaitEvent(st, ev_done, 0));
+  return TSQR_OK;
+}
 
 tsqr_status plan_for(int op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* o, size_t work_bytes,
                      const void* work, Plan* P) {
@@ -278,13 +375,19 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
   if (esz == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
-  const int prec = (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? opts->prec : 0;
+  const int prec =
+      (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD || op == TSQR_OP_DIRECT_HOST)) ? opts->prec : 0;
   Plan P;
-  int rc =
-      make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec, device_sms());
+  int chunks = 1;
+  int rc = op == TSQR_OP_DIRECT_HOST
+               ? make_host_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, &chunks,
+                                prec, device_sms())
+               : make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec,
+                           device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   const int L = static_cast<int>(P.levels.size());
   switch (op) {
+    case TSQR_OP_DIRECT_HOST: *launches = 3 * chunks + 3 * (L - 1) + 1; break;  // chunks x (Step 1, T, Step 3)
     case TSQR_OP_DIRECT: *launches = 3 * L + 1; break;        // L up (+ T build), sign fix, L down
     case TSQR_OP_SVD: *launches = 3 * L + 2; break;           // + Jacobi SVD
     case TSQR_OP_CHOLQR: *launches = 4 * (1 + refine_steps) + refine_steps; break;  // gram, reduce, chol, rowmul (+ combine)
@@ -312,11 +415,16 @@ tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
   if (esz == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
-  if (op < TSQR_OP_DIRECT || op > TSQR_OP_BACKWARD) return TSQR_ERR_ARG;
-  const int prec = (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? opts->prec : 0;
+  if (op < TSQR_OP_DIRECT || op > TSQR_OP_DIRECT_HOST) return TSQR_ERR_ARG;
+  const int prec =
+      (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD || op == TSQR_OP_DIRECT_HOST)) ? opts->prec : 0;
   Plan P;
-  int rc =
-      make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec, device_sms());
+  int chunks = 1;
+  int rc = op == TSQR_OP_DIRECT_HOST
+               ? make_host_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, &chunks,
+                                prec, device_sms())
+               : make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec,
+                           device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   *bytes = op_bytes(P, op);
   return TSQR_OK;
@@ -338,6 +446,31 @@ tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_
   if (!work || work_bytes < P.bytes || !aligned16(work)) return TSQR_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   s = run_direct(P, A, Q, R, ldr, work, st, opts, [](double*) { return TSQR_OK; });
+  if (s != TSQR_OK) return s;
+  return finish(work, opts, st);
+}
+
+tsqr_status tsqr_direct_host(const void* A, int64_t m, int64_t n, int32_t dtype, void* Q, double* R,
+                             void* dbuf, void* work, size_t work_bytes, const tsqr_opts* opts,
+                             void* stream, void* copy_stream) {
+  if (!A || !Q || !R || !dbuf || esz_of(dtype) == 0) return TSQR_ERR_ARG;
+  if (stream == copy_stream) return TSQR_ERR_ARG;
+  tsqr_status s = check_opts(opts);
+  if (s != TSQR_OK) return s;
+  if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  if (!aligned16(dbuf)) return TSQR_ERR_ALIGN;
+  const int esz = esz_of(dtype);
+  if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
+  Plan P;
+  int chunks = 1;
+  int rc = make_host_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, &chunks,
+                          opts ? opts->prec : 0, device_sms());
+  if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
+  if (!work || work_bytes < P.bytes || !aligned16(work)) return TSQR_ERR_WORKSPACE;
+  if (overlaps(dbuf, (size_t)m * n * esz, work, P.bytes)) return TSQR_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = run_direct_host(P, chunks, static_cast<const char*>(A), static_cast<char*>(Q), R, static_cast<char*>(dbuf),
+                      work, st, static_cast<cudaStream_t>(copy_stream));
   if (s != TSQR_OK) return s;
   return finish(work, opts, st);
 }

@@ -234,4 +234,37 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   return TSQR_OK;
 }
 
+int make_host_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int* chunks,
+                   int prec, int sms) {
+  Plan P0;
+  int rc = make_plan(m, n, esz, block_rows, fanout, &P0, prec, sms);
+  if (rc != TSQR_OK) return rc;
+  if (sms < 1) sms = kDefaultSMs;
+  const int64_t slots = (int64_t)sms * P0.cfg0.ctas;
+  if (block_rows <= 0) {
+    int64_t c = (m * n * esz) / kHostChunkBytes;
+    c = c < 1 ? 1 : (c > kMaxHostChunks ? kMaxHostChunks : c);
+    if (c > 1) {
+      // c chunks of w waves each, blocks no taller than the default plan's
+      const int64_t p0 = P0.levels[0].p;
+      const int64_t w = (p0 + c * slots - 1) / (c * slots);
+      const int64_t p = c * slots * (w < 1 ? 1 : w);
+      int64_t al = 1;
+      while ((al * n * esz) % 16 != 0) ++al;
+      int64_t b = (m + p - 1) / p;
+      b = (b + al - 1) / al * al;
+      if (b >= n && b >= P0.cfg0.B) {
+        Plan P1;
+        if (make_plan(m, n, esz, b, fanout, &P1, prec, sms) == TSQR_OK) P0 = P1;
+      }
+    }
+  }
+  const int64_t p = P0.levels[0].p;
+  int64_t c = p / slots;
+  c = c < 1 ? 1 : (c > kMaxHostChunks ? kMaxHostChunks : c);
+  *chunks = (int)c;
+  *plan = P0;
+  return TSQR_OK;
+}
+
 }  // namespace tsqr

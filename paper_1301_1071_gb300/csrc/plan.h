@@ -109,4 +109,14 @@ size_t op_bytes(const Plan& P, int op);
 int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec = 0,
               int sms = kDefaultSMs);
 
+// Plan of the host-buffer entry point (tsqr_direct_host): the row blocks are
+// taken in `chunks` (<= kMaxHostChunks) consecutive groups, each a whole
+// number of waves of resident CTAs, so that chunk c's copy overlaps chunk
+// c - 1's kernels.  block_rows == 0: the block height is chosen so that A
+// splits into chunks of about kHostChunkBytes (at most kMaxHostChunks).
+constexpr int kMaxHostChunks = 8;
+constexpr int64_t kHostChunkBytes = 128ll << 20;
+int make_host_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int* chunks,
+                   int prec = 0, int sms = kDefaultSMs);
+
 }  // namespace tsqr

@@ -71,7 +71,8 @@ def test_workspace_size_host_only(lib):
 
 def test_workspace_tiled_blocks(lib):
     """Blocks taller than the register tile are accepted: one R per block and
-    one T per tile (binary64 R tile of 640 rows at n = 25, then 614-row tiles)."""
+    one T per tile (lower bound with 640-row tiles, then 614-row tiles; the
+    default binary64 tile at n = 25 is smaller, so it needs more)."""
     st, b = _ws(lib, 0, 200_000, 25, 0, block_rows=5000)
     assert st == 0
     p, kt = 40, 1 + -(-(5000 - 640) // 614)
@@ -95,6 +96,28 @@ def test_workspace_size_rejects(lib, m, n, dt, b, f, want):
 def test_plans_for_every_n(lib, dt):
     """Every op has a plan (tile choice, tree, workspace) for n = 1 .. NMAX."""
     for n in range(1, 101):
-        for op in range(5):
+        for op in range(6):
             st, b = _ws(lib, op, 300_000, n, dt)
             assert st == 0 and b > 0, (op, n, st)
+
+
+def _launches(lib, op, m, n, dt, block_rows=0):
+    f = lib.tsqr_launch_count
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Opts),
+                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    f.restype = ctypes.c_int
+    o = Opts(block_rows, 0, 0, None, 0, 0)
+    out = ctypes.c_int32(0)
+    assert f(op, m, n, dt, ctypes.byref(o), 0, ctypes.byref(out)) == 0
+    return out.value
+
+
+def test_host_path_plan(lib):
+    """tsqr_direct_host (op 5): one copy chunk for a small problem (the same
+    launches as tsqr_direct); a 1.6 GB matrix is split into several chunks
+    of whole waves, each chunk adding a Step-1, T and Step-3 launch."""
+    assert _launches(lib, 5, 100_000, 10, 0, block_rows=1000) == _launches(lib, 0, 100_000, 10, 0, block_rows=1000)
+    big_host, big_dev = _launches(lib, 5, 8_000_000, 25, 0), _launches(lib, 0, 8_000_000, 25, 0)
+    assert big_host >= big_dev + 3 * 3
+    st, b = _ws(lib, 5, 8_000_000, 25, 0)
+    assert st == 0 and 0 < b < 8_000_000 * 25 * 8 // 4
