@@ -353,73 +353,170 @@ cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop,
 // Compact-WY T factors of p row blocks, in place (one warp per block): the
 // slot holds tau_j on the diagonal and the Gram entries G(i,j) = v_i^T v_j
 // above it; T(j,j) = tau_j and T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j),
-// column by column (H_1 ... H_k = I - Y T Y^T).  Each warp stages its slot in
-// shared memory at row stride n + 1 (lane i walks row i: at most two-way bank
-// conflicts), runs the recursion there in type F and writes the upper
-// triangle back (binary64 slots; F = binary32 for the row blocks of binary32
-// data, whose Gram entries are binary32 values).
+// column by column (H_1 ... H_k = I - Y T Y^T).  Each warp stages the upper
+// triangle of its slot in shared memory, packed by columns (entry (i, c),
+// i <= c, at c (c + 1) / 2 + i: half the space of a square stage, so twice
+// the warps per SM), runs the recursion there in type F and writes it back
+// (binary64 slots; F = binary32 for the row blocks of binary32 data, whose
+// Gram entries are binary32 values).  Step j runs over l (the sum index)
+// with the rows i = lane + 32 s of every segment s advancing together, two
+// accumulators each (independent chains); segments whose rows all exceed l
+// are skipped (warp-uniform).
+constexpr int kBuildTSegs = 4;  // 32-row segments: n <= 128
+constexpr int kBuildTPad = 64;  // spare entries after each warp's triangle (no read ever reaches them)
+
 template <class F>
 __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
   F* tsm = reinterpret_cast<F*>(tsm_raw);
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int ld = n + 1;
-  F* t = tsm + static_cast<size_t>(wl) * n * ld;
+  const int np = n * (n + 1) / 2;
+  F* t = tsm + static_cast<size_t>(wl) * (np + kBuildTPad);
   const int64_t blk = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wl;
   if (blk >= p) return;  // warp-level work only: no CTA barrier below
   double* g = Tst + blk * n * n;
   for (int i = 0; i < n; ++i)
-    for (int c = i + lane; c < n; c += 32) t[i * ld + c] = static_cast<F>(g[i * n + c]);
+    for (int c = i + lane; c < n; c += 32) t[c * (c + 1) / 2 + i] = static_cast<F>(g[i * n + c]);
   __syncwarp();
   for (int j = 1; j < n; ++j) {
-    const F tj = t[j * ld + j];
-    F v[4];
+    const F* gj = t + j * (j + 1) / 2;  // column j: G(l, j) for l < j, tau_j at l = j
+    const F tj = gj[j];
+    F acc[kBuildTSegs][2];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int i = lane + 32 * s;
-      F a0 = F(0), a1 = F(0);
-      if (i < j) {
-        const F* ti = t + i * ld;
-        a0 = ti[i] * ti[j];  // T(i,i) = tau_i times G(i,j)
-        int l = i + 1;
-        for (; l + 1 < j; l += 2) {
-          a0 = fma(ti[l], t[l * ld + j], a0);
-          a1 = fma(ti[l + 1], t[(l + 1) * ld + j], a1);
-        }
-        if (l < j) a0 = fma(ti[l], t[l * ld + j], a0);
+    for (int s = 0; s < kBuildTSegs; ++s) acc[s][0] = acc[s][1] = F(0);
+    const F* tl = t;  // column l of T, advanced by l + 1 entries per step
+    int l = 0;
+    // four columns per pass: their loads are issued before the FMAs use them
+    for (; l + 3 < j; l += 4) {
+      const F* t1 = tl + l + 1;
+      const F* t2 = t1 + l + 2;
+      const F* t3 = t2 + l + 3;
+      const F g0 = gj[l], g1 = gj[l + 1], g2 = gj[l + 2], g3 = gj[l + 3];
+#pragma unroll
+      for (int s = 0; s < kBuildTSegs; ++s) {
+        if (32 * s > l + 3) break;
+        const int i = lane + 32 * s;
+        F x0 = F(0), x1 = F(0), x2 = F(0), x3 = F(0);  // rows below a column's diagonal add 0
+        if (i <= l) x0 = tl[i];
+        if (i <= l + 1) x1 = t1[i];
+        if (i <= l + 2) x2 = t2[i];
+        if (i <= l + 3) x3 = t3[i];
+        acc[s][0] = fma(x2, g2, fma(x0, g0, acc[s][0]));
+        acc[s][1] = fma(x3, g3, fma(x1, g1, acc[s][1]));
       }
-      v[s] = -tj * (a0 + a1);
+      tl = t3 + l + 4;
+    }
+    for (; l < j; ++l) {
+      const F gl = gj[l];
+#pragma unroll
+      for (int s = 0; s < kBuildTSegs; ++s) {
+        if (32 * s > l) break;  // rows of this and later segments all exceed l
+        const int i = lane + 32 * s;
+        if (i <= l) {  // static accumulator indices keep acc in registers
+          if (l & 1) acc[s][1] = fma(tl[i], gl, acc[s][1]);
+          else acc[s][0] = fma(tl[i], gl, acc[s][0]);
+        }
+      }
+      tl += l + 1;
     }
     __syncwarp();
+    F* tcol = t + j * (j + 1) / 2;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < kBuildTSegs; ++s) {
       const int i = lane + 32 * s;
-      if (i < j) t[i * ld + j] = v[s];
+      if (i < j) tcol[i] = -tj * (acc[s][0] + acc[s][1]);
     }
     __syncwarp();
   }
   for (int i = 0; i < n; ++i)
-    for (int c = i + lane; c < n; c += 32) g[i * n + c] = static_cast<double>(t[i * ld + c]);
+    for (int c = i + lane; c < n; c += 32) g[i * n + c] = static_cast<double>(t[c * (c + 1) / 2 + i]);
+}
+
+// Few slots (the upper tree levels): one slot per CTA of kBuildTWarps warps;
+// step j splits the sum index l over the warps, and warp 0 adds the
+// partials in warp order (deterministic) before the CTA moves on.
+constexpr int kBuildTWarps = 8;
+
+template <class F>
+__global__ void __launch_bounds__(32 * kBuildTWarps) k_build_t_cta(double* __restrict__ Tst, int n) {
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  const int np = n * (n + 1) / 2;
+  F* t = reinterpret_cast<F*>(tsm_raw);
+  F* part = t + ((np + 1) & ~1);  // kBuildTWarps x 32 kBuildTSegs partial sums
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* g = Tst + static_cast<int64_t>(blockIdx.x) * n * n;
+  for (int i = 0; i < n; ++i)
+    for (int c = i + threadIdx.x; c < n; c += blockDim.x) t[c * (c + 1) / 2 + i] = static_cast<F>(g[i * n + c]);
+  __syncthreads();
+  for (int j = 1; j < n; ++j) {
+    const F* gj = t + j * (j + 1) / 2;
+    const int l0 = j * w / kBuildTWarps, l1 = j * (w + 1) / kBuildTWarps;
+    F acc[kBuildTSegs][2];
+#pragma unroll
+    for (int s = 0; s < kBuildTSegs; ++s) acc[s][0] = acc[s][1] = F(0);
+    const F* tl = t + l0 * (l0 + 1) / 2;
+    for (int l = l0; l < l1; ++l) {
+      const F gl = gj[l];
+#pragma unroll
+      for (int s = 0; s < kBuildTSegs; ++s) {
+        if (32 * s > l) break;
+        const int i = lane + 32 * s;
+        if (i <= l) {  // static accumulator indices keep acc in registers
+          if (l & 1) acc[s][1] = fma(tl[i], gl, acc[s][1]);
+          else acc[s][0] = fma(tl[i], gl, acc[s][0]);
+        }
+      }
+      tl += l + 1;
+    }
+#pragma unroll
+    for (int s = 0; s < kBuildTSegs; ++s) part[(w * kBuildTSegs + s) * 32 + lane] = acc[s][0] + acc[s][1];
+    __syncthreads();
+    if (w == 0) {
+      const F tj = gj[j];
+      F* tcol = t + j * (j + 1) / 2;
+#pragma unroll
+      for (int s = 0; s < kBuildTSegs; ++s) {
+        const int i = lane + 32 * s;
+        if (i < j) {
+          F v = F(0);
+          for (int ww = 0; ww < kBuildTWarps; ++ww) v += part[(ww * kBuildTSegs + s) * 32 + lane];
+          tcol[i] = -tj * v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < n; ++i)
+    for (int c = i + threadIdx.x; c < n; c += blockDim.x) g[i * n + c] = static_cast<double>(t[c * (c + 1) / 2 + i]);
+}
+
+template <class F>
+static cudaError_t build_t_typed(double* Tst, int64_t p, int n, int sms, cudaStream_t st) {
+  const size_t np = static_cast<size_t>(n) * (n + 1) / 2;
+  if (p < 2 * static_cast<int64_t>(sms)) {
+    // few slots: latency decides, so one CTA of several warps per slot
+    const size_t smem = (((np + 1) & ~static_cast<size_t>(1)) + kBuildTWarps * kBuildTSegs * 32) * sizeof(F);
+    cudaError_t e = cudaFuncSetAttribute(k_build_t_cta<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_build_t_cta<F><<<static_cast<unsigned>(p), 32 * kBuildTWarps, smem, st>>>(Tst, n);
+    return cudaGetLastError();
+  }
+  // many slots: one warp per slot, as many warps (<= 16) as packed triangles fit in 220 KB
+  const size_t per_warp = (np + kBuildTPad) * sizeof(F);
+  int warps = static_cast<int>((220u * 1024u) / per_warp);
+  warps = warps < 1 ? 1 : (warps > 16 ? 16 : warps);
+  const size_t smem = static_cast<size_t>(warps) * per_warp;
+  const int64_t grid = (p + warps - 1) / warps;
+  cudaError_t e = cudaFuncSetAttribute(k_build_t<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_build_t<F><<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(Tst, p, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_build_t(double* Tst, int64_t p, int n, bool binary32, cudaStream_t st) {
-  // as many warps (<= 8) as n (n + 1) staged values each fit in 200 KB
-  const size_t per_warp = static_cast<size_t>(n) * (n + 1) * (binary32 ? sizeof(float) : sizeof(double));
-  int warps = static_cast<int>((200u * 1024u) / per_warp);
-  warps = warps < 1 ? 1 : (warps > 8 ? 8 : warps);
-  const size_t smem = static_cast<size_t>(warps) * per_warp;
-  const int64_t grid = (p + warps - 1) / warps;
-  cudaError_t e;
-  if (binary32) {
-    e = cudaFuncSetAttribute(k_build_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_build_t<float><<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(Tst, p, n);
-  } else {
-    e = cudaFuncSetAttribute(k_build_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_build_t<double><<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(Tst, p, n);
-  }
-  return cudaGetLastError();
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return binary32 ? build_t_typed<float>(Tst, p, n, sms, st) : build_t_typed<double>(Tst, p, n, sms, st);
 }
 
 // G = sum over the nparts partials, in index order (one thread per entry).
