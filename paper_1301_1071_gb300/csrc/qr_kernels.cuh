@@ -487,28 +487,31 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         }
         __syncwarp();
 
-        // phase B: as in the general loop, with one row group
-        T d[NPC], rj[NPC];
+        // phase B: as in the general loop, with one row group; R's row j
+        //      goes to shared memory, transposed into the Gram buffer's lower
+        //      triangle (entry (c, j) = r_jc, c >= j; the Gram entries sit
+        //      at (k, j), k < j), and back into the register rows < n once
+        //      the tile is done: row j's registers are not read again within
+        //      the tile (x is zero there for every later column)
+        T d[NPC];
         {
-          T dl = T(0), rl = T(0);
+          T dl = T(0);
           const int mycol = cs + lane * CS;
           if (lane < NPC && mycol < n) {
             const T Sc = rcur[warp * 32 + lane];
             const T pc = pcur[mycol];
             if (mycol > j) {
-              rl = Sc * f.ib;
+              const T rl = Sc * f.ib;
               dl = (pc - rl) * f.scal;
+              gram[mycol * n + j] = f.ident ? pc : rl;
             } else if (mycol == j) {
-              rl = f.beta;
+              gram[mycol * n + j] = f.beta;
             } else {
               gram[mycol * n + j] = f.scal * (Sc - f.beta * pc);
             }
           }
 #pragma unroll
-          for (int c = 0; c < NPC; ++c) {
-            d[c] = shfl_from(dl, c);
-            rj[c] = shfl_from(rl, c);
-          }
+          for (int c = 0; c < NPC; ++c) d[c] = shfl_from(dl, c);
         }
 
         // phase C: trailing update with the look-ahead of column j + 1
@@ -524,17 +527,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
           case 4: tile_update_la<4, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
           default: tile_update_la<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
         }
-        if (!f.ident) {
-#pragma unroll
-          for (int q = 0; q < QH; ++q)
-            if (rbase + 32 * q == j) {
-#pragma unroll
-              for (int c = 0; c < NPC; ++c) {
-                const int col = cs + c * CS;
-                if (col >= j && col < n) a[q][c] = rj[c];
-              }
-            }
-        }
         if (j + 1 < n) {
 #pragma unroll
           for (int q = 0; q < QH; ++q)
@@ -546,7 +538,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         __syncwarp();
         jb3 = jn3;
       }
-      __syncthreads();  // gram and taus are read CTA-wide below
+      __syncthreads();  // gram, R's rows and taus are read CTA-wide below
+      // R's rows back into the register rows < n (their entries on and above
+      // the diagonal; below it they hold Y's vectors, or the zeros of a
+      // carried R)
+#pragma unroll
+      for (int q = 0; q < QH; ++q) {
+        const int r = rbase + 32 * q;
+        if (r < n) {
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) {
+            const int col = cs + c * CS;
+            if (col >= r && col < n) a[q][c] = gram[col * n + r];
+          }
+        }
+      }
     } else {
       for (int j = 0; j < n; ++j) {
         const int jb = j & 1;
