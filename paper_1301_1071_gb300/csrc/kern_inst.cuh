@@ -1,7 +1,8 @@
 // kern_inst.cuh -- instantiates the TSQR kernels for one (storage, compute)
-// type pair and five register tiles (R_i rows per thread, at most T_i threads
-// per CTA so that registers x threads <= 64K); included once per dtype
-// translation unit.  KernelCfg::tile selects the tile.
+// type pair and six register tiles (R_i rows x N_i columns per thread, at
+// most T_i threads per CTA so that registers x threads <= 64K; N_i = 5 unless
+// TSQR_N_i says otherwise); included once per dtype translation unit.
+// KernelCfg::tile selects the tile.
 #pragma once
 
 #include "launch.h"
@@ -10,25 +11,25 @@
 
 namespace tsqr {
 
-template <int R, int MAXT>
+template <int R, int MAXT, int NPC>
 static cudaError_t local_qr_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
                               int64_t p, TSQR_S* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
   if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
   // the look-ahead form when the tile is one row group
-  auto fn = k.NRG == 1 ? k_local_qr<TSQR_S, TSQR_T, kNpc, R, MAXT, true>
-                       : k_local_qr<TSQR_S, TSQR_T, kNpc, R, MAXT, false>;
+  auto fn = k.NRG == 1 ? k_local_qr<TSQR_S, TSQR_T, NPC, R, MAXT, true>
+                       : k_local_qr<TSQR_S, TSQR_T, NPC, R, MAXT, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_qr);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)p, k.NT, k.smem_qr, st>>>(A, m, n, (int)b, (int)bt, kt, k.CS, k.NRG, Y, Rst, Tst, status);
   return cudaGetLastError();
 }
 
-template <int R, int MAXT>
+template <int R, int MAXT, int NPC>
 static cudaError_t form_q_R(const KernelCfg& k, const TSQR_S* Y, int64_t m, int n, int64_t b, int64_t bt, int kt,
                             int64_t p, const double* T, const double* C, int64_t cblocks, TSQR_S* Q,
                             int32_t* status, cudaStream_t st) {
   if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
-  auto fn = k_form_q<TSQR_S, TSQR_T, kNpc, R, MAXT>;
+  auto fn = k_form_q<TSQR_S, TSQR_T, NPC, R, MAXT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_fq);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)p, k.NT, k.smem_fq, st>>>(Y, m, n, (int)b, (int)bt, kt, k.fq_rows, k.CS, k.NRG, k.skew, T, C,
@@ -41,11 +42,12 @@ cudaError_t TSQR_LOCAL_QR_NAME(const KernelCfg& k, const void* A, int64_t m, int
   const TSQR_S* a = static_cast<const TSQR_S*>(A);
   TSQR_S* y = static_cast<TSQR_S*>(Y);
   switch (k.tile) {
-    case 0: return local_qr_R<TSQR_R0, TSQR_T0>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
-    case 1: return local_qr_R<TSQR_R1, TSQR_T1>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
-    case 2: return local_qr_R<TSQR_R2, TSQR_T2>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
-    case 3: return local_qr_R<TSQR_R3, TSQR_T3>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
-    case 4: return local_qr_R<TSQR_R4, TSQR_T4>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 0: return local_qr_R<TSQR_R0, TSQR_T0, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 1: return local_qr_R<TSQR_R1, TSQR_T1, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 2: return local_qr_R<TSQR_R2, TSQR_T2, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 3: return local_qr_R<TSQR_R3, TSQR_T3, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 4: return local_qr_R<TSQR_R4, TSQR_T4, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 5: return local_qr_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -56,22 +58,23 @@ cudaError_t TSQR_FORM_Q_NAME(const KernelCfg& k, const void* Y, int64_t m, int n
   const TSQR_S* y = static_cast<const TSQR_S*>(Y);
   TSQR_S* q = static_cast<TSQR_S*>(Q);
   switch (k.tile) {
-    case 0: return form_q_R<TSQR_R0, TSQR_T0>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
-    case 1: return form_q_R<TSQR_R1, TSQR_T1>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
-    case 2: return form_q_R<TSQR_R2, TSQR_T2>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
-    case 3: return form_q_R<TSQR_R3, TSQR_T3>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
-    case 4: return form_q_R<TSQR_R4, TSQR_T4>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 0: return form_q_R<TSQR_R0, TSQR_T0, kNpc>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 1: return form_q_R<TSQR_R1, TSQR_T1, kNpc>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 2: return form_q_R<TSQR_R2, TSQR_T2, kNpc>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 3: return form_q_R<TSQR_R3, TSQR_T3, kNpc>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 4: return form_q_R<TSQR_R4, TSQR_T4, kNpc>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 5: return form_q_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 #ifdef TSQR_ROWMUL_NAME
-template <int R, int MAXT>
+template <int R, int MAXT, int NPC>
 static cudaError_t rowmul_R(const KernelCfg& k, const TSQR_S* X, const double* M1, const TSQR_S* Y,
                             const double* M2, int64_t m, int n, int64_t b, int64_t p, TSQR_S* out,
                             int32_t* status, cudaStream_t st) {
   if (k.NT > MAXT) return cudaErrorInvalidConfiguration;
-  auto fn = k_rowmul<TSQR_S, TSQR_T, kNpc, R, MAXT>;
+  auto fn = k_rowmul<TSQR_S, TSQR_T, NPC, R, MAXT>;
   const size_t smem = k.smem_rm;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -86,11 +89,12 @@ cudaError_t TSQR_ROWMUL_NAME(const KernelCfg& k, const void* X, const double* M1
   const TSQR_S* y = static_cast<const TSQR_S*>(Y);
   TSQR_S* o = static_cast<TSQR_S*>(out);
   switch (k.tile) {
-    case 0: return rowmul_R<TSQR_R0, TSQR_T0>(k, x, M1, y, M2, m, n, b, p, o, status, st);
-    case 1: return rowmul_R<TSQR_R1, TSQR_T1>(k, x, M1, y, M2, m, n, b, p, o, status, st);
-    case 2: return rowmul_R<TSQR_R2, TSQR_T2>(k, x, M1, y, M2, m, n, b, p, o, status, st);
-    case 3: return rowmul_R<TSQR_R3, TSQR_T3>(k, x, M1, y, M2, m, n, b, p, o, status, st);
-    case 4: return rowmul_R<TSQR_R4, TSQR_T4>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 0: return rowmul_R<TSQR_R0, TSQR_T0, kNpc>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 1: return rowmul_R<TSQR_R1, TSQR_T1, kNpc>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 2: return rowmul_R<TSQR_R2, TSQR_T2, kNpc>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 3: return rowmul_R<TSQR_R3, TSQR_T3, kNpc>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 4: return rowmul_R<TSQR_R4, TSQR_T4, kNpc>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 5: return rowmul_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, x, M1, y, M2, m, n, b, p, o, status, st);
     default: return cudaErrorInvalidValue;
   }
 }

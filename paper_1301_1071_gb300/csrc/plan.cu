@@ -19,15 +19,20 @@ static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 // per-thread limit is 255 / 168 / 128 / 96 registers at MAXT = 256 / 384 /
 // 512 / 640; R x 5 values (x2 registers for 8-byte and double-float values)
 // leave about 60 registers for the rest of the kernel, with no spills.
-// The last tile exceeds that budget (its registers spill); it is taken only
-// when no other tile holds the rows asked for (binary64 tree nodes of two
-// R factors at n > 64).
-struct TileChoice { int R, maxt; bool spills; };
-constexpr int kNumTiles = 5;
-static const TileChoice kTiles64[kNumTiles] = {
-    {16, 256, false}, {10, 384, false}, {6, 512, false}, {4, 640, false}, {8, 640, true}};
-static const TileChoice kTiles32[kNumTiles] = {
-    {32, 256, false}, {20, 384, false}, {12, 512, false}, {8, 640, false}, {16, 640, true}};
+// Tile 4 exceeds that budget (its registers spill); it is taken only when no
+// other tile holds the rows asked for (binary64 tree nodes of two R factors
+// at n > 64).  Tile 5 is wide: 8 columns per thread, 256 threads (n <= 64),
+// taken exactly for 50 < n <= 64, where it beat the 5-column tiles (fewer
+// warps sharing each column's reduction and reflector hand-off: 4,000,000 x
+// 64 FP64 164.9 -> 114.1 ms, FP32 20.4 -> 18.1 ms); at n <= 50 its padded
+// columns and fewer warps make it slower.
+struct TileChoice { int R, maxt; bool spills; int npc; };
+constexpr int kNumTiles = 6;
+static const TileChoice kTiles64[kNumTiles] = {{16, 256, false, kNpc}, {10, 384, false, kNpc}, {6, 512, false, kNpc},
+                                               {4, 640, false, kNpc},  {8, 640, true, kNpc},   {12, 256, false, 8}};
+static const TileChoice kTiles32[kNumTiles] = {{32, 256, false, kNpc}, {20, 384, false, kNpc}, {12, 512, false, kNpc},
+                                               {8, 640, false, kNpc},  {16, 640, true, kNpc},  {24, 256, false, 8}};
+static bool wide_n(int n) { return n > 50 && n <= 64; }
 
 // Registers a thread may use under __launch_bounds__(maxt, 1): each of the
 // 4 sub-partitions holds 16K registers for ceil(maxt / 128) warps.
@@ -44,14 +49,19 @@ constexpr size_t kSmemPerSM = 233472;  // 228 KB per SM, 1 KB of it reserved per
 bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int min_b) {
   if (n < 1 || n > TSQR_NMAX) return false;
   const int esz = kind == kKindF32 ? 4 : 8;
-  const int CS = (n + kNpc - 1) / kNpc;
-  const int NPAD = CS * kNpc;
   const TileChoice* tiles = kind == kKindF32 ? kTiles32 : kTiles64;
   KernelCfg best;
   best.kind = kind;
-  for (int pass = 0; pass < 2 && best.B == 0; ++pass)  // pass 1 admits the spilling tile
+  // pass 0: the tiles of this n's width; pass 1: any spill-free tile;
+  // pass 2: the spilling tile.  A wanted capacity (want_b) considers both
+  // widths from the start: the tightest fit wins.
+  for (int pass = want_b > 0 ? 1 : 0; pass < 3 && best.B == 0; ++pass)
   for (int ti = 0; ti < kNumTiles; ++ti) {
-    if (tiles[ti].spills != (pass == 1)) continue;
+    if (tiles[ti].spills != (pass == 2)) continue;
+    if (pass == 0 && (tiles[ti].npc != kNpc) != wide_n(n)) continue;
+    const int npc = tiles[ti].npc;
+    const int CS = (n + npc - 1) / npc;
+    const int NPAD = CS * npc;
     const int R = tiles[ti].R;
     for (int NRG = tiles[ti].maxt / (32 * CS); NRG >= 1; --NRG) {
       const int B = 32 * NRG * R;
@@ -87,7 +97,7 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
         take = best.B == 0 || B > best.B || (B == best.B && NT < best.NT);
       }
       if (take) {
-        best.npc = kNpc; best.R = R; best.CS = CS; best.NRG = NRG; best.NT = NT; best.B = B;
+        best.npc = npc; best.R = R; best.CS = CS; best.NRG = NRG; best.NT = NT; best.B = B;
         best.smem_qr = a; best.smem_fq = f; best.tile = ti; best.fq_rows = fq_rows;
         best.rm_rows = rm_rows; best.smem_rm = RowMulSmem(rm_rows, n, NPAD, esz, esz).total;
         best.ctas = ctas;
@@ -179,7 +189,9 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcMaxN;
   {
     const int kind_rm = esz == 4 ? kKindF32 : kKindF64;
-    const int NPAD = (int)((n + kNpc - 1) / kNpc) * kNpc;
+    // the coefficient blocks' padded width: the wider of the two tile widths'
+    // paddings (the tile chosen below may be either)
+    const int NPAD = (int)std::max((n + kNpc - 1) / kNpc * kNpc, (n + 7) / 8 * 8);
     int64_t b2 = 32;
     while (RowMulSmem((int)(2 * (b2 + 32)), (int)n, NPAD, esz, esz).total <= kSmemMax) b2 += 32;
     if (RowMulSmem((int)(2 * b2), (int)n, NPAD, esz, esz).total > kSmemMax) return TSQR_ERR_SHAPE;
@@ -189,7 +201,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
       return TSQR_ERR_SHAPE;
     P.b_rm2 = P.cfg_rm2.B < b2 ? P.cfg_rm2.B : b2;
     P.cfg_rm2.rm_rows = (int)(2 * P.b_rm2);
-    P.cfg_rm2.smem_rm = RowMulSmem(P.cfg_rm2.rm_rows, (int)n, NPAD, esz, esz).total;
+    P.cfg_rm2.smem_rm = RowMulSmem(P.cfg_rm2.rm_rows, (int)n, P.cfg_rm2.CS * P.cfg_rm2.npc, esz, esz).total;
   }
   Level l0;
   l0.rows = m;

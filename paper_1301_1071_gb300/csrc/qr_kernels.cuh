@@ -300,6 +300,19 @@ __device__ __forceinline__ void tile_update_la(T (&a)[R][NPC], const T (&d)[NPC]
   }
 }
 
+// Calls f(std::integral_constant<int, C>()) with C = min(c0, NPC): the first
+// trailing local column of a column step, as a compile-time constant for
+// the register-tile updates (c0 >= 0, warp-uniform).
+template <int NPC, int C = 0, class F>
+__device__ __forceinline__ void with_c0(int c0, F&& f) {
+  if constexpr (C >= NPC) {
+    f(std::integral_constant<int, NPC>());
+  } else {
+    if (c0 == C) f(std::integral_constant<int, C>());
+    else with_c0<NPC, C + 1>(c0, f);
+  }
+}
+
 // Y between Step 1 and Step 3 is kept in the compute format when that has the
 // storage's size (double-float pairs in place of binary64): no conversion.
 template <class S, class T>
@@ -519,14 +532,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
         T* rfn = refl + (jb ^ 1) * 8;
         const int bn = 1 + (jb ^ 1);
-        switch (c0) {
-          case 0: tile_update_la<0, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
-          case 1: tile_update_la<1, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
-          case 2: tile_update_la<2, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
-          case 3: tile_update_la<3, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
-          case 4: tile_update_la<4, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
-          default: tile_update_la<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT); break;
-        }
+        with_c0<NPC>(c0, [&](auto ic) {
+          tile_update_la<decltype(ic)::value, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn,
+                                                      taus, bn, NT);
+        });
         if (j + 1 < n) {
 #pragma unroll
           for (int q = 0; q < QH; ++q)
@@ -647,14 +656,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
         const bool own_j = (cs == j % CS);
         const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
-        switch (c0) {
-          case 0: tile_update<0, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-          case 1: tile_update<1, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-          case 2: tile_update<2, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-          case 3: tile_update<3, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-          case 4: tile_update<4, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-          default: tile_update<NPC, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg); break;
-        }
+        with_c0<NPC>(c0, [&](auto ic) {
+          tile_update<decltype(ic)::value, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg);
+        });
         // rows j and j+1 (< n <= 128) are register rows q < 4 of row group 0:
         // the thread holding row j writes R's row j, the one holding row j+1
         // publishes it (after this step's update)
@@ -768,7 +772,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
 // l mod n, l mod n + 1, ... (cyclic), so that the lanes' reads of one step
 // spread over the banks (the sum is the same up to rounding order).
 // ---------------------------------------------------------------------------
-constexpr int kMaxE = 16;  // n NPAD / (32 CS NRG) = 5 n / (32 NRG) <= 16 for n <= 100
+// entries of an n x NPAD product per thread: n NPAD / (32 CS NRG) = NPC n / (32 NRG)
+template <int NPC>
+constexpr int max_entries() { return (NPC * 100 + 31) / 32; }  // n <= 100
 
 template <class S, class T, int NPC, int R, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int n, int b, int bt, int kt, int srows,
@@ -817,6 +823,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_form_q(const S* Yg, int64_t m, int 
     const int tr0 = t == 0 ? 0 : B + (t - 1) * bt;  // first row of the tile's data in the block
     const int cnt = t == 0 ? (rows < B ? rows : B) : (rows - tr0 < bt ? rows - tr0 : bt);
     const double* Tb = Tg + (static_cast<int64_t>(blockIdx.x) * kt + t) * n * n;
+    constexpr int kMaxE = max_entries<NPC>();
     T w[kMaxE];
     const T* src = Xm;
     if (t == 0) {

@@ -27,7 +27,7 @@ def _direct(A, **kw):
 
 @pytest.mark.parametrize("m,n,b,f", [(100_000, 10, 1000, 0), (4099, 25, 0, 0), (3000, 7, 64, 2),
                                      (20_000, 50, 0, 0), (3000, 100, 0, 0), (513, 1, 0, 0),
-                                     (203_457, 25, 5000, 0), (60_000, 50, 2999, 0)])
+                                     (203_457, 25, 5000, 0), (60_000, 50, 2999, 0), (40_000, 60, 3000, 0)])
 def test_df64_parity_gaussian(m, n, b, f):
     A = ti.gaussian(m, n, 2000 + m + n)
     Q, R = _direct(A, block_rows=b, fanout=f)

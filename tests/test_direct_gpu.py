@@ -77,6 +77,8 @@ SHAPES = [
     (30_000, 32, 2500, 0),    # carried R fills one 32-row register slice
     (50_000, 33, 3000, 0),    # carried R padded to two slices (rows 33..63 zero)
     (40_000, 64, 2000, 0),
+    (30_000, 56, 0, 0),       # the wide register tile (8 columns per thread, 50 < n <= 64)
+    (25_000, 51, 3000, 0),    # wide tile, padded columns, several tiles per block
     (1_000_003, 25, 0, 0),    # default block height (two tiles per block)
 ]
 
