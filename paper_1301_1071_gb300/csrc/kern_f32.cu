@@ -14,6 +14,9 @@
 #define TSQR_R5 24  // the wide tile: 8 columns per thread (50 < n <= 64)
 #define TSQR_T5 256
 #define TSQR_N5 8
+#define TSQR_R6 10  // 10 columns per thread (n > 64)
+#define TSQR_T6 384
+#define TSQR_N6 10
 #define TSQR_LOCAL_QR_NAME launch_local_qr_f32
 #define TSQR_FORM_Q_NAME launch_form_q_f32
 #define TSQR_ROWMUL_NAME launch_rowmul_f32

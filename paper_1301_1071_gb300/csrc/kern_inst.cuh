@@ -1,5 +1,5 @@
 // kern_inst.cuh -- instantiates the TSQR kernels for one (storage, compute)
-// type pair and six register tiles (R_i rows x N_i columns per thread, at
+// type pair and seven register tiles (R_i rows x N_i columns per thread, at
 // most T_i threads per CTA so that registers x threads <= 64K; N_i = 5 unless
 // TSQR_N_i says otherwise); included once per dtype translation unit.
 // KernelCfg::tile selects the tile.
@@ -48,6 +48,7 @@ cudaError_t TSQR_LOCAL_QR_NAME(const KernelCfg& k, const void* A, int64_t m, int
     case 3: return local_qr_R<TSQR_R3, TSQR_T3, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
     case 4: return local_qr_R<TSQR_R4, TSQR_T4, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
     case 5: return local_qr_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 6: return local_qr_R<TSQR_R6, TSQR_T6, TSQR_N6>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -64,6 +65,7 @@ cudaError_t TSQR_FORM_Q_NAME(const KernelCfg& k, const void* Y, int64_t m, int n
     case 3: return form_q_R<TSQR_R3, TSQR_T3, kNpc>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
     case 4: return form_q_R<TSQR_R4, TSQR_T4, kNpc>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
     case 5: return form_q_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
+    case 6: return form_q_R<TSQR_R6, TSQR_T6, TSQR_N6>(k, y, m, n, b, bt, kt, p, T, C, cblocks, q, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -95,6 +97,7 @@ cudaError_t TSQR_ROWMUL_NAME(const KernelCfg& k, const void* X, const double* M1
     case 3: return rowmul_R<TSQR_R3, TSQR_T3, kNpc>(k, x, M1, y, M2, m, n, b, p, o, status, st);
     case 4: return rowmul_R<TSQR_R4, TSQR_T4, kNpc>(k, x, M1, y, M2, m, n, b, p, o, status, st);
     case 5: return rowmul_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, x, M1, y, M2, m, n, b, p, o, status, st);
+    case 6: return rowmul_R<TSQR_R6, TSQR_T6, TSQR_N6>(k, x, M1, y, M2, m, n, b, p, o, status, st);
     default: return cudaErrorInvalidValue;
   }
 }

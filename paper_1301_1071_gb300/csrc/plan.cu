@@ -27,12 +27,15 @@ static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 // 64 FP64 164.9 -> 114.1 ms, FP32 20.4 -> 18.1 ms); at n <= 50 its padded
 // columns and fewer warps make it slower.
 struct TileChoice { int R, maxt; bool spills; int npc; };
-constexpr int kNumTiles = 6;
+constexpr int kNumTiles = 7;
 static const TileChoice kTiles64[kNumTiles] = {{16, 256, false, kNpc}, {10, 384, false, kNpc}, {6, 512, false, kNpc},
-                                               {4, 640, false, kNpc},  {8, 640, true, kNpc},   {12, 256, false, 8}};
+                                               {4, 640, false, kNpc},  {8, 640, true, kNpc},   {12, 256, false, 8},
+                                               {5, 384, false, 10}};
 static const TileChoice kTiles32[kNumTiles] = {{32, 256, false, kNpc}, {20, 384, false, kNpc}, {12, 512, false, kNpc},
-                                               {8, 640, false, kNpc},  {16, 640, true, kNpc},  {24, 256, false, 8}};
-static bool wide_n(int n) { return n > 50 && n <= 64; }
+                                               {8, 640, false, kNpc},  {16, 640, true, kNpc},  {24, 256, false, 8},
+                                               {10, 384, false, 10}};
+// columns per thread preferred for n
+static int pref_npc(int n) { return n <= 50 ? kNpc : (n <= 64 ? 8 : 10); }
 
 // Registers a thread may use under __launch_bounds__(maxt, 1): each of the
 // 4 sub-partitions holds 16K registers for ceil(maxt / 128) warps.
@@ -58,7 +61,7 @@ bool choose_cfg(int kind, int n, KernelCfg* out, int64_t want_b, int policy, int
   for (int pass = want_b > 0 ? 1 : 0; pass < 3 && best.B == 0; ++pass)
   for (int ti = 0; ti < kNumTiles; ++ti) {
     if (tiles[ti].spills != (pass == 2)) continue;
-    if (pass == 0 && (tiles[ti].npc != kNpc) != wide_n(n)) continue;
+    if (pass == 0 && tiles[ti].npc != pref_npc(n)) continue;
     const int npc = tiles[ti].npc;
     const int CS = (n + npc - 1) / npc;
     const int NPAD = CS * npc;
@@ -191,7 +194,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
     const int kind_rm = esz == 4 ? kKindF32 : kKindF64;
     // the coefficient blocks' padded width: the wider of the two tile widths'
     // paddings (the tile chosen below may be either)
-    const int NPAD = (int)std::max((n + kNpc - 1) / kNpc * kNpc, (n + 7) / 8 * 8);
+    const int NPAD = (int)std::max(std::max((n + kNpc - 1) / kNpc * kNpc, (n + 7) / 8 * 8), (n + 9) / 10 * 10);
     int64_t b2 = 32;
     while (RowMulSmem((int)(2 * (b2 + 32)), (int)n, NPAD, esz, esz).total <= kSmemMax) b2 += 32;
     if (RowMulSmem((int)(2 * b2), (int)n, NPAD, esz, esz).total > kSmemMax) return TSQR_ERR_SHAPE;

@@ -79,6 +79,7 @@ SHAPES = [
     (40_000, 64, 2000, 0),
     (30_000, 56, 0, 0),       # the wide register tile (8 columns per thread, 50 < n <= 64)
     (25_000, 51, 3000, 0),    # wide tile, padded columns, several tiles per block
+    (40_000, 77, 2500, 0),    # 10 columns per thread (n > 64), padded, several tiles per block
     (1_000_003, 25, 0, 0),    # default block height (two tiles per block)
 ]
 
