@@ -41,7 +41,9 @@ FP32_PEAK_GFLOPS = 80540.0  # nominal GB300 FP32 CUDA-core rate (152 SMs x 128 F
 # and write Y (Step 1), read Y and write Q (Step 3); Cholesky QR and indirect
 # TSQR read A twice and write Q once; refinement repeats the method; the
 # adjoint reads Q and dQ for the Gram, then Q and dQ again and writes dA.
-ALG_PASSES = {"direct": 4, "cholqr": 3, "cholqr_ir": 6, "indirect": 3, "indirect_ir": 6, "backward": 5}
+# The R-only and singular-value-only paths read A once.
+ALG_PASSES = {"direct": 4, "cholqr": 3, "cholqr_ir": 6, "indirect": 3, "indirect_ir": 6, "backward": 5,
+              "r_only": 1, "svd_values": 1}
 
 WORKLOADS = {
     "sweep": dict(m=8_000_000, n=25, dtype="f64", kappa=1e15, block_rows=0, seed=ti.SEED_SWEEP,
@@ -458,6 +460,24 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
         out[name] = {"rows_s": m / (ms * 1e-3) if ms == ms else None, "ms": ms, "orth_error_2": err,
                      "hbm_gbs_algorithmic": (ALG_PASSES[name] * m * n * A.element_size() / (ms * 1e-3) / 1e9
                                              if ms == ms else None)}
+    # R only and singular values only (Steps 1-2, + the SVD of R): one read of A
+    for name, fn in [("r_only", lambda: T.r(A, check=False)),
+                     ("svd_values", lambda: T.svd_values(A, check=False))]:
+        ms = timed(fn)
+        out[name] = {"rows_s": m / (ms * 1e-3), "ms": ms,
+                     "hbm_gbs_algorithmic": ALG_PASSES[name] * m * n * A.element_size() / (ms * 1e-3) / 1e9}
+    # comparison only: torch.linalg.qr (cuSOLVER geqrf + orgqr on a
+    # column-major copy of A); the copy A^T -> column-major is timed alone too
+    try:
+        ms_copy = timed(lambda: A.t().contiguous())
+        ms = timed(lambda: torch.linalg.qr(A, mode="reduced"))
+        Qc, _ = torch.linalg.qr(A, mode="reduced")
+        out["cusolver_geqrf_orgqr"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "column_major_copy_ms": ms_copy,
+                                       "orth_error_2": orth(Qc), "api": "torch.linalg.qr (reduced)",
+                                       "backend": str(torch.backends.cuda.preferred_linalg_library())}
+        del Qc
+    except Exception as e:  # reported, not fatal
+        out["cusolver_geqrf_orgqr"] = {"error": f"{type(e).__name__}: {e}"}
     return out
 
 

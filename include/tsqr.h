@@ -86,7 +86,9 @@ typedef enum tsqr_op {
   TSQR_OP_CHOLQR = 2,
   TSQR_OP_INDIRECT = 3,
   TSQR_OP_BACKWARD = 4,
-  TSQR_OP_DIRECT_HOST = 5 /* tsqr_direct_host: its own row-block plan (copy chunks) */
+  TSQR_OP_DIRECT_HOST = 5, /* tsqr_direct_host: its own row-block plan (copy chunks) */
+  TSQR_OP_R = 6,           /* tsqr_r */
+  TSQR_OP_SVD_VALUES = 7   /* tsqr_svd_values */
 } tsqr_op;
 
 typedef struct tsqr_opts {
@@ -137,6 +139,35 @@ tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_
 tsqr_status tsqr_svd(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
                      void* U, int64_t ldu, double* S, double* V, int64_t ldv,
                      void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
+
+/*
+ * R factor only (Sec. II-B, the R-only TSQR reduction; Sec. III-B names it
+ * the method of choice when only R or only the singular values are wanted):
+ * Steps 1 and 2 of direct TSQR with no Householder vectors, T factors or Q2
+ * blocks kept, then the sign normalisation diag(R) >= 0.  A is read once and
+ * nothing of size m is written.
+ * In:  A (m x n, dtype, lda == n).  Out: R (n x n binary64, ldr == n, upper
+ * triangular, diag(R) >= 0) -- the R of tsqr_direct up to rounding.
+ * opts->prec: NATIVE or DF64 (FP64 data); TF32X3 only affects Step 3, which
+ * this call does not run, and computes as NATIVE.  The workspace is that of
+ * TSQR_OP_R (the same size as TSQR_OP_DIRECT).  Errors as tsqr_direct.
+ */
+tsqr_status tsqr_r(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                   double* R, int64_t ldr,
+                   void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
+
+/*
+ * Singular values (and right singular vectors) only (Sec. III-B, SVD
+ * paragraph: Steps 1 and 2 plus the SVD of R suffice, with the R-only TSQR):
+ * tsqr_r's R, then R = U_R diag(S) V^T by the one-sided Jacobi method of
+ * tsqr_svd (S descending, V's columns signed as there).  No U is formed.
+ * Out: S (n, binary64), V (n x n binary64, ldv == n), or V == NULL when only
+ * S is wanted.  A Jacobi method that does not converge sets TSQR_ERR_NOCONV
+ * in the status word.  Workspace: TSQR_OP_SVD_VALUES.
+ */
+tsqr_status tsqr_svd_values(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                            double* S, double* V, int64_t ldv,
+                            void* work, size_t work_bytes, const tsqr_opts* opts, void* stream);
 
 /*
  * Cholesky QR (Sec. II-A; Q = A R^{-1} of Sec. II-C): R = chol(A^T A) with

@@ -9,6 +9,8 @@ device is unavailable.
     Q, R = direct(A)                 # Sec. III-B direct TSQR (Alg. 2 tree)
     Qh, Rh = direct_host(Ah)         # same, host buffers, copies overlapped
     U, S, V = svd(A)                 # SVD variant, U = Q U_R
+    R = r(A)                         # R only (Sec. II-B), A read once
+    S, V = svd_values(A)             # singular values / V only (Sec. III-B)
     Q, R = cholqr(A, refine=0)       # Cholesky QR (+ refinement)
     Q, R = indirect_refine(A, 1)     # indirect TSQR + refinement
     dA = backward(Q, R, dQ, dR)      # QR adjoint
@@ -22,7 +24,7 @@ import threading
 
 import torch
 
-__all__ = ["direct", "direct_host", "direct_static", "svd", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
+__all__ = ["direct", "direct_host", "direct_static", "svd", "r", "svd_values", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
            "workspace_size", "launch_count", "library_path", "load", "STATUS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,7 +34,7 @@ _lib = None
 
 F64, F32 = 0, 1
 PREC = {"native": 0, "df64": 1, "tf32x3": 2}
-OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD, OP_DIRECT_HOST = 0, 1, 2, 3, 4, 5
+OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD, OP_DIRECT_HOST, OP_R, OP_SVD_VALUES = range(8)
 NMAX = 100
 STATUS = {0: "TSQR_OK", 1: "TSQR_ERR_ARG", 2: "TSQR_ERR_SHAPE", 3: "TSQR_ERR_ALIGN",
           4: "TSQR_ERR_WORKSPACE", 5: "TSQR_ERR_CUDA", 6: "TSQR_ERR_NOT_SPD", 7: "TSQR_ERR_SINGULAR",
@@ -73,6 +75,8 @@ def load():
             "tsqr_direct_static": [P, I64, I64, I64, I32, P, I64, P, I64, OP, P],
             "tsqr_direct_host": [P, I64, I64, I32, P, P, P, P, SZ, OP, P, P],
             "tsqr_svd": [P, I64, I64, I64, I32, P, I64, P, P, I64, P, SZ, OP, P],
+            "tsqr_r": [P, I64, I64, I64, I32, P, I64, P, SZ, OP, P],
+            "tsqr_svd_values": [P, I64, I64, I64, I32, P, P, I64, P, SZ, OP, P],
             "cholqr": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
             "tsqr_indirect_refine": [P, I64, I64, I64, I32, P, I64, P, I64, I32, P, SZ, OP, P],
             "tsqr_backward": [P, P, P, P, I64, I64, I32, P, P, SZ, OP, P],
@@ -257,6 +261,40 @@ def svd(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tenso
     _raise(st, "tsqr_svd")
     _status(work, "tsqr_svd", check)
     return U, S, V
+
+
+def r(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
+      check: bool = True, prec: str = "native"):
+    """R factor only (Steps 1-2, no Q): returns R, n x n float64, diag(R) >= 0."""
+    m, n = _check_tall(A)
+    A = A.contiguous()
+    lib = load()
+    R = torch.empty(n, n, dtype=torch.float64, device=A.device)
+    work = _workspace(OP_R, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
+    o = _opts(block_rows, fanout, prec=prec)
+    st = lib.tsqr_r(_ptr(A), m, n, n, _dtype_code(A), _ptr(R), n, _ptr(work), work.numel(), ctypes.byref(o),
+                    _stream(A.device))
+    _raise(st, "tsqr_r")
+    _status(work, "tsqr_r", check)
+    return R
+
+
+def svd_values(A: torch.Tensor, want_v: bool = True, block_rows: int = 0, fanout: int = 0,
+               work: torch.Tensor | None = None, check: bool = True, prec: str = "native"):
+    """Singular values (descending, float64) and, if ``want_v``, V (n x n
+    float64) without forming U: returns (S, V) (V is None when not wanted)."""
+    m, n = _check_tall(A)
+    A = A.contiguous()
+    lib = load()
+    S = torch.empty(n, dtype=torch.float64, device=A.device)
+    V = torch.empty(n, n, dtype=torch.float64, device=A.device) if want_v else None
+    work = _workspace(OP_SVD_VALUES, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
+    o = _opts(block_rows, fanout, prec=prec)
+    st = lib.tsqr_svd_values(_ptr(A), m, n, n, _dtype_code(A), _ptr(S), _ptr(V), n, _ptr(work), work.numel(),
+                             ctypes.byref(o), _stream(A.device))
+    _raise(st, "tsqr_svd_values")
+    _status(work, "tsqr_svd_values", check)
+    return S, V
 
 
 def cholqr(A: torch.Tensor, refine: int = 0, work: torch.Tensor | None = None, check: bool = True):

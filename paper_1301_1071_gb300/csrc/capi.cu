@@ -25,6 +25,10 @@ cudaError_t launch_local_qr_df64(const KernelCfg&, const void*, int64_t, int, in
                                  double*, int32_t*, cudaStream_t);
 cudaError_t launch_form_q_df64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, const double*,
                                const double*, int64_t, void*, int32_t*, cudaStream_t);
+cudaError_t launch_local_r_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, double*,
+                               int32_t*, cudaStream_t);
+cudaError_t launch_local_r_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, double*,
+                               int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f64(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f32(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
@@ -53,9 +57,15 @@ cudaError_t launch_gram(int esz, const void* X, const void* Y, int64_t m, int n,
 
 cudaError_t launch_local_qr(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
                             int64_t p, void* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+  // R only (Y == NULL) on a one-row-group tile: the form without Gram dot products
+  const bool r_only = Y == nullptr && k.NRG == 1;
   switch (k.kind) {
-    case kKindF64: return launch_local_qr_f64(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
-    case kKindF32: return launch_local_qr_f32(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
+    case kKindF64:
+      return r_only ? launch_local_r_f64(k, A, m, n, b, bt, kt, p, Rst, status, st)
+                    : launch_local_qr_f64(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
+    case kKindF32:
+      return r_only ? launch_local_r_f32(k, A, m, n, b, bt, kt, p, Rst, status, st)
+                    : launch_local_qr_f32(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
     case kKindDF64: return launch_local_qr_df64(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
     default: return cudaErrorInvalidValue;
   }
@@ -101,6 +111,12 @@ tsqr_status check_opts(const tsqr_opts* o) {
   if (o->prec != TSQR_PREC_NATIVE && o->prec != TSQR_PREC_DF64 && o->prec != TSQR_PREC_TF32X3) return TSQR_ERR_ARG;
   if (o->block_rows < 0 || o->tree_fanout < 0 || o->tree_fanout == 1) return TSQR_ERR_ARG;
   return TSQR_OK;
+}
+
+// Ops whose plan follows opts->prec (the others compute in the data's type).
+bool op_takes_prec(int op) {
+  return op == TSQR_OP_DIRECT || op == TSQR_OP_SVD || op == TSQR_OP_DIRECT_HOST || op == TSQR_OP_R ||
+         op == TSQR_OP_SVD_VALUES;
 }
 
 char* at(void* work, size_t off) { return static_cast<char*>(work) + off; }
@@ -336,7 +352,7 @@ tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, 
 
 tsqr_status plan_for(int op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* o, size_t work_bytes,
                      const void* work, Plan* P) {
-  const int prec = (o && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD)) ? o->prec : 0;
+  const int prec = (o && op_takes_prec(op)) ? o->prec : 0;
   int rc = make_plan(m, n, esz_of(dtype), o ? o->block_rows : 0, o ? o->tree_fanout : 0, P, prec,
                      device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
@@ -375,8 +391,7 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
   if (esz == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
-  const int prec =
-      (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD || op == TSQR_OP_DIRECT_HOST)) ? opts->prec : 0;
+  const int prec = (opts && op_takes_prec(op)) ? opts->prec : 0;
   Plan P;
   int chunks = 1;
   int rc = op == TSQR_OP_DIRECT_HOST
@@ -393,6 +408,8 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
     case TSQR_OP_CHOLQR: *launches = 4 * (1 + refine_steps) + refine_steps; break;  // gram, reduce, chol, rowmul (+ combine)
     case TSQR_OP_INDIRECT: *launches = (L + 3) * (1 + refine_steps) + refine_steps; break;
     case TSQR_OP_BACKWARD: *launches = 4; break;              // gram, reduce, prep, rowmul
+    case TSQR_OP_R: *launches = L + 1; break;                 // L levels up (R only), sign fix
+    case TSQR_OP_SVD_VALUES: *launches = L + 2; break;        // + Jacobi SVD
     default: return TSQR_ERR_ARG;
   }
   return TSQR_OK;
@@ -415,9 +432,8 @@ tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
   if (esz == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
-  if (op < TSQR_OP_DIRECT || op > TSQR_OP_DIRECT_HOST) return TSQR_ERR_ARG;
-  const int prec =
-      (opts && (op == TSQR_OP_DIRECT || op == TSQR_OP_SVD || op == TSQR_OP_DIRECT_HOST)) ? opts->prec : 0;
+  if (op < TSQR_OP_DIRECT || op > TSQR_OP_SVD_VALUES) return TSQR_ERR_ARG;
+  const int prec = (opts && op_takes_prec(op)) ? opts->prec : 0;
   Plan P;
   int chunks = 1;
   int rc = op == TSQR_OP_DIRECT_HOST
@@ -493,6 +509,42 @@ tsqr_status tsqr_svd(const void* A, int64_t m, int64_t n, int64_t lda, int32_t d
   TSQR_TRY(run_direct(P, A, U, Rt, n, work, st, opts, [&](double* ctop) {
     return launch_jacobi_svd(Rt, n, ni, ctop, S, V, ldv, status, st) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA;
   }));
+  return finish(work, opts, st);
+}
+
+tsqr_status tsqr_r(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, double* R, int64_t ldr,
+                   void* work, size_t work_bytes, const tsqr_opts* opts, void* stream) {
+  tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
+  if (s != TSQR_OK) return s;
+  if (!R) return TSQR_ERR_ARG;
+  if (ldr != n) return TSQR_ERR_ALIGN;
+  Plan P;
+  TSQR_TRY(plan_for(TSQR_OP_R, m, n, dtype, opts, work_bytes, work, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TSQR_CUDA(cudaMemsetAsync(status_ptr(work), 0, sizeof(int32_t), st));
+  // Sec. II-B: Steps 1-2 keep only the R factors; the top R is sign-normalised
+  TSQR_TRY(run_r_only(P, esz_of(dtype), A, R, work, st));
+  return finish(work, opts, st);
+}
+
+tsqr_status tsqr_svd_values(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, double* S, double* V,
+                            int64_t ldv, void* work, size_t work_bytes, const tsqr_opts* opts, void* stream) {
+  tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
+  if (s != TSQR_OK) return s;
+  if (!S) return TSQR_ERR_ARG;
+  if (V && ldv != n) return TSQR_ERR_ALIGN;
+  Plan P;
+  TSQR_TRY(plan_for(TSQR_OP_SVD_VALUES, m, n, dtype, opts, work_bytes, work, &P));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t* status = status_ptr(work);
+  const size_t nn = (size_t)n * n;
+  double* Rt = reinterpret_cast<double*>(at(work, P.off_small));
+  double* Vt = V ? V : Rt + nn;  // V not wanted: a scratch slot takes it
+  double* ctop = reinterpret_cast<double*>(at(work, P.off_ctop));
+  TSQR_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
+  // Sec. III-B: the singular values of A are those of R (Steps 1-2 + SVD of R)
+  TSQR_TRY(run_r_only(P, esz_of(dtype), A, Rt, work, st));
+  TSQR_CUDA(launch_jacobi_svd(Rt, n, static_cast<int>(n), ctop, S, Vt, n, status, st));
   return finish(work, opts, st);
 }
 

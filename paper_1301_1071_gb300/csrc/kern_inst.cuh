@@ -1,7 +1,9 @@
 // kern_inst.cuh -- instantiates the TSQR kernels for one (storage, compute)
 // type pair and seven register tiles (R_i rows x N_i columns per thread, at
 // most T_i threads per CTA so that registers x threads <= 64K; N_i = 5 unless
-// TSQR_N_i says otherwise); included once per dtype translation unit.
+// TSQR_N_i says otherwise); included once per translation unit, which names
+// the launchers it wants (TSQR_LOCAL_QR_NAME and TSQR_FORM_Q_NAME,
+// TSQR_LOCAL_R_NAME, TSQR_ROWMUL_NAME with TSQR_GRAM_NAME).
 // KernelCfg::tile selects the tile.
 #pragma once
 
@@ -11,6 +13,7 @@
 
 namespace tsqr {
 
+#ifdef TSQR_LOCAL_QR_NAME
 template <int R, int MAXT, int NPC>
 static cudaError_t local_qr_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
                               int64_t p, TSQR_S* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
@@ -69,6 +72,39 @@ cudaError_t TSQR_FORM_Q_NAME(const KernelCfg& k, const void* Y, int64_t m, int n
     default: return cudaErrorInvalidValue;
   }
 }
+#endif  // TSQR_LOCAL_QR_NAME
+
+#ifdef TSQR_LOCAL_R_NAME
+// R-only local QR (Y, T and the Gram dot products left out) for the
+// one-row-group tiles (the look-ahead loop); other tiles take the general
+// kernel with Y == NULL.
+template <int R, int MAXT, int NPC>
+static cudaError_t local_r_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                             int64_t p, double* Rst, int32_t* status, cudaStream_t st) {
+  if (k.NT > MAXT || k.NRG != 1) return cudaErrorInvalidConfiguration;
+  auto fn = k_local_qr<TSQR_S, TSQR_T, NPC, R, MAXT, true, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_qr);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)p, k.NT, k.smem_qr, st>>>(A, m, n, (int)b, (int)bt, kt, k.CS, k.NRG, nullptr, Rst, nullptr,
+                                           status);
+  return cudaGetLastError();
+}
+
+cudaError_t TSQR_LOCAL_R_NAME(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                              int64_t p, double* Rst, int32_t* status, cudaStream_t st) {
+  const TSQR_S* a = static_cast<const TSQR_S*>(A);
+  switch (k.tile) {
+    case 0: return local_r_R<TSQR_R0, TSQR_T0, kNpc>(k, a, m, n, b, bt, kt, p, Rst, status, st);
+    case 1: return local_r_R<TSQR_R1, TSQR_T1, kNpc>(k, a, m, n, b, bt, kt, p, Rst, status, st);
+    case 2: return local_r_R<TSQR_R2, TSQR_T2, kNpc>(k, a, m, n, b, bt, kt, p, Rst, status, st);
+    case 3: return local_r_R<TSQR_R3, TSQR_T3, kNpc>(k, a, m, n, b, bt, kt, p, Rst, status, st);
+    case 4: return local_r_R<TSQR_R4, TSQR_T4, kNpc>(k, a, m, n, b, bt, kt, p, Rst, status, st);
+    case 5: return local_r_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, a, m, n, b, bt, kt, p, Rst, status, st);
+    case 6: return local_r_R<TSQR_R6, TSQR_T6, TSQR_N6>(k, a, m, n, b, bt, kt, p, Rst, status, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+#endif  // TSQR_LOCAL_R_NAME
 
 #ifdef TSQR_ROWMUL_NAME
 template <int R, int MAXT, int NPC>

@@ -13,8 +13,8 @@ namespace tsqr {
 
 static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
 
-// Register-tile heights and their thread bounds (must match kern_f64.cu,
-// kern_df64.cu and kern_f32.cu).  Each SM sub-partition holds 16K registers
+// Register-tile heights and their thread bounds (must match tiles_f64.h and
+// tiles_f32.h).  Each SM sub-partition holds 16K registers
 // and a CTA of MAXT threads puts ceil(MAXT/128) warps on each, so the
 // per-thread limit is 255 / 168 / 128 / 96 registers at MAXT = 256 / 384 /
 // 512 / 640; R x 5 values (x2 registers for 8-byte and double-float values)

@@ -204,6 +204,21 @@ __device__ __forceinline__ void column_dots(const T (&a)[R][NPC], const T* xcur,
   }
 }
 
+// The dot products of column_dots for the local columns c >= C0 only (the
+// others are set to zero): the R-only form needs no Gram entries, so the
+// columns at or left of the pivot (Householder vectors) are skipped.
+template <int C0, int NPC, int R, class T>
+__device__ __forceinline__ void column_dots_from(const T (&a)[R][NPC], const T* xcur, int rbase, T (&s)[NPC]) {
+#pragma unroll
+  for (int c = 0; c < NPC; ++c) s[c] = T(0);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const T xq = xcur[rbase + 32 * q];
+#pragma unroll
+    for (int c = C0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
+  }
+}
+
 // Trailing update of the thread's tile for column j, with the first trailing
 // local column C0 known at compile time: a[q][c] -= d[c] x_q for c >= C0.
 // The thread's rows are rbase + 32 q (q < R); the published pivot column x_j
@@ -335,13 +350,17 @@ using YStore = typename std::conditional<std::is_same<T, df64>::value, df64, S>:
 // zero, so the Householder vectors of tile t are [I; V_t] and only V_t is
 // stored (over A_t's rows of Y).
 // LA (look-ahead form) is launched exactly when NRG == 1.
+// GRAM = false (look-ahead form, binary64 / binary32 compute, Y == NULL):
+// the R-only form skips the dot products that only give Gram entries (about
+// a third of the column loop's FMAs); R is the same bit for bit.
 // Launch: blockDim = 32*CS*NRG <= MAXT, gridDim = p, dynamic smem = LocalQrSmem.
 // ---------------------------------------------------------------------------
-template <class S, class T, int NPC, int R, int MAXT, bool LA>
+template <class S, class T, int NPC, int R, int MAXT, bool LA, bool GRAM = true>
 __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, int64_t m, int n, int b, int bt,
                                                        int kt, int CS, int NRG, S* Y, double* __restrict__ Rst,
                                                        double* __restrict__ Tst, int32_t* status) {
   static_assert(R >= 4, "rows < 128 must lie in row group 0");
+  static_assert(GRAM || (LA && !std::is_same<T, df64>::value), "the R-only form is the binary look-ahead loop");
   constexpr int QH = 4;  // register rows that can hold rows < n (n <= 128)
   extern __shared__ __align__(128) unsigned char smem[];
   const int NT = blockDim.x;
@@ -492,10 +511,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         f.tau = rf[3];
         f.ident = rf[4] != T(0);
 
-        // phase A: s = x_j^T A for this warp's columns
+        // phase A: s = x_j^T A for this warp's columns (R-only: the columns
+        //      right of the pivot only)
         {
           T s[NPC];
-          column_dots(a, xcur, rbase, s);
+          if constexpr (GRAM) {
+            column_dots(a, xcur, rbase, s);
+          } else {
+            const int c0a = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
+            with_c0<NPC>(c0a, [&](auto ic) { column_dots_from<decltype(ic)::value>(a, xcur, rbase, s); });
+          }
           TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
         }
         __syncwarp();
@@ -519,7 +544,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
               gram[mycol * n + j] = f.ident ? pc : rl;
             } else if (mycol == j) {
               gram[mycol * n + j] = f.beta;
-            } else {
+            } else if (GRAM) {
               gram[mycol * n + j] = f.scal * (Sc - f.beta * pc);
             }
           }
@@ -685,7 +710,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       }
     }
 
-    if (Y != nullptr) {
+    if (GRAM && Y != nullptr) {
       // ---- the Gram entries v_i^T v_j (i < j) and tau_j of the compact-WY
       //      form, binary64, into the upper triangle of the tile's T slot (the
       //      strictly lower part is never read); k_build_t turns them into T

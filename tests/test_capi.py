@@ -96,7 +96,7 @@ def test_workspace_size_rejects(lib, m, n, dt, b, f, want):
 def test_plans_for_every_n(lib, dt):
     """Every op has a plan (tile choice, tree, workspace) for n = 1 .. NMAX."""
     for n in range(1, 101):
-        for op in range(6):
+        for op in range(8):
             st, b = _ws(lib, op, 300_000, n, dt)
             assert st == 0 and b > 0, (op, n, st)
 
@@ -121,3 +121,16 @@ def test_host_path_plan(lib):
     assert big_host >= big_dev + 3 * 3
     st, b = _ws(lib, 5, 8_000_000, 25, 0)
     assert st == 0 and 0 < b < 8_000_000 * 25 * 8 // 4
+
+
+def test_r_only_plans(lib):
+    """tsqr_r (op 6) launches one local QR per tree level and the sign fix;
+    tsqr_svd_values (op 7) adds the Jacobi SVD; both take the workspace of
+    tsqr_direct (op 0)."""
+    for m, n, b in [(100_000, 10, 1000), (8_000_000, 25, 0), (3000, 7, 64)]:
+        direct = _launches(lib, 0, m, n, 0, block_rows=b)
+        levels = (direct - 1) // 3
+        assert _launches(lib, 6, m, n, 0, block_rows=b) == levels + 1
+        assert _launches(lib, 7, m, n, 0, block_rows=b) == levels + 2
+        assert _ws(lib, 6, m, n, 0, block_rows=b) == _ws(lib, 0, m, n, 0, block_rows=b)
+    assert _ws(lib, 8, 1000, 10, 0)[0] == 1  # unknown op
