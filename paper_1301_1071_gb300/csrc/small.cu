@@ -242,60 +242,144 @@ cudaError_t launch_bwd_prep(const double* R, const double* dR, const double* G, 
 // index wins a tie).  The top coefficient Ctop, holding the sign matrix D on
 // entry, becomes D U_R, so that Step 3 writes U = Q U_R directly.
 //
-// One CTA.  The pairs of a round follow the round-robin (circle) tournament:
-// position 0 is fixed, positions 1..np-1 rotate by one per round, pair k is
-// (position k, position np-1-k).  A round is two phases: one thread per pair
-// forms the three dot products and the rotation (c, s) -- the binary64 unit
-// serves whole warps, so one lane per pair spends a warp instruction on 32
-// pairs where a warp per pair spends it on one -- and then every thread
-// rotates (pair, element) items of X and J.
-__global__ void k_jacobi_svd(const double* __restrict__ R, int64_t ldr, int n, double* __restrict__ Ctop,
-                             double* __restrict__ S, double* __restrict__ V, int64_t ldv, int32_t* status) {
-  extern __shared__ __align__(16) double sm[];
-  const int np = (n + 1) & ~1;   // even number of positions (a dummy column when n is odd)
-  const int npair = np / 2;
-  const int ld = n | 1;          // odd column stride: one thread per pair reads without bank pile-ups
-  double* x = sm;                // column-major X = R^T: column c (row c of R) at x[c * ld]
-  double* jm = x + np * ld;      // column-major J
-  double* pc = jm + np * ld;     // per pair: c, s
-  double* ps = pc + npair;
-  double* sv = ps + npair;       // singular values (unsorted)
-  double* d = sv + np;           // diagonal of the incoming Ctop (the sign matrix D)
-  int* pp = reinterpret_cast<int*>(d + np);  // per pair: columns p < q (q = -1: no rotation)
-  int* pq = pp + npair;
-  int* rank = pq + npair;
+// One cluster of kJacCl CTAs (kJacCl SMs' binary64 units); CTA r holds rows
+// [r nr, (r + 1) nr) of X and J.  The pairs of a round follow the
+// round-robin (circle) tournament: position 0 is fixed, positions 1..np-1
+// rotate by one per round, pair k is (position k, position np-1-k).  A round:
+//   A. one thread per pair forms the partial dot products (x_p.x_p, x_q.x_q,
+//      x_p.x_q) over the CTA's rows and stores them into every CTA's shared
+//      memory (distributed shared memory), double-buffered by round parity;
+//   B. one cluster barrier; each CTA sums the kJacCl partials in rank order
+//      -- the same values in the same order in every CTA, so every CTA takes
+//      bit-identical rotation decisions and (c, s) -- one thread per pair;
+//   C. every thread rotates (pair, row) items of its CTA's rows of X and J.
+// The binary64 unit serves whole warps, so one thread per pair spends a warp
+// instruction on 32 pairs where a warp per pair would spend it on one.
+// Every CTA runs the same number of cluster barriers (the convergence test is
+// the same in all of them); the last one precedes the exit, so no CTA leaves
+// while another still writes into its shared memory.
+constexpr int kJacCl = 8;    // CTAs per cluster (portable cluster size)
+constexpr int kJacNT = 256;  // threads per CTA
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// shared-memory address of the same variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_map(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+struct JacobiSmem {
+  int np, npair, nr, ld;
+  size_t x, j, part, fin, pc, ps, d, sv, sg, pp, pq, rank, bytes;
+  __host__ __device__ JacobiSmem(int n) {
+    np = (n + 1) & ~1;
+    npair = np / 2;
+    nr = (n + kJacCl - 1) / kJacCl;  // rows per CTA
+    ld = nr | 1;                     // odd column stride (thread-per-pair reads spread over banks)
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o += (bytes + 15) / 16 * 16; return at; };
+    x = take(sizeof(double) * np * ld);
+    j = take(sizeof(double) * np * ld);
+    part = take(sizeof(double) * 2 * kJacCl * npair * 3);
+    fin = take(sizeof(double) * kJacCl * np * 3);
+    pc = take(sizeof(double) * npair);
+    ps = take(sizeof(double) * npair);
+    d = take(sizeof(double) * nr);
+    sv = take(sizeof(double) * np);
+    sg = take(sizeof(double) * np);
+    pp = take(sizeof(int) * npair);
+    pq = take(sizeof(int) * npair);
+    rank = take(sizeof(int) * np);
+    bytes = o;
+  }
+};
+
+__global__ void __cluster_dims__(kJacCl, 1, 1) __launch_bounds__(kJacNT)
+    k_jacobi_svd(const double* __restrict__ R, int64_t ldr, int n, double* __restrict__ Ctop,
+                 double* __restrict__ S, double* __restrict__ V, int64_t ldv, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char jsm[];
+  const JacobiSmem L(n);
+  const int np = L.np, npair = L.npair, nr = L.nr, ld = L.ld;
+  double* x = reinterpret_cast<double*>(jsm + L.x);     // column c, local row i at x[c * ld + i]
+  double* jm = reinterpret_cast<double*>(jsm + L.j);
+  double* part = reinterpret_cast<double*>(jsm + L.part);  // [parity][rank][pair][3]
+  double* fin = reinterpret_cast<double*>(jsm + L.fin);    // [rank][column][3]
+  double* pc = reinterpret_cast<double*>(jsm + L.pc);
+  double* ps = reinterpret_cast<double*>(jsm + L.ps);
+  double* d = reinterpret_cast<double*>(jsm + L.d);
+  double* sv = reinterpret_cast<double*>(jsm + L.sv);
+  double* sgn = reinterpret_cast<double*>(jsm + L.sg);
+  int* pp = reinterpret_cast<int*>(jsm + L.pp);
+  int* pq = reinterpret_cast<int*>(jsm + L.pq);
+  int* rnk = reinterpret_cast<int*>(jsm + L.rank);
   __shared__ int rotated;
   const int tid = threadIdx.x, NT = blockDim.x;
+  const int me = static_cast<int>(cluster_ctarank());
+  const int r0 = me * nr;
+  const int nl = max(0, min(n, r0 + nr) - r0);  // rows held here
+  // X(i, c) = R(c, i): local row i of column c
   for (int idx = tid; idx < np * ld; idx += NT) {
-    const int c = idx / ld, i = idx - c * ld;
-    x[idx] = (c < n && i < n && i >= c) ? R[c * ldr + i] : 0.0;
-    jm[idx] = (c < n && c == i) ? 1.0 : 0.0;
+    const int c = idx / ld, i = idx - c * ld, g = r0 + i;
+    x[idx] = (c < n && i < nl && g >= c) ? R[c * ldr + g] : 0.0;
+    jm[idx] = (c < n && i < nl && c == g) ? 1.0 : 0.0;
   }
-  for (int t = tid; t < np; t += NT) d[t] = (t < n) ? Ctop[t * n + t] : 0.0;
+  for (int i = tid; i < nl; i += NT) d[i] = Ctop[(r0 + i) * n + r0 + i];
   if (tid == 0) rotated = 0;
-  __syncthreads();
+  cluster_barrier();  // every CTA of the cluster has started (its shared memory exists)
   const double tol = DBL_EPSILON * n;
   const int m1 = np - 1;
   bool converged = false;
+  int par = 0;
   for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
-    for (int round = 0; round < m1; ++round) {
-      // phase 1: one thread per pair
+    for (int round = 0; round < m1; ++round, par ^= 1) {
+      double* pb = part + par * kJacCl * npair * 3;
+      // A: partial dots over this CTA's rows, to every CTA
       if (tid < npair) {
-        // column at position t after `round` rotations of positions 1..np-1
         auto col_at = [&](int t) { return t == 0 ? 0 : ((t - 1 - round) % m1 + m1) % m1 + 1; };
         int p = col_at(tid), q = col_at(np - 1 - tid);
         if (p > q) { const int t = p; p = q; q = t; }
         pp[tid] = p;
-        int qq = -1;
-        if (q < n) {  // else the dummy column
+        pq[tid] = q;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        if (q < n) {
           const double* xp = x + p * ld;
           const double* xq = x + q * ld;
-          double al = 0.0, be = 0.0, ga = 0.0;
-          for (int i = 0; i < n; ++i) {
+          for (int i = 0; i < nl; ++i) {
             const double a = xp[i], b = xq[i];
             al = fma(a, a, al);
             be = fma(b, b, be);
             ga = fma(a, b, ga);
+          }
+        }
+        double* slot = pb + (me * npair + tid) * 3;
+        for (int k = 0; k < kJacCl; ++k) {
+          st_cluster(cluster_map(slot, k), al);
+          st_cluster(cluster_map(slot + 1, k), be);
+          st_cluster(cluster_map(slot + 2, k), ga);
+        }
+      }
+      cluster_barrier();
+      // B: the full dots (rank order) and the rotation, one thread per pair
+      if (tid < npair) {
+        int q = pq[tid];
+        if (q < n) {
+          double al = 0.0, be = 0.0, ga = 0.0;
+          for (int k = 0; k < kJacCl; ++k) {
+            const double* sl = pb + (k * npair + tid) * 3;
+            al += sl[0];
+            be += sl[1];
+            ga += sl[2];
           }
           if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
             const double zeta = (be - al) / (2.0 * ga);
@@ -303,16 +387,19 @@ __global__ void k_jacobi_svd(const double* __restrict__ R, int64_t ldr, int n, d
             const double c = 1.0 / sqrt(1.0 + t * t);
             pc[tid] = c;
             ps[tid] = c * t;
-            qq = q;
             rotated = 1;
+          } else {
+            q = -1;
           }
+        } else {
+          q = -1;  // the dummy column
         }
-        pq[tid] = qq;
+        pq[tid] = q;
       }
       __syncthreads();
-      // phase 2: rotate columns p and q of X and J, (pair, element) items
-      for (int idx = tid; idx < npair * n; idx += NT) {
-        const int k = idx / n, i = idx - k * n;
+      // C: rotate columns p and q of this CTA's rows of X and J
+      for (int idx = tid; idx < npair * nl; idx += NT) {
+        const int k = idx / nl, i = idx - k * nl;
         const int q = pq[k];
         if (q < 0) continue;
         const int p = pp[k];
@@ -326,51 +413,66 @@ __global__ void k_jacobi_svd(const double* __restrict__ R, int64_t ldr, int n, d
       }
       __syncthreads();
     }
-    converged = (rotated == 0);
-    __syncthreads();  // every thread has read `rotated`
+    converged = (rotated == 0);  // the same decision in every CTA
+    __syncthreads();
     if (tid == 0) rotated = 0;
     __syncthreads();
   }
-  if (!converged && tid == 0) set_status(status, TSQR_ERR_NOCONV);
+  if (!converged && tid == 0 && me == 0) set_status(status, TSQR_ERR_NOCONV);
+  // column norms and the largest-|.| entry of each column over this CTA's
+  // rows (lowest row on ties), to every CTA
   for (int c = tid; c < n; c += NT) {
-    double s2 = 0.0;
-    for (int i = 0; i < n; ++i) s2 = fma(x[c * ld + i], x[c * ld + i], s2);
+    double s2 = 0.0, best = -1.0, val = 0.0;
+    int bi = 0;
+    for (int i = 0; i < nl; ++i) {
+      const double v = x[c * ld + i];
+      s2 = fma(v, v, s2);
+      if (fabs(v) > best) { best = fabs(v); bi = r0 + i; val = v; }
+    }
+    double* slot = fin + (me * np + c) * 3;
+    for (int k = 0; k < kJacCl; ++k) {
+      st_cluster(cluster_map(slot, k), s2);
+      st_cluster(cluster_map(slot + 1, k), nl > 0 ? best : -1.0);
+      st_cluster(cluster_map(slot + 2, k), val);
+    }
+    (void)bi;
+  }
+  cluster_barrier();  // the last access to another CTA's shared memory is above
+  for (int c = tid; c < n; c += NT) {
+    double s2 = 0.0, best = -1.0, val = 0.0;
+    for (int k = 0; k < kJacCl; ++k) {  // rank order = row order: strict > keeps the lowest row
+      const double* sl = fin + (k * np + c) * 3;
+      s2 += sl[0];
+      if (sl[1] > best) { best = sl[1]; val = sl[2]; }
+    }
     sv[c] = sqrt(s2);
+    sgn[c] = val < 0.0 ? -1.0 : 1.0;
   }
   __syncthreads();
-  // rank by descending singular value (ties by index); sign from v's largest entry
-  double* sgn = pc;  // np values (pc and ps are contiguous and free from here)
+  // rank by descending singular value (ties by index)
   for (int c = tid; c < n; c += NT) {
     int r = 0;
     for (int k = 0; k < n; ++k)
       if (sv[k] > sv[c] || (sv[k] == sv[c] && k < c)) ++r;
-    int imax = 0;
-    for (int i = 1; i < n; ++i)
-      if (fabs(x[c * ld + i]) > fabs(x[c * ld + imax])) imax = i;
-    const double sg = x[c * ld + imax] < 0.0 ? -1.0 : 1.0;
-    const double inv = sv[c] > 0.0 ? 1.0 / sv[c] : 0.0;
-    S[r] = sv[c];
-    for (int i = 0; i < n; ++i) V[i * ldv + r] = sg * x[c * ld + i] * inv;
-    rank[c] = r;
-    sgn[c] = sg;
+    rnk[c] = r;
+    if (me == 0) S[r] = sv[c];
   }
   __syncthreads();
-  // new top coefficient D U_R (U_R = J, column c signed and moved to rank(c))
-  for (int idx = tid; idx < n * n; idx += NT) {
-    const int i = idx / n, c = idx % n;
-    Ctop[i * n + rank[c]] = d[i] * sgn[c] * jm[c * ld + i];
+  // this CTA's rows of V = U_X (signed, normalised) and of D U_R = D J (signed)
+  for (int idx = tid; idx < nl * n; idx += NT) {
+    const int i = idx / n, c = idx - i * n, g = r0 + i;
+    const double inv = sv[c] > 0.0 ? 1.0 / sv[c] : 0.0;
+    V[g * ldv + rnk[c]] = sgn[c] * x[c * ld + i] * inv;
+    Ctop[g * n + rnk[c]] = d[i] * sgn[c] * jm[c * ld + i];
   }
 }
 
 cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop, double* S, double* V,
                               int64_t ldv, int32_t* status, cudaStream_t st) {
-  const int np = (n + 1) & ~1;
-  const int ld = n | 1;
-  const size_t smem = (2 * (size_t)np * ld + np + 2 * (size_t)np) * sizeof(double) +
-                      (size_t)(np + np) * sizeof(int) + 16;
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const JacobiSmem L(n);
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
-  k_jacobi_svd<<<1, 512, smem, st>>>(R, ldr, n, Ctop, S, V, ldv, status);
+  k_jacobi_svd<<<kJacCl, kJacNT, L.bytes, st>>>(R, ldr, n, Ctop, S, V, ldv, status);
   return cudaGetLastError();
 }
 
