@@ -186,8 +186,8 @@ tsqr_status run_tree(const Plan& P, double* R, int64_t ldr, void* work, cudaStre
     const Level& lv = P.levels[l];
     const double* C = (l == L - 1) ? ctop : S(l);
     const int64_t cb = (l == L - 1) ? 1 : lv.p;
-    const cudaError_t e =
-        launch_form_q(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, T(l), C, cb, S(l - 1), status, st);
+    // a node is f stacked triangles: the structured product (tree.cu)
+    const cudaError_t e = launch_tree_down(S(l - 1), lv.rows, n, static_cast<int>(lv.b / n), lv.p, T(l), C, cb, st);
     if (e != cudaSuccess) return TSQR_ERR_CUDA;
   }
   return TSQR_OK;

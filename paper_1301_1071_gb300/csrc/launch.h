@@ -20,6 +20,13 @@ cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, i
                           int64_t p, const double* T, const double* C, int64_t cblocks, void* Q,
                           int32_t* status, cudaStream_t st);
 
+// Step-2 down pass of one tree level (binary64): node b's rows of Y (f
+// stacked blocks of n rows, the last node possibly fewer) become its
+// children's coefficient blocks from C (cblocks == 1: one block for all),
+// using Y = [I; V_2; ...; V_f] with V_k upper triangular.
+cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, const double* T, const double* C,
+                             int64_t cblocks, cudaStream_t st);
+
 // Step 3 for binary32 data on the tensor cores (3xTF32), n <= 64; the block
 // and tile geometry (b, B = the Step-1 register tile, bt, kt) of Step 1.
 cudaError_t launch_form_q_tc(float* Y, int64_t m, int n, int64_t b, int B, int64_t bt, int kt, int64_t p,
