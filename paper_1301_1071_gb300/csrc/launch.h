@@ -20,6 +20,16 @@ cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, i
                           int64_t p, const double* T, const double* C, int64_t cblocks, void* Q,
                           int32_t* status, cudaStream_t st);
 
+// Step-2 up pass of one tree level (binary64): node b = f stacked
+// triangular blocks of X (rows x n) -> its R (raw signs) into Rout's block
+// b; with Y (may alias X): the Householder vectors over the node's rows and
+// tau + Gram entries into the node's T slot (Tst); Y == NULL: R only.
+// tree_up_fits: the node fits one CTA's shared memory (else the row-block
+// kernel takes the level).
+bool tree_up_fits(int n, int f);
+cudaError_t launch_tree_up(const double* X, int64_t rows, int n, int f, int64_t p, double* Y, double* Rout,
+                           double* Tst, cudaStream_t st);
+
 // Step-2 down pass of one tree level (binary64): node b's rows of Y (f
 // stacked blocks of n rows, the last node possibly fewer) become its
 // children's coefficient blocks from C (cblocks == 1: one block for all),

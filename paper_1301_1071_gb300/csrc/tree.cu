@@ -1,6 +1,7 @@
-// tree.cu -- the Step-2 tree's down pass (Sec. III-B Step 2, Alg. 2): the
-// coefficient blocks of a level's children from the level's coefficient
-// block C, one CTA per tree node, binary64.
+// tree.cu -- the Step-2 tree (Sec. III-B Step 2, Alg. 2) on the structure of
+// its nodes, one CTA per node, binary64: the up pass (Householder QR of f
+// stacked triangles) and the down pass (the coefficient blocks of a level's
+// children from the level's coefficient block C).
 //
 // A tree node stacks f upper-triangular R factors, [R_1; ...; R_f].  Its
 // Householder vectors keep that structure exactly: the entries of R_1 below
@@ -127,6 +128,144 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
   }
 }
 
+// ---------------------------------------------------------------------------
+// Up pass: Householder QR of a node [R_1; ...; R_f] (f upper-triangular n x n
+// blocks; the last node may have fewer).  Column j's reflector involves row
+// j of R_1 and rows 0..j of every other block -- the other entries of the
+// column are zero and stay zero (no reflector reaches them) -- so each column
+// step costs (f - 1)(j + 1)(n - j) FMAs for the dots and as many for the
+// update, where the dense factorisation of the f n x n node costs f n (n - j).
+// Reflector convention as the row-block kernel: for the column's squared norm
+// S and its pivot alpha, beta = -copysign(sqrt(S), alpha), v = x / (alpha -
+// beta) with v_j = 1, tau = (beta - alpha) / beta; a zero column gives the
+// identity (tau = 0).  Outputs as the row-block kernel's: the node's R (raw
+// signs, zeros below the diagonal) into Rout's block, the Householder vectors
+// over the node's rows of Y (blocks 2..f; block 1 holds R and is never read),
+// tau_j and the Gram entries v_i^T v_j (i < j) into the node's T slot
+// (k_build_t forms T).  WANT_Y = false: R only.
+// The node sits in shared memory, row r at M[r * ldm].
+template <bool WANT_Y>
+__global__ void __launch_bounds__(512) k_tree_up(const double* X, int64_t rows, int n, int f, double* Y,
+                                                 double* Rout, double* Tst) {
+  extern __shared__ __align__(16) double usm[];
+  const int ldm = n + 1;
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t node = blockIdx.x;
+  const int64_t r0 = node * f * n;
+  const int nb = static_cast<int>((rows - r0) / n < f ? (rows - r0) / n : f);
+  double* M = usm;                      // nb n rows
+  double* part = M + nb * n * ldm;      // n x (f - 1) partial dots
+  double* wv = part + n * (f - 1);      // tau w_c per column
+  double* red = wv + n;                 // 32 warp sums
+  double* sc = red + 32;                // beta, scal, tau, taus[n]
+  double* taus = sc + 4;
+  const double* Xn = X + r0 * n;
+  for (int idx = tid; idx < nb * n * n; idx += NT) {
+    const int r = idx / n, c = idx - r * n;
+    M[r * ldm + c] = c >= r % n ? Xn[idx] : 0.0;  // the blocks are triangular; below: exact zeros
+  }
+  __syncthreads();
+  const int nsub = nb - 1;  // blocks below the first
+  for (int j = 0; j < n; ++j) {
+    const int ej = nsub * (j + 1);  // sub-column entries (k >= 1, lr <= j)
+    // squared norm of the sub-column
+    double ss = 0.0;
+    for (int e = tid; e < ej; e += NT) {
+      const int k = 1 + e / (j + 1), lr = e - (k - 1) * (j + 1);
+      const double v = M[(k * n + lr) * ldm + j];
+      ss = fma(v, v, ss);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      double s2 = 0.0;
+      for (int w = 0; w < (NT >> 5); ++w) s2 += red[w];  // fixed order
+      const double alpha = M[j * ldm + j];
+      const double sigma = sqrt(fma(alpha, alpha, s2));
+      if (sigma == 0.0) {
+        sc[0] = alpha; sc[1] = 0.0; sc[2] = 0.0;
+      } else {
+        const double beta = alpha >= 0.0 ? -sigma : sigma;
+        sc[0] = beta;
+        sc[1] = 1.0 / (alpha - beta);
+        sc[2] = (beta - alpha) / beta;
+      }
+      taus[j] = sc[2];
+      M[j * ldm + j] = sc[0];
+    }
+    __syncthreads();
+    const double scal = sc[1], tau = sc[2];
+    // v: the scaled sub-column
+    for (int e = tid; e < ej; e += NT) {
+      const int k = 1 + e / (j + 1), lr = e - (k - 1) * (j + 1);
+      M[(k * n + lr) * ldm + j] *= scal;
+    }
+    __syncthreads();
+    const int nc = n - 1 - j;  // trailing columns
+    if (nc > 0 && tau != 0.0) {
+      // partial dots v_k^T a_c over block k, items (c, k)
+      for (int it = tid; it < nc * nsub; it += NT) {
+        const int k = 1 + it / nc, c = j + 1 + (it - (k - 1) * nc);
+        const double* col = M + static_cast<size_t>(k) * n * ldm;
+        double acc = 0.0;
+        for (int lr = 0; lr <= j; ++lr) acc = fma(col[lr * ldm + j], col[lr * ldm + c], acc);
+        part[c * (f - 1) + (k - 1)] = acc;
+      }
+      __syncthreads();
+      // w_c = a_jc + sum_k (block order); row j of R
+      for (int c = j + 1 + tid; c < n; c += NT) {
+        double w = M[j * ldm + c];
+        for (int k = 0; k < nsub; ++k) w += part[c * (f - 1) + k];
+        const double tw = tau * w;
+        wv[c] = tw;
+        M[j * ldm + c] -= tw;
+      }
+      __syncthreads();
+      // a_c -= (tau w_c) v on the sub-column rows, items (k, lr, c)
+      const int per = (j + 1) * nc;
+      for (int it = tid; it < nsub * per; it += NT) {
+        const int k = 1 + it / per;
+        const int rem = it - (k - 1) * per;
+        const int lr = rem / nc, c = j + 1 + (rem - lr * nc);
+        double* row = M + (static_cast<size_t>(k) * n + lr) * ldm;
+        row[c] = fma(-wv[c], row[j], row[c]);
+      }
+      __syncthreads();
+    }
+  }
+  // R of the node (raw signs)
+  double* Rn = Rout + node * n * n;
+  for (int idx = tid; idx < n * n; idx += NT) {
+    const int i = idx / n, c = idx - i * n;
+    Rn[idx] = c >= i ? M[i * ldm + c] : 0.0;
+  }
+  if constexpr (WANT_Y) {
+    // Householder vectors over the node's rows (block 1: R, never read)
+    double* Yn = Y + r0 * n;
+    for (int idx = tid; idx < nb * n * n; idx += NT) {
+      const int r = idx / n, c = idx - r * n;
+      Yn[idx] = M[r * ldm + c];
+    }
+    // tau and the Gram entries G(i, c) = sum_k sum_{lr <= i} v_i(lr) v_c(lr), i < c
+    double* Tn = Tst + node * n * n;
+    for (int idx = tid; idx < n * n; idx += NT) {
+      const int i = idx / n, c = idx - i * n;
+      if (c < i) continue;
+      double g = taus[i];
+      if (c > i) {
+        g = 0.0;
+        for (int k = 1; k < nb; ++k) {
+          const double* blk = M + static_cast<size_t>(k) * n * ldm;
+          for (int lr = 0; lr <= i; ++lr) g = fma(blk[lr * ldm + i], blk[lr * ldm + c], g);
+        }
+      }
+      Tn[idx] = g;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, const double* T, const double* C,
@@ -149,6 +288,23 @@ cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, c
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)p, NT, smem, st>>>(Y, rows, n, f, T, C, cblocks, KB);
+  return cudaGetLastError();
+}
+
+size_t tree_up_smem(int n, int f) {
+  return (static_cast<size_t>(f) * n * (n + 1) + static_cast<size_t>(n) * (f - 1) + n + 32 + 4 + n) * sizeof(double);
+}
+
+bool tree_up_fits(int n, int f) { return f >= 2 && tree_up_smem(n, f) <= kSmemMax; }
+
+cudaError_t launch_tree_up(const double* X, int64_t rows, int n, int f, int64_t p, double* Y, double* Rout,
+                           double* Tst, cudaStream_t st) {
+  if (!tree_up_fits(n, f)) return cudaErrorInvalidConfiguration;
+  const size_t smem = tree_up_smem(n, f);
+  auto fn = Y ? k_tree_up<true> : k_tree_up<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)p, 512, smem, st>>>(X, rows, n, f, Y, Rout, Tst);
   return cudaGetLastError();
 }
 
