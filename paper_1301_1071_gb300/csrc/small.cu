@@ -490,6 +490,7 @@ cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop,
 // are skipped (warp-uniform).
 constexpr int kBuildTSegs = 4;  // 32-row segments: n <= 128
 constexpr int kBuildTPad = 64;  // spare entries after each warp's triangle (no read ever reaches them)
+constexpr int kBuildTStage = 8;  // rows of a slot whose loads are issued together
 
 template <class F>
 __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
@@ -501,8 +502,25 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
   const int64_t blk = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + wl;
   if (blk >= p) return;  // warp-level work only: no CTA barrier below
   double* g = Tst + blk * n * n;
-  for (int i = 0; i < n; ++i)
-    for (int c = i + lane; c < n; c += 32) t[c * (c + 1) / 2 + i] = static_cast<F>(g[i * n + c]);
+  // stage the upper triangle kBuildTStage rows at a time: all their loads are
+  // in flight before the first store (one DRAM round trip per row otherwise)
+  for (int i0 = 0; i0 < n; i0 += kBuildTStage) {
+    double v[kBuildTStage][kBuildTSegs];
+#pragma unroll
+    for (int r = 0; r < kBuildTStage; ++r)
+#pragma unroll
+      for (int s = 0; s < kBuildTSegs; ++s) {
+        const int i = i0 + r, c = i + lane + 32 * s;
+        v[r][s] = (i < n && c < n) ? g[i * n + c] : 0.0;
+      }
+#pragma unroll
+    for (int r = 0; r < kBuildTStage; ++r)
+#pragma unroll
+      for (int s = 0; s < kBuildTSegs; ++s) {
+        const int i = i0 + r, c = i + lane + 32 * s;
+        if (i < n && c < n) t[c * (c + 1) / 2 + i] = static_cast<F>(v[r][s]);
+      }
+  }
   __syncwarp();
   for (int j = 1; j < n; ++j) {
     const F* gj = t + j * (j + 1) / 2;  // column j: G(l, j) for l < j, tau_j at l = j
@@ -571,8 +589,21 @@ __global__ void __launch_bounds__(32 * kBuildTWarps) k_build_t_cta(double* __res
   F* part = t + ((np + 1) & ~1);  // kBuildTWarps x 32 kBuildTSegs partial sums
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double* g = Tst + static_cast<int64_t>(blockIdx.x) * n * n;
-  for (int i = 0; i < n; ++i)
-    for (int c = i + threadIdx.x; c < n; c += blockDim.x) t[c * (c + 1) / 2 + i] = static_cast<F>(g[i * n + c]);
+  // n <= 128 < blockDim.x: one entry per thread and row; kBuildTStage rows'
+  // loads in flight together
+  for (int i0 = 0; i0 < n; i0 += kBuildTStage) {
+    double v[kBuildTStage];
+#pragma unroll
+    for (int r = 0; r < kBuildTStage; ++r) {
+      const int i = i0 + r, c = i + static_cast<int>(threadIdx.x);
+      v[r] = (i < n && c < n) ? g[i * n + c] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < kBuildTStage; ++r) {
+      const int i = i0 + r, c = i + static_cast<int>(threadIdx.x);
+      if (i < n && c < n) t[c * (c + 1) / 2 + i] = static_cast<F>(v[r]);
+    }
+  }
   __syncthreads();
   for (int j = 1; j < n; ++j) {
     const F* gj = t + j * (j + 1) / 2;
