@@ -161,6 +161,26 @@ tsqr_status mark(const tsqr_opts* o, int i, cudaStream_t st) {
   } while (0)
 #define TSQR_CUDA(x) TSQR_TRY((x) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA)
 
+// A second stream and its fork / join events for one call (created and
+// released per call; the stream and events are released by the driver once
+// their work has completed).
+constexpr size_t kOverlapTBytes = static_cast<size_t>(TSQR_STATIC_WORK_BYTES);  // 16 MiB of T slots
+
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool make() {
+    return cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
+  }
+  ~SideStream() {
+    if (join) cudaEventDestroy(join);
+    if (fork) cudaEventDestroy(fork);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 // Step 2 (Alg. 2) after Step 1 has filled the level-0 stack: the tree up
 // (each level's stack is the tall input of the next), the top sign fix into
 // R, `extra` on the top coefficient, and the tree down (the Q of level l's
@@ -216,8 +236,24 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   if (launch_local_qr(P.cfg0, A, P.m, n, l0.b, l0.bt, l0.kt, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
     return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  if (launch_build_t(T(0), l0.p * l0.kt, n, P.esz == 4, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  // The row blocks' T factors are read only by Step 3 and the tree reads only
+  // the stack of R factors, so a large T build runs on a side stream beside
+  // the tree (whose upper levels leave most SMs idle); Step 3 waits for both.
+  // Small builds stay on the stream: they take less time than the side
+  // stream's set-up is worth (and no workspace of tsqr_direct_static, at most
+  // TSQR_STATIC_WORK_BYTES, reaches the threshold).
+  const bool overlap_t = static_cast<size_t>(l0.p) * l0.kt * n * n * sizeof(double) >= kOverlapTBytes;
+  SideStream side;
+  if (overlap_t) {
+    if (!side.make()) return TSQR_ERR_CUDA;
+    TSQR_CUDA(cudaEventRecord(side.fork, st));
+    TSQR_CUDA(cudaStreamWaitEvent(side.s, side.fork, 0));
+  }
+  if (launch_build_t(T(0), l0.p * l0.kt, n, P.esz == 4, overlap_t ? side.s : st) != cudaSuccess)
+    return TSQR_ERR_CUDA;
+  if (overlap_t) TSQR_CUDA(cudaEventRecord(side.join, side.s));
   TSQR_TRY(run_tree(P, R, ldr, work, st, extra));
+  if (overlap_t) TSQR_CUDA(cudaStreamWaitEvent(st, side.join, 0));
   // Step 3: Q_i = Q1_i Q2_i over the Y_i held in Q.
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
   const double* C0 = (L == 1) ? ctop : S(0);
