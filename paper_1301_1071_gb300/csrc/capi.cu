@@ -146,8 +146,9 @@ tsqr_status check_tall(const void* A, int64_t m, int64_t n, int64_t lda, int32_t
   return TSQR_OK;
 }
 
-// Direct TSQR on a built plan.  ctop_extra (optional) is launched between the
-// sign fix and the down pass (the SVD variant folds U_R into Ctop there).
+// Direct TSQR on a built plan.  extra(ctop, stream) is launched on the tree's
+// stream between the sign fix and the down pass (the SVD variant folds U_R
+// into Ctop there).
 tsqr_status mark(const tsqr_opts* o, int i, cudaStream_t st) {
   if (!o || !o->stage_events || !o->stage_events[i]) return TSQR_OK;
   return cudaEventRecord(static_cast<cudaEvent_t>(o->stage_events[i]), st) == cudaSuccess ? TSQR_OK
@@ -161,16 +162,18 @@ tsqr_status mark(const tsqr_opts* o, int i, cudaStream_t st) {
   } while (0)
 #define TSQR_CUDA(x) TSQR_TRY((x) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA)
 
-// A second stream and its fork / join events for one call (created and
-// released per call; the stream and events are released by the driver once
-// their work has completed).
+// A second stream (the device's highest priority) and its fork / join events
+// for one call (created and released per call; the stream and events are
+// released by the driver once their work has completed).
 constexpr size_t kOverlapTBytes = static_cast<size_t>(TSQR_STATIC_WORK_BYTES);  // 16 MiB of T slots
 
 struct SideStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   bool make() {
-    return cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+    int least = 0, greatest = 0;
+    return cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+           cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) == cudaSuccess &&
            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
   }
@@ -207,7 +210,7 @@ tsqr_status run_tree(const Plan& P, double* R, int64_t ldr, void* work, cudaStre
     if (launch_build_t(T(l), lv.p * lv.kt, n, false, st) != cudaSuccess) return TSQR_ERR_CUDA;
   }
   if (launch_sign_fix(S(L - 1), n, R, ldr, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;
-  if (extra(ctop) != TSQR_OK) return TSQR_ERR_CUDA;
+  if (extra(ctop, st) != TSQR_OK) return TSQR_ERR_CUDA;
   for (size_t l = L - 1; l >= 1; --l) {
     const Level& lv = P.levels[l];
     const double* C = (l == L - 1) ? ctop : S(l);
@@ -237,23 +240,28 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
     return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
   // The row blocks' T factors are read only by Step 3 and the tree reads only
-  // the stack of R factors, so a large T build runs on a side stream beside
-  // the tree (whose upper levels leave most SMs idle); Step 3 waits for both.
-  // Small builds stay on the stream: they take less time than the side
-  // stream's set-up is worth (and no workspace of tsqr_direct_static, at most
-  // TSQR_STATIC_WORK_BYTES, reaches the threshold).
+  // the stack of R factors, so for a large T build the tree runs on a side
+  // stream of the device's highest priority beside it: the block scheduler
+  // starts the tree's pending CTAs ahead of the T build's as SMs free up, and
+  // the T build fills the SMs the tree's upper levels leave idle.  Step 3
+  // waits for both.  Small builds stay in line: they take less time than the
+  // side stream's set-up is worth (and no workspace of tsqr_direct_static, at
+  // most TSQR_STATIC_WORK_BYTES, reaches the threshold).
   const bool overlap_t = static_cast<size_t>(l0.p) * l0.kt * n * n * sizeof(double) >= kOverlapTBytes;
   SideStream side;
+  cudaStream_t tree_st = st;
   if (overlap_t) {
     if (!side.make()) return TSQR_ERR_CUDA;
     TSQR_CUDA(cudaEventRecord(side.fork, st));
     TSQR_CUDA(cudaStreamWaitEvent(side.s, side.fork, 0));
+    tree_st = side.s;
   }
-  if (launch_build_t(T(0), l0.p * l0.kt, n, P.esz == 4, overlap_t ? side.s : st) != cudaSuccess)
-    return TSQR_ERR_CUDA;
-  if (overlap_t) TSQR_CUDA(cudaEventRecord(side.join, side.s));
-  TSQR_TRY(run_tree(P, R, ldr, work, st, extra));
-  if (overlap_t) TSQR_CUDA(cudaStreamWaitEvent(st, side.join, 0));
+  if (launch_build_t(T(0), l0.p * l0.kt, n, P.esz == 4, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  TSQR_TRY(run_tree(P, R, ldr, work, tree_st, extra));
+  if (overlap_t) {
+    TSQR_CUDA(cudaEventRecord(side.join, side.s));
+    TSQR_CUDA(cudaStreamWaitEvent(st, side.join, 0));
+  }
   // Step 3: Q_i = Q1_i Q2_i over the Y_i held in Q.
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
   const double* C0 = (L == 1) ? ctop : S(0);
@@ -372,7 +380,7 @@ tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, 
     TSQR_CUDA(launch_build_t(T0 + b0 * l0.kt * nn, pcnt * l0.kt, n, P.esz == 4, st));
   }
   // Step 2, then R back to the host
-  TSQR_TRY(run_tree(P, Rd, n, work, st, [](double*) { return TSQR_OK; }));
+  TSQR_TRY(run_tree(P, Rd, n, work, st, [](double*, cudaStream_t) { return TSQR_OK; }));
   TSQR_CUDA(cudaMemcpyAsync(Rh, Rd, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
   // Step 3, chunk by chunk, each chunk of Q copied back behind the next
   const double* C0 = (L == 1) ? ctop : S0;
@@ -507,7 +515,7 @@ tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   if (!work || work_bytes < P.bytes || !aligned16(work)) return TSQR_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  s = run_direct(P, A, Q, R, ldr, work, st, opts, [](double*) { return TSQR_OK; });
+  s = run_direct(P, A, Q, R, ldr, work, st, opts, [](double*, cudaStream_t) { return TSQR_OK; });
   if (s != TSQR_OK) return s;
   return finish(work, opts, st);
 }
@@ -552,8 +560,8 @@ tsqr_status tsqr_svd(const void* A, int64_t m, int64_t n, int64_t lda, int32_t d
   double* Rt = reinterpret_cast<double*>(at(work, P.off_small));
   int32_t* status = status_ptr(work);
   const int ni = static_cast<int>(n);
-  TSQR_TRY(run_direct(P, A, U, Rt, n, work, st, opts, [&](double* ctop) {
-    return launch_jacobi_svd(Rt, n, ni, ctop, S, V, ldv, status, st) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA;
+  TSQR_TRY(run_direct(P, A, U, Rt, n, work, st, opts, [&](double* ctop, cudaStream_t ts) {
+    return launch_jacobi_svd(Rt, n, ni, ctop, S, V, ldv, status, ts) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA;
   }));
   return finish(work, opts, st);
 }
