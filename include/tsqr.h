@@ -34,6 +34,13 @@
  *    NOCONV) are written to the status word in the workspace: read them with
  *    tsqr_read_status(), or set opts->sync = 1 to have the call synchronise
  *    the stream and return that status.  No kernel traps.
+ *  - tsqr_direct, tsqr_svd (and tsqr_direct_static through tsqr_direct),
+ *    when the row blocks' T factors cover at least 16 MiB, run the Step-2
+ *    tree on an internal stream of the device's highest priority, forked
+ *    from `stream` after Step 1 and joined back into it before Step 3 (one
+ *    stream and two events created and released per call).  To the caller
+ *    the call is still ordered on `stream` alone: earlier work on it precedes
+ *    the call, and later work waits for all of it.
  *  - Calls that share a workspace must be ordered (same stream).
  */
 #ifndef TSQR_GB300_H
