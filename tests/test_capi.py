@@ -134,3 +134,72 @@ def test_r_only_plans(lib):
         assert _launches(lib, 7, m, n, 0, block_rows=b) == levels + 2
         assert _ws(lib, 6, m, n, 0, block_rows=b) == _ws(lib, 0, m, n, 0, block_rows=b)
     assert _ws(lib, 8, 1000, 10, 0)[0] == 1  # unknown op
+
+
+def _r_fn(lib):
+    f = lib.tsqr_r
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(Opts), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return f
+
+
+def _sv_fn(lib):
+    f = lib.tsqr_svd_values
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(Opts),
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return f
+
+
+# Stand-in addresses: every case below is rejected by the host-side checks
+# before any launch, so nothing is ever read or written through them.
+_P16 = 1 << 20        # 16-byte aligned
+_P8 = (1 << 20) + 8   # not 16-byte aligned
+
+
+@pytest.mark.parametrize("args,want", [
+    (dict(A=None), 1),                    # NULL A
+    (dict(R=None), 1),                    # NULL R
+    (dict(dtype=7), 1),                   # unknown dtype
+    (dict(n=101), 2),                     # n > NMAX
+    (dict(m=5), 2),                       # m < n
+    (dict(lda=11), 3),                    # lda != n
+    (dict(A=_P8), 3),                     # A not 16-byte aligned
+    (dict(ldr=9), 3),                     # ldr != n
+    (dict(work=None), 4),                 # no workspace
+    (dict(work_bytes=64), 4),             # workspace too small
+    (dict(prec=2), 1),                    # TF32X3 on FP64 data
+])
+def test_r_only_rejects_before_any_launch(lib, args, want):
+    """tsqr_r's argument, shape, alignment and workspace errors (Sec. II-B
+    R-only TSQR) are returned synchronously, before any launch."""
+    a = dict(A=_P16, m=1000, n=10, lda=10, dtype=0, R=_P16, ldr=10, work=_P16, work_bytes=1 << 30, prec=0)
+    a.update(args)
+    if "lda" not in args and "n" in args:
+        a["lda"] = a["n"]
+        a["ldr"] = a["n"]
+    o = Opts(0, 0, 0, None, a["prec"], 0)
+    st = _r_fn(lib)(a["A"], a["m"], a["n"], a["lda"], a["dtype"], a["R"], a["ldr"], a["work"], a["work_bytes"],
+                    ctypes.byref(o), None)
+    assert st == want
+
+
+@pytest.mark.parametrize("args,want", [
+    (dict(S=None), 1),                    # NULL S
+    (dict(ldv=9), 3),                     # V given with ldv != n
+    (dict(n=0), 2),                       # n < 1
+    (dict(work=None), 4),                 # no workspace
+])
+def test_svd_values_rejects_before_any_launch(lib, args, want):
+    """tsqr_svd_values (Sec. III-B, singular values only) checks its
+    arguments before any launch; V may be NULL (only S wanted)."""
+    a = dict(A=_P16, m=1000, n=10, lda=10, S=_P16, V=_P16, ldv=10, work=_P16, work_bytes=1 << 30)
+    a.update(args)
+    if "n" in args:
+        a["lda"] = a["ldv"] = a["n"]
+    o = Opts(0, 0, 0, None, 0, 0)
+    st = _sv_fn(lib)(a["A"], a["m"], a["n"], a["lda"], 0, a["S"], a["V"], a["ldv"], a["work"], a["work_bytes"],
+                     ctypes.byref(o), None)
+    assert st == want
