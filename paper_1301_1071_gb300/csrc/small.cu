@@ -492,7 +492,10 @@ constexpr int kBuildTSegs = 4;  // 32-row segments: n <= 128
 constexpr int kBuildTPad = 64;  // spare entries after each warp's triangle (no read ever reaches them)
 constexpr int kBuildTStage = 8;  // rows of a slot whose loads are issued together
 
-template <class F>
+// SEGS >= ceil(n / 32) 32-row segments (2, 3 or kBuildTSegs): the staging
+// and the accumulators are sized for this n, which keeps the registers, and
+// so the warps resident per SM, in line with the work (n = 64: two segments).
+template <class F, int SEGS>
 __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
   F* tsm = reinterpret_cast<F*>(tsm_raw);
@@ -505,18 +508,18 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
   // stage the upper triangle kBuildTStage rows at a time: all their loads are
   // in flight before the first store (one DRAM round trip per row otherwise)
   for (int i0 = 0; i0 < n; i0 += kBuildTStage) {
-    double v[kBuildTStage][kBuildTSegs];
+    double v[kBuildTStage][SEGS];
 #pragma unroll
     for (int r = 0; r < kBuildTStage; ++r)
 #pragma unroll
-      for (int s = 0; s < kBuildTSegs; ++s) {
+      for (int s = 0; s < SEGS; ++s) {
         const int i = i0 + r, c = i + lane + 32 * s;
         v[r][s] = (i < n && c < n) ? g[i * n + c] : 0.0;
       }
 #pragma unroll
     for (int r = 0; r < kBuildTStage; ++r)
 #pragma unroll
-      for (int s = 0; s < kBuildTSegs; ++s) {
+      for (int s = 0; s < SEGS; ++s) {
         const int i = i0 + r, c = i + lane + 32 * s;
         if (i < n && c < n) t[c * (c + 1) / 2 + i] = static_cast<F>(v[r][s]);
       }
@@ -525,9 +528,9 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
   for (int j = 1; j < n; ++j) {
     const F* gj = t + j * (j + 1) / 2;  // column j: G(l, j) for l < j, tau_j at l = j
     const F tj = gj[j];
-    F acc[kBuildTSegs][2];
+    F acc[SEGS][2];
 #pragma unroll
-    for (int s = 0; s < kBuildTSegs; ++s) acc[s][0] = acc[s][1] = F(0);
+    for (int s = 0; s < SEGS; ++s) acc[s][0] = acc[s][1] = F(0);
     const F* tl = t;  // column l of T, advanced by l + 1 entries per step
     int l = 0;
     // four columns per pass: their loads are issued before the FMAs use them
@@ -537,7 +540,7 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
       const F* t3 = t2 + l + 3;
       const F g0 = gj[l], g1 = gj[l + 1], g2 = gj[l + 2], g3 = gj[l + 3];
 #pragma unroll
-      for (int s = 0; s < kBuildTSegs; ++s) {
+      for (int s = 0; s < SEGS; ++s) {
         if (32 * s > l + 3) break;
         const int i = lane + 32 * s;
         F x0 = F(0), x1 = F(0), x2 = F(0), x3 = F(0);  // rows below a column's diagonal add 0
@@ -553,7 +556,7 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
     for (; l < j; ++l) {
       const F gl = gj[l];
 #pragma unroll
-      for (int s = 0; s < kBuildTSegs; ++s) {
+      for (int s = 0; s < SEGS; ++s) {
         if (32 * s > l) break;  // rows of this and later segments all exceed l
         const int i = lane + 32 * s;
         if (i <= l) {  // static accumulator indices keep acc in registers
@@ -566,7 +569,7 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
     __syncwarp();
     F* tcol = t + j * (j + 1) / 2;
 #pragma unroll
-    for (int s = 0; s < kBuildTSegs; ++s) {
+    for (int s = 0; s < SEGS; ++s) {
       const int i = lane + 32 * s;
       if (i < j) tcol[i] = -tj * (acc[s][0] + acc[s][1]);
     }
@@ -664,9 +667,17 @@ static cudaError_t build_t_typed(double* Tst, int64_t p, int n, int sms, cudaStr
   warps = warps < 1 ? 1 : (warps > 16 ? 16 : warps);
   const size_t smem = static_cast<size_t>(warps) * per_warp;
   const int64_t grid = (p + warps - 1) / warps;
-  cudaError_t e = cudaFuncSetAttribute(k_build_t<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // n <= 32 keeps the four-segment form: its registers hold the build to one
+  // CTA per SM, which leaves room for the tree's CTA beside it when the build
+  // runs concurrently with the tree (with one-segment staging the build filled
+  // every SM's shared memory and the tree waited: Step 2 of 8,000,000 x 25
+  // FP64 0.98 -> 1.10 ms)
+  const int segs = (n + 31) / 32;
+  auto fn = segs == 2 ? k_build_t<F, 2> : segs == 3 ? k_build_t<F, 3> : k_build_t<F, kBuildTSegs>;
+  if (segs > kBuildTSegs) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_build_t<F><<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(Tst, p, n);
+  fn<<<static_cast<unsigned>(grid), 32 * warps, smem, st>>>(Tst, p, n);
   return cudaGetLastError();
 }
 
