@@ -221,6 +221,59 @@ def test_indirect_refine_matches_and_degrades():
     assert st == 0 and oracle.orth_error(Q1)[0] < 1e-13  # one refinement step repairs it
 
 
+@pytest.mark.parametrize("kappa,seed", [(1e6, 51), (1e10, 52)])
+def test_refinement_combines_r2_times_r1(kappa, seed):
+    """Iterative refinement (Sec. I; Sec. II-C) ends with Q = Q0 R2^{-1} and
+    R = R2 R1, so Q R = Q0 R1 = A holds by construction whatever R2 is.  At
+    kappa >= 1e6 the second factor R2 is far from I (||R2 - I|| ~ kappa eps
+    for indirect TSQR, ~ kappa^2 eps for Cholesky QR), so a combine in the
+    wrong order (R1 R2) leaves a residual and an R error of order
+    ||R2 - I|| (1e-10 .. 1e-6 here), far above these bars."""
+    A = ti.conditioned(2000, 10, kappa, seed)
+    Ro = oracle.householder_r(A)
+    st, Q0, R1 = oracle.indirect_refine(A, 0)
+    assert st == 0
+    R2 = oracle.householder_r(Q0)
+    assert np.linalg.norm(R2 - np.eye(10)) > 1e-10        # the pin is not vacuous
+    runs = [("indirect", oracle.indirect_refine(A, 1))]
+    if kappa * kappa * EPS < 0.1:                          # Cholesky QR survives kappa = 1e6 only
+        runs.append(("cholqr", oracle.cholqr(A, 1)))
+    for name, (st, Q, R) in runs:
+        assert st == 0, name
+        rF, r2 = oracle.residual(A, Q, R)
+        assert rF <= 10 * 10 * EPS and r2 <= 10 * 10 * EPS, (name, rF, r2)
+        # the refined R is the unique R of A (Sec. II-A) to working accuracy
+        assert _rel(R, Ro) <= 1e-12, (name, _rel(R, Ro))
+        assert oracle.orth_error(Q)[0] <= 1e-13, name
+
+
+def test_residual_two_norm_known_answer():
+    """rel2 = ||A - QR||_2 / ||R||_2 (Sec. I-B) on a rank-one perturbation of
+    known 2-norm: A = H diag(s) V^T has exactly orthonormal H (Hadamard
+    columns), so ||R||_2 = ||A||_2 = s_max; its exact QR factors applied to
+    A + delta u w^T (unit u, w) leave the residual delta u w^T, whose 2-norm
+    is delta and whose Frobenius norm is delta as well."""
+    n = 6
+    H = _hadamard(7)[:, :n] / np.sqrt(128.0)
+    s = np.array([4.0, 2.0, 1.0, 0.5, 0.25, 0.125])
+    V = ti.random_orthogonal(n, 73)
+    A = (H * s) @ V.T
+    Q, R = oracle.householder_qr(A)
+    u = ti.gaussian(128, 1, 74)[:, 0]
+    u /= np.linalg.norm(u)
+    w = ti.gaussian(n, 1, 75)[:, 0]
+    w /= np.linalg.norm(w)
+    delta = 1e-9
+    Ap = A + delta * np.outer(u, w)
+    rF, r2 = oracle.residual(Ap, Q, R)
+    assert abs(r2 - delta / 4.0) <= 1e-5 * delta / 4.0, r2
+    assert abs(rF - delta / np.linalg.norm(Ap)) <= 1e-5 * rF
+    # a rank-one residual: 2-norm and Frobenius norm agree (a squared or
+    # unsquared 2-norm would not)
+    rF2, r22 = oracle.residual(A + 1e-7 * np.outer(u, w), Q, R)
+    assert abs(r22 * 4.0 - 1e-7) <= 1e-5 * 1e-7
+
+
 def test_upper_inverse():
     R = np.triu(ti.gaussian(6, 6, 49)) + 3 * np.eye(6)
     X = oracle.upper_inverse(R)
