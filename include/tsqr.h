@@ -38,9 +38,11 @@
  *    when the row blocks' T factors cover at least 16 MiB, run the Step-2
  *    tree on an internal stream of the device's highest priority, forked
  *    from `stream` after Step 1 and joined back into it before Step 3 (one
- *    stream and two events created and released per call).  To the caller
- *    the call is still ordered on `stream` alone: earlier work on it precedes
- *    the call, and later work waits for all of it.
+ *    such stream per device, created on the first large call and kept until
+ *    the process exits; two events created and released per call).  To the
+ *    caller the call is still ordered on `stream` alone: earlier work on it
+ *    precedes the call, and later work waits for all of it -- also when the
+ *    call returns an error after the fork.
  *  - Calls that share a workspace must be ordered (same stream).
  */
 #ifndef TSQR_GB300_H
@@ -83,8 +85,15 @@ typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
  * TF32X3: TSQR_F32 data only.  Step 1 as NATIVE; the Step-3 product
  *         Y_i W_i runs on the tensor cores as 3xTF32 split precision
  *         (Y = Yh + Yl, W = Wh + Wl rounded to TF32; Y W ~ Yh Wh + Yh Wl +
- *         Yl Wh, binary32 accumulation) for n <= 64 (NATIVE Step 3 above). */
-typedef enum tsqr_prec { TSQR_PREC_NATIVE = 0, TSQR_PREC_DF64 = 1, TSQR_PREC_TF32X3 = 2 } tsqr_prec;
+ *         Yl Wh, binary32 accumulation) for n <= 64 (NATIVE Step 3 above).
+ * AUTO:   the library's choice for the data: TSQR_F32 data takes TF32X3 at
+ *         n >= 64 and NATIVE below; TSQR_F64 data takes NATIVE. */
+typedef enum tsqr_prec {
+  TSQR_PREC_NATIVE = 0,
+  TSQR_PREC_DF64 = 1,
+  TSQR_PREC_TF32X3 = 2,
+  TSQR_PREC_AUTO = 3
+} tsqr_prec;
 
 /* Which computation a workspace is sized for. */
 typedef enum tsqr_op {
@@ -275,6 +284,34 @@ tsqr_status tsqr_direct_host(const void* A, int64_t m, int64_t n, int32_t dtype,
  */
 tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* opts,
                               int32_t refine_steps, int32_t* launches);
+
+/*
+ * The plan a call of `op` would use for this shape and opts (host-only;
+ * launches nothing): the row-block partition of Step 1 (Sec. III-B: row
+ * blocks of block_rows rows, the last one possibly shorter) and the
+ * recursive Step-2 tree (Sec. III-C, Alg. 2: levels of tree_fanout stacked
+ * R factors per node until one node remains).
+ *   block_rows      rows per Step-1 row block
+ *   blocks          number of row blocks (= R factors in the first stack)
+ *   tiles_per_block register tiles per block (a taller block is factored
+ *                   tile by tile, a flat tree inside the CTA)
+ *   tree_levels     Step-2 tree levels (0: a single block, no tree)
+ *   tree_fanout     R factors merged per tree node
+ *   prec            the tsqr_prec the call computes in (TSQR_PREC_AUTO resolved)
+ *   step3_tensor    1 when Step 3 runs on the tensor cores
+ */
+typedef struct tsqr_plan_info {
+  int64_t block_rows;
+  int64_t blocks;
+  int32_t tiles_per_block;
+  int32_t tree_levels;
+  int32_t tree_fanout;
+  int32_t prec;
+  int32_t step3_tensor;
+  int32_t reserved;
+} tsqr_plan_info;
+tsqr_status tsqr_plan_query(int32_t op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* opts,
+                            tsqr_plan_info* info);
 
 /*
  * Synchronises `stream` and returns the device status word of the last call

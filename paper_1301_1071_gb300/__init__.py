@@ -19,13 +19,14 @@ device is unavailable.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 import threading
 
 import torch
 
 __all__ = ["direct", "direct_host", "direct_static", "svd", "r", "svd_values", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
-           "workspace_size", "launch_count", "library_path", "load", "STATUS"]
+           "workspace_size", "launch_count", "plan_info", "library_path", "load", "STATUS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libtsqr_gb300.so")
@@ -33,7 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 F64, F32 = 0, 1
-PREC = {"native": 0, "df64": 1, "tf32x3": 2}
+PREC = {"native": 0, "df64": 1, "tf32x3": 2, "auto": 3}
 OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD, OP_DIRECT_HOST, OP_R, OP_SVD_VALUES = range(8)
 NMAX = 100
 STATUS = {0: "TSQR_OK", 1: "TSQR_ERR_ARG", 2: "TSQR_ERR_SHAPE", 3: "TSQR_ERR_ALIGN",
@@ -51,6 +52,12 @@ class Opts(ctypes.Structure):
     _fields_ = [("block_rows", ctypes.c_int64), ("tree_fanout", ctypes.c_int32),
                 ("sync", ctypes.c_int32), ("stage_events", ctypes.POINTER(ctypes.c_void_p)),
                 ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("block_rows", ctypes.c_int64), ("blocks", ctypes.c_int64), ("tiles_per_block", ctypes.c_int32),
+                ("tree_levels", ctypes.c_int32), ("tree_fanout", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("step3_tensor", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -82,6 +89,7 @@ def load():
             "tsqr_backward": [P, P, P, P, I64, I64, I32, P, P, SZ, OP, P],
             "tsqr_read_status": [P, P],
             "tsqr_launch_count": [I32, I64, I64, I32, OP, I32, ctypes.POINTER(I32)],
+            "tsqr_plan_query": [I32, I64, I64, I32, OP, ctypes.POINTER(PlanInfo)],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -99,6 +107,19 @@ def _dtype_code(t: torch.Tensor) -> int:
     if t.dtype == torch.float32:
         return F32
     raise TypeError(f"unsupported dtype {t.dtype} (float64 or float32)")
+
+
+def _on_device(fn):
+    """Runs `fn` with the device of its first (tensor) argument current: the
+    library resolves the workspace, the static scratch and its launches
+    against the current device, and the stream passed is that device's."""
+    @functools.wraps(fn)
+    def wrapped(A, *args, **kw):
+        if isinstance(A, torch.Tensor) and A.is_cuda:
+            with torch.cuda.device(A.device):
+                return fn(A, *args, **kw)
+        return fn(A, *args, **kw)
+    return wrapped
 
 
 def _check_tall(A: torch.Tensor):
@@ -139,6 +160,22 @@ def launch_count(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fano
     return int(out.value)
 
 
+def plan_info(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fanout=0, prec="native") -> dict:
+    """The row-block partition and Step-2 tree a call would use (host-only
+    query): block_rows, blocks, tiles_per_block, tree_levels, tree_fanout,
+    the resolved precision and whether Step 3 runs on the tensor cores."""
+    lib = load()
+    code = F64 if dtype == torch.float64 else F32
+    info = PlanInfo()
+    o = _opts(block_rows, fanout, prec=prec)
+    _raise(lib.tsqr_plan_query(op, m, n, code, ctypes.byref(o), ctypes.byref(info)), "tsqr_plan_query")
+    names = {v: k for k, v in PREC.items()}
+    return {"block_rows": int(info.block_rows), "blocks": int(info.blocks),
+            "tiles_per_block": int(info.tiles_per_block), "tree_levels": int(info.tree_levels),
+            "tree_fanout": int(info.tree_fanout), "prec": names.get(int(info.prec), int(info.prec)),
+            "step3_tensor": bool(info.step3_tensor)}
+
+
 def _stream(device) -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
@@ -174,6 +211,7 @@ def _status(work: torch.Tensor, what: str, check: bool):
         _raise(st, what)
 
 
+@_on_device
 def direct(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
            out: tuple | None = None, check: bool = True, stage_events=None, prec: str = "native"):
     """Direct TSQR: returns (Q, R), Q m x n in A's dtype, R n x n float64,
@@ -211,6 +249,11 @@ def direct_host(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, out: tupl
         raise ValueError(f"unsupported shape {tuple(A.shape)}: need 1 <= n <= {NMAX} and m >= n")
     A = A.contiguous()
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        return _direct_host(A, m, n, dev, block_rows, fanout, out, dbuf, work, copy_stream, check, prec)
+
+
+def _direct_host(A, m, n, dev, block_rows, fanout, out, dbuf, work, copy_stream, check, prec):
     lib = load()
     if out is not None:
         Q, R = out
@@ -229,6 +272,7 @@ def direct_host(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, out: tupl
     return Q, R
 
 
+@_on_device
 def direct_static(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, prec: str = "native"):
     """Direct TSQR on the library's fixed device scratch (no workspace is
     allocated for the call; problems needing more than 16 MiB of workspace
@@ -245,6 +289,7 @@ def direct_static(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, prec: s
     return Q, R
 
 
+@_on_device
 def svd(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
         check: bool = True, prec: str = "native"):
     """SVD via direct TSQR: A = U diag(S) V^T (U m x n in A's dtype; S, V float64)."""
@@ -263,6 +308,7 @@ def svd(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tenso
     return U, S, V
 
 
+@_on_device
 def r(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor | None = None,
       check: bool = True, prec: str = "native"):
     """R factor only (Steps 1-2, no Q): returns R, n x n float64, diag(R) >= 0."""
@@ -279,6 +325,7 @@ def r(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor 
     return R
 
 
+@_on_device
 def svd_values(A: torch.Tensor, want_v: bool = True, block_rows: int = 0, fanout: int = 0,
                work: torch.Tensor | None = None, check: bool = True, prec: str = "native"):
     """Singular values (descending, float64) and, if ``want_v``, V (n x n
@@ -297,6 +344,7 @@ def svd_values(A: torch.Tensor, want_v: bool = True, block_rows: int = 0, fanout
     return S, V
 
 
+@_on_device
 def cholqr(A: torch.Tensor, refine: int = 0, work: torch.Tensor | None = None, check: bool = True):
     """Cholesky QR (+ `refine` refinement passes): returns (Q, R)."""
     m, n = _check_tall(A)
@@ -313,6 +361,7 @@ def cholqr(A: torch.Tensor, refine: int = 0, work: torch.Tensor | None = None, c
     return Q, R
 
 
+@_on_device
 def indirect_refine(A: torch.Tensor, refine: int = 1, block_rows: int = 0, fanout: int = 0,
                     work: torch.Tensor | None = None, check: bool = True):
     """Indirect TSQR + `refine` refinement passes: returns (Q, R)."""
@@ -330,6 +379,7 @@ def indirect_refine(A: torch.Tensor, refine: int = 1, block_rows: int = 0, fanou
     return Q, R
 
 
+@_on_device
 def backward(Q: torch.Tensor, R: torch.Tensor, dQ: torch.Tensor | None, dR: torch.Tensor | None,
              work: torch.Tensor | None = None, check: bool = True):
     """QR adjoint: dA = (dQ + Q copyltu(M)) R^{-T}, M = R dR^T - dQ^T Q."""

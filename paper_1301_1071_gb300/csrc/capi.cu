@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/tsqr.h"
@@ -108,7 +109,7 @@ int esz_of(int32_t dtype) { return dtype == TSQR_F64 ? 8 : (dtype == TSQR_F32 ? 
 tsqr_status check_opts(const tsqr_opts* o) {
   if (!o) return TSQR_OK;
   if (o->reserved != 0) return TSQR_ERR_ARG;
-  if (o->prec != TSQR_PREC_NATIVE && o->prec != TSQR_PREC_DF64 && o->prec != TSQR_PREC_TF32X3) return TSQR_ERR_ARG;
+  if (o->prec < TSQR_PREC_NATIVE || o->prec > TSQR_PREC_AUTO) return TSQR_ERR_ARG;
   if (o->block_rows < 0 || o->tree_fanout < 0 || o->tree_fanout == 1) return TSQR_ERR_ARG;
   return TSQR_OK;
 }
@@ -162,25 +163,61 @@ tsqr_status mark(const tsqr_opts* o, int i, cudaStream_t st) {
   } while (0)
 #define TSQR_CUDA(x) TSQR_TRY((x) == cudaSuccess ? TSQR_OK : TSQR_ERR_CUDA)
 
-// A second stream (the device's highest priority) and its fork / join events
-// for one call (created and released per call; the stream and events are
-// released by the driver once their work has completed).
+// A second stream (the device's highest priority) for the Step-2 tree: one
+// per device, created on first use and kept until the process exits, and a
+// fork / join event pair per call.  Once forked, the guard's destructor
+// always records the join on the side stream and makes the caller's stream
+// wait for it, on every exit path (an error after the fork included), so
+// that work queued on the side stream is never left unordered with `stream`.
 constexpr size_t kOverlapTBytes = static_cast<size_t>(TSQR_STATIC_WORK_BYTES);  // 16 MiB of T slots
 
-struct SideStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  bool make() {
+cudaStream_t device_side_stream() {
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static cudaStream_t streams[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev]) {
     int least = 0, greatest = 0;
-    return cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
-           cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) == cudaSuccess &&
-           cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
-           cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
+    cudaStream_t s = nullptr;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest) != cudaSuccess)
+      return nullptr;
+    streams[dev] = s;
+  }
+  return streams[dev];
+}
+
+struct SideStream {
+  cudaStream_t s = nullptr, caller = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool forked = false;
+  // Forks the side stream from `st`: false (nothing forked) on failure.
+  bool make(cudaStream_t st) {
+    caller = st;
+    s = device_side_stream();
+    if (!s || cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess)
+      return false;
+    if (cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(s, fork, 0) != cudaSuccess) return false;
+    forked = true;
+    return true;
+  }
+  // Orders the caller's stream after everything queued on the side stream.
+  cudaError_t rejoin() {
+    if (!forked) return cudaSuccess;
+    forked = false;
+    cudaError_t e = cudaEventRecord(join, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, join, 0);
+    // an ordering that cannot be expressed with the event: wait on the host
+    if (e != cudaSuccess) cudaStreamSynchronize(s);
+    return e;
   }
   ~SideStream() {
-    if (join) cudaEventDestroy(join);
+    rejoin();
+    if (join) cudaEventDestroy(join);  // released by the driver once its work has completed
     if (fork) cudaEventDestroy(fork);
-    if (s) cudaStreamDestroy(s);
   }
 };
 
@@ -248,20 +285,15 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   // side stream's set-up is worth (and no workspace of tsqr_direct_static, at
   // most TSQR_STATIC_WORK_BYTES, reaches the threshold).
   const bool overlap_t = static_cast<size_t>(l0.p) * l0.kt * n * n * sizeof(double) >= kOverlapTBytes;
-  SideStream side;
+  SideStream side;  // on every exit after a fork, `st` is made to wait for the side stream
   cudaStream_t tree_st = st;
   if (overlap_t) {
-    if (!side.make()) return TSQR_ERR_CUDA;
-    TSQR_CUDA(cudaEventRecord(side.fork, st));
-    TSQR_CUDA(cudaStreamWaitEvent(side.s, side.fork, 0));
+    if (!side.make(st)) return TSQR_ERR_CUDA;
     tree_st = side.s;
   }
   if (launch_build_t(T(0), l0.p * l0.kt, n, P.esz == 4, st) != cudaSuccess) return TSQR_ERR_CUDA;
   TSQR_TRY(run_tree(P, R, ldr, work, tree_st, extra));
-  if (overlap_t) {
-    TSQR_CUDA(cudaEventRecord(side.join, side.s));
-    TSQR_CUDA(cudaStreamWaitEvent(st, side.join, 0));
-  }
+  TSQR_CUDA(side.rejoin());
   // Step 3: Q_i = Q1_i Q2_i over the Y_i held in Q.
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
   const double* C0 = (L == 1) ? ctop : S(0);
@@ -466,6 +498,35 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
     case TSQR_OP_SVD_VALUES: *launches = L + 2; break;        // + Jacobi SVD
     default: return TSQR_ERR_ARG;
   }
+  return TSQR_OK;
+}
+
+tsqr_status tsqr_plan_query(int32_t op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* opts,
+                            tsqr_plan_info* info) {
+  if (!info) return TSQR_ERR_ARG;
+  const int esz = esz_of(dtype);
+  if (esz == 0) return TSQR_ERR_ARG;
+  tsqr_status s = check_opts(opts);
+  if (s != TSQR_OK) return s;
+  if (op < TSQR_OP_DIRECT || op > TSQR_OP_SVD_VALUES) return TSQR_ERR_ARG;
+  const int prec = (opts && op_takes_prec(op)) ? opts->prec : 0;
+  Plan P;
+  int chunks = 1;
+  int rc = op == TSQR_OP_DIRECT_HOST
+               ? make_host_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, &chunks,
+                                prec, device_sms())
+               : make_plan(m, n, esz, opts ? opts->block_rows : 0, opts ? opts->tree_fanout : 0, &P, prec,
+                           device_sms());
+  if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
+  std::memset(info, 0, sizeof(*info));
+  info->block_rows = P.levels[0].b;
+  info->blocks = P.levels[0].p;
+  info->tiles_per_block = P.levels[0].kt;
+  info->tree_levels = static_cast<int32_t>(P.levels.size()) - 1;
+  info->tree_fanout = P.levels.size() > 1 ? static_cast<int32_t>(P.levels[1].b / n) : 0;
+  info->prec = P.prec;
+  const bool q_pass = op == TSQR_OP_DIRECT || op == TSQR_OP_SVD || op == TSQR_OP_DIRECT_HOST;
+  info->step3_tensor = (q_pass && P.tc3) ? 1 : 0;
   return TSQR_OK;
 }
 

@@ -138,8 +138,16 @@ size_t op_bytes(const Plan& P, int op) {
   return (op == TSQR_OP_CHOLQR || op == TSQR_OP_BACKWARD) ? P.bytes_gram : P.bytes;
 }
 
+int resolve_prec(int prec, int esz, int64_t n) {
+  if (prec != TSQR_PREC_AUTO) return prec;
+  // binary32 data: the Step-3 product on the tensor cores from n = 64 up,
+  // where its share of the pass outgrows the split's overhead
+  return (esz == 4 && n >= kAutoTf32MinN) ? TSQR_PREC_TF32X3 : TSQR_PREC_NATIVE;
+}
+
 int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec, int sms) {
   if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  prec = resolve_prec(prec, esz, n);
   if (prec != TSQR_PREC_NATIVE && !(prec == TSQR_PREC_DF64 && esz == 8) && !(prec == TSQR_PREC_TF32X3 && esz == 4))
     return TSQR_ERR_ARG;
   Plan P;
@@ -189,6 +197,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   int64_t f = fanout > 0 ? fanout : fmax;
   if (f < 2 || f > fmax) return TSQR_ERR_SHAPE;
 
+  P.prec = prec;
   P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcMaxN;
   {
     const int kind_rm = esz == 4 ? kKindF32 : kKindF64;

@@ -69,6 +69,7 @@ struct Plan {
   int esz = 8;           // element size of the tall matrices
   KernelCfg cfg0;        // Step-1 kernel config (dtype of A)
   KernelCfg cfg64;       // tree kernel config (binary64)
+  int prec = 0;          // the resolved tsqr_prec (TSQR_PREC_AUTO taken)
   bool tc3 = false;      // Step 3 on the tensor cores (3xTF32, binary32 data, n <= 64)
   // k_rowmul with two inputs (the adjoint): a register tile close to the
   // b_rm2 rows per block whose two inputs fit in shared memory together
@@ -98,6 +99,12 @@ constexpr int kMaxTilesF32 = 128;   // binary32 data: its binary64 tree is costl
 constexpr int kMaxTilesDF64 = 8;
 constexpr int kDefaultSMs = 152;  // GB300
 constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM of a GB300)
+
+// TSQR_PREC_AUTO -> the concrete mode for this dtype and n (other modes
+// are returned unchanged): binary32 data at n >= kAutoTf32MinN takes the
+// 3xTF32 Step 3, everything else the data's own arithmetic.
+constexpr int kAutoTf32MinN = 64;
+int resolve_prec(int prec, int esz, int64_t n);
 
 // Workspace bytes of `op` (tsqr_op) under a built plan.
 size_t op_bytes(const Plan& P, int op);

@@ -154,9 +154,22 @@ def _sv_fn(lib):
 
 
 # Stand-in addresses: every case below is rejected by the host-side checks
-# before any launch, so nothing is ever read or written through them.
+# before any launch, so nothing is ever read or written through them.  Where
+# a GPU is visible these tests are skipped: a check that stopped rejecting a
+# case would otherwise launch kernels on those addresses.
 _P16 = 1 << 20        # 16-byte aligned
 _P8 = (1 << 20) + 8   # not 16-byte aligned
+
+
+def _gpu_visible():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        return False
+
+
+stand_in_addresses = pytest.mark.skipif(_gpu_visible(), reason="stand-in device addresses: host-only test")
 
 
 @pytest.mark.parametrize("args,want", [
@@ -172,6 +185,7 @@ _P8 = (1 << 20) + 8   # not 16-byte aligned
     (dict(work_bytes=64), 4),             # workspace too small
     (dict(prec=2), 1),                    # TF32X3 on FP64 data
 ])
+@stand_in_addresses
 def test_r_only_rejects_before_any_launch(lib, args, want):
     """tsqr_r's argument, shape, alignment and workspace errors (Sec. II-B
     R-only TSQR) are returned synchronously, before any launch."""
@@ -192,6 +206,7 @@ def test_r_only_rejects_before_any_launch(lib, args, want):
     (dict(n=0), 2),                       # n < 1
     (dict(work=None), 4),                 # no workspace
 ])
+@stand_in_addresses
 def test_svd_values_rejects_before_any_launch(lib, args, want):
     """tsqr_svd_values (Sec. III-B, singular values only) checks its
     arguments before any launch; V may be NULL (only S wanted)."""
@@ -203,3 +218,78 @@ def test_svd_values_rejects_before_any_launch(lib, args, want):
     st = _sv_fn(lib)(a["A"], a["m"], a["n"], a["lda"], 0, a["S"], a["V"], a["ldv"], a["work"], a["work_bytes"],
                      ctypes.byref(o), None)
     assert st == want
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("block_rows", ctypes.c_int64), ("blocks", ctypes.c_int64), ("tiles_per_block", ctypes.c_int32),
+                ("tree_levels", ctypes.c_int32), ("tree_fanout", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("step3_tensor", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def _plan(lib, op, m, n, dt, block_rows=0, fanout=0, prec=0):
+    f = lib.tsqr_plan_query
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Opts),
+                  ctypes.POINTER(PlanInfo)]
+    f.restype = ctypes.c_int
+    o = Opts(block_rows, fanout, 0, None, prec, 0)
+    info = PlanInfo()
+    st = f(op, m, n, dt, ctypes.byref(o), ctypes.byref(info))
+    return st, info
+
+
+def test_plan_query_partition_and_tree(lib):
+    """The row-block partition of Sec. III-B's example shape and the Alg. 2
+    tree: 100,000 x 10 in blocks of 1,000 gives 100 R factors; with 10 of
+    them per node the tree has two levels (100 -> 10 -> 1)."""
+    st, info = _plan(lib, 0, 100_000, 10, 0, block_rows=1000, fanout=10)
+    assert st == 0
+    assert (info.block_rows, info.blocks) == (1000, 100) and info.tiles_per_block >= 1
+    assert info.tree_fanout == 10 and info.tree_levels == 2
+    # one block: no tree
+    st, info = _plan(lib, 0, 900, 10, 0, block_rows=1000)
+    assert st == 0 and info.blocks == 1 and info.tree_levels == 0
+    # levels agree with the launch count (3 launches per level + sign fix)
+    for m, n, b in [(8_000_000, 25, 0), (50_000_000, 50, 1024), (50_000_000, 50, 8192)]:
+        st, info = _plan(lib, 0, m, n, 1 if n == 50 else 0, block_rows=b)
+        assert st == 0
+        assert _launches_dt(lib, 0, m, n, 1 if n == 50 else 0, b) == 3 * (info.tree_levels + 1) + 1
+        assert info.blocks == -(-m // info.block_rows)
+
+
+def _launches_dt(lib, op, m, n, dt, block_rows):
+    f = lib.tsqr_launch_count
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Opts),
+                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    f.restype = ctypes.c_int
+    o = Opts(block_rows, 0, 0, None, 0, 0)
+    out = ctypes.c_int32(0)
+    assert f(op, m, n, dt, ctypes.byref(o), 0, ctypes.byref(out)) == 0
+    return out.value
+
+
+@pytest.mark.parametrize("dt,n,want_prec,want_tc", [
+    (1, 50, 0, 0),   # binary32 below n = 64: native binary32 Step 3
+    (1, 64, 2, 1),   # binary32 at n = 64: 3xTF32 Step 3 on the tensor cores
+    (0, 64, 0, 0),   # binary64 data: native binary64
+    (0, 25, 0, 0),
+])
+def test_auto_precision_plan(lib, dt, n, want_prec, want_tc):
+    """TSQR_PREC_AUTO resolves to 3xTF32 for binary32 data at n >= 64 (the
+    threshold at which the split-precision products are asked for) and to
+    the data's own arithmetic otherwise."""
+    st, info = _plan(lib, 0, 1_000_000, n, dt, prec=3)
+    assert st == 0
+    assert info.prec == want_prec and info.step3_tensor == want_tc
+    # the explicit modes are reported as given
+    st, info = _plan(lib, 0, 1_000_000, n, dt, prec=0)
+    assert st == 0 and info.prec == 0 and info.step3_tensor == 0
+    # R only: no Step 3, so never on the tensor cores
+    st, info = _plan(lib, 6, 1_000_000, n, dt, prec=3)
+    assert st == 0 and info.step3_tensor == 0
+
+
+def test_plan_query_rejects(lib):
+    assert _plan(lib, 0, 10, 20, 0)[0] == 2          # m < n
+    assert _plan(lib, 9, 1000, 10, 0)[0] == 1        # unknown op
+    assert _plan(lib, 0, 1000, 10, 0, prec=4)[0] == 1  # unknown precision mode
+    assert _plan(lib, 0, 1000, 10, 0, prec=2)[0] == 1  # TF32X3 on binary64 data

@@ -86,3 +86,32 @@ def test_tf32x3_rejected_for_f64():
     import paper_1301_1071_gb300 as T
     with pytest.raises(T.TSQRError):
         T.direct(torch.randn(1000, 8, dtype=torch.float64, device="cuda"), prec="tf32x3")
+
+
+@pytest.mark.parametrize("n", [50, 64, 77])
+def test_auto_precision_parity(n):
+    """TSQR_PREC_AUTO: binary32 data at n >= 64 runs the 3xTF32 Step 3, below
+    it the binary32 FMA Step 3; the result is bit for bit that of the mode it
+    resolves to, and within the FP32 bars of the oracle."""
+    import paper_1301_1071_gb300 as T
+    A_np = ti.gaussian(30_000, n, 3100 + n).astype(np.float32)
+    A = torch.tensor(A_np, device="cuda")
+    Qa, Ra = T.direct(A, prec="auto")
+    Qx, Rx = T.direct(A, prec="tf32x3" if n >= 64 else "native")
+    torch.cuda.synchronize()
+    assert torch.equal(Qa, Qx) and torch.equal(Ra, Rx)
+    A64 = A_np.astype(np.float64)
+    Qo, Ro = oracle.householder_qr(A64)
+    tol = 10 * n * np.linalg.cond(A64) * EPS32
+    Q, R = Qa.double().cpu().numpy(), Ra.cpu().numpy()
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= tol
+    assert np.max(np.abs(Q - Qo)) <= tol
+    assert oracle.orth_error(Q)[0] <= 1e-5
+
+
+def test_auto_precision_f64_is_binary64():
+    import paper_1301_1071_gb300 as T
+    A = torch.tensor(ti.gaussian(20_000, 30, 3200), device="cuda")
+    Qa, Ra = T.direct(A, prec="auto")
+    Qn, Rn = T.direct(A)
+    assert torch.equal(Qa, Qn) and torch.equal(Ra, Rn)
