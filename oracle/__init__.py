@@ -87,6 +87,7 @@ def _load():
         "oracle_residual": [P, P, P, I64, I64, P, P],
         "oracle_gram_dot2": [P, P, I64, I64, P],
         "oracle_num_threads": [],
+        "oracle_set_num_threads": [ctypes.c_int],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -254,3 +255,9 @@ def gram_dot2(X, Y):
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    """Threads of the oracle's parallel loops (independent columns or rows;
+    the results are the same bits for every thread count)."""
+    _check(_load().oracle_set_num_threads(int(t)), "set_num_threads")

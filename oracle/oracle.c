@@ -49,6 +49,13 @@
 #define OR_ERR_SINGULAR 7
 #define OR_ERR_NOCONV 10
 
+/* Loops over independent columns (or rows) run on several threads when they
+ * hold more than this many entries.  Only loops whose iterations compute
+ * disjoint results are parallel, each iteration doing exactly the operations
+ * of the serial loop, so the bits do not depend on the thread count. */
+#define OR_PAR_MIN 65536
+#define OR_NMAX_BWD 1024
+
 /* ------------------------------------------------------------------------ */
 /* Householder QR (Sec. III-A, textbook method), column-major work copy.     */
 /* ------------------------------------------------------------------------ */
@@ -90,7 +97,10 @@ static void house_factor_colmajor(double* W, int64_t m, int64_t n, double* tau) 
     for (int64_t i = 1; i < len; ++i) x[i] = x[i] / denom;
     tau[j] = (beta - alpha) / beta;
     x[0] = beta;
-    /* apply H_j = I - tau v v^T to the trailing columns */
+    /* apply H_j = I - tau v v^T to the trailing columns.  Each column's
+       update is the same sequence of operations whichever thread runs it,
+       so the result does not depend on the thread count. */
+#pragma omp parallel for schedule(static) if (len * (n - j - 1) > OR_PAR_MIN)
     for (int64_t k = j + 1; k < n; ++k) {
       double* y = W + k * m + j;
       double w = y[0];
@@ -105,8 +115,9 @@ static void house_factor_colmajor(double* W, int64_t m, int64_t n, double* tau) 
 static double* to_colmajor(const double* A, int64_t m, int64_t n) {
   double* W = (double*)malloc(sizeof(double) * (size_t)(m * n));
   if (!W) return NULL;
-  for (int64_t i = 0; i < m; ++i)
-    for (int64_t j = 0; j < n; ++j) W[j * m + i] = A[i * n + j];
+#pragma omp parallel for schedule(static) if (m * n > OR_PAR_MIN)
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) W[j * m + i] = A[i * n + j];
   return W;
 }
 
@@ -139,6 +150,7 @@ int oracle_householder_qr(const double* A, int64_t m, int64_t n, double* Q, doub
       if (tau[j] == 0.0) continue;
       const double* v = W + j * m + j; /* v[0] is implicitly 1 */
       int64_t len = m - j;
+#pragma omp parallel for schedule(static) if (len * n > OR_PAR_MIN)
       for (int64_t k = 0; k < n; ++k) {
         double* y = M + k * m + j;
         double w = y[0];
@@ -148,6 +160,7 @@ int oracle_householder_qr(const double* A, int64_t m, int64_t n, double* Q, doub
         for (int64_t i = 1; i < len; ++i) y[i] -= w * v[i];
       }
     }
+#pragma omp parallel for schedule(static) if (m * n > OR_PAR_MIN)
     for (int64_t i = 0; i < m; ++i)
       for (int64_t j = 0; j < n; ++j) Q[i * n + j] = d[j] * M[j * m + i];
   }
@@ -316,12 +329,11 @@ int oracle_indirect_refine(const double* A, int64_t m, int64_t n, int refine_ste
  */
 int oracle_qr_backward(const double* Q, const double* R, const double* dQ, const double* dR,
                        int64_t m, int64_t n, double* dA) {
-  if (!Q || !R || !dA || n < 1 || m < n) return OR_ERR_ARG;
+  if (!Q || !R || !dA || n < 1 || n > OR_NMAX_BWD || m < n) return OR_ERR_ARG;
   for (int64_t j = 0; j < n; ++j)
     if (R[j * n + j] == 0.0) return OR_ERR_SINGULAR;
   double* M = (double*)calloc((size_t)(n * n), sizeof(double));
   double* C = (double*)malloc(sizeof(double) * (size_t)(n * n));
-  double* B = (double*)malloc(sizeof(double) * (size_t)n);
   if (dR)
     for (int64_t i = 0; i < n; ++i)
       for (int64_t j = 0; j < n; ++j) {
@@ -329,31 +341,41 @@ int oracle_qr_backward(const double* Q, const double* R, const double* dQ, const
         for (int64_t k = 0; k < n; ++k) s += R[i * n + k] * dR[j * n + k];
         M[i * n + j] = s;
       }
-  if (dQ)
+  if (dQ) {
+    /* (dQ^T Q)_ij = sum over rows r, in increasing r, for every (i, j): the
+       rows run in the outer loop and each thread owns whole rows i of the
+       sum, so every entry is the same sequence of additions for any thread
+       count. */
+    double* S = (double*)calloc((size_t)(n * n), sizeof(double));
+#pragma omp parallel for schedule(static) if (m * n > OR_PAR_MIN)
     for (int64_t i = 0; i < n; ++i)
-      for (int64_t j = 0; j < n; ++j) {
-        double s = 0.0;
-        for (int64_t r = 0; r < m; ++r) s += dQ[r * n + i] * Q[r * n + j];
-        M[i * n + j] -= s;
+      for (int64_t r = 0; r < m; ++r) {
+        const double di = dQ[r * n + i];
+        for (int64_t j = 0; j < n; ++j) S[i * n + j] += di * Q[r * n + j];
       }
+    for (int64_t k = 0; k < n * n; ++k) M[k] -= S[k];
+    free(S);
+  }
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = 0; j < n; ++j) C[i * n + j] = (i >= j) ? M[i * n + j] : M[j * n + i];
+#pragma omp parallel for schedule(static) if (m * n > OR_PAR_MIN)
   for (int64_t r = 0; r < m; ++r) {
+    double b[OR_NMAX_BWD];
     /* b = dQ_r + Q_r C */
     for (int64_t j = 0; j < n; ++j) {
       double s = dQ ? dQ[r * n + j] : 0.0;
       for (int64_t k = 0; k < n; ++k) s += Q[r * n + k] * C[k * n + j];
-      B[j] = s;
+      b[j] = s;
     }
     /* x R^T = b  <=>  R x^T = b^T: back substitution */
     double* x = dA + r * n;
     for (int64_t j = n - 1; j >= 0; --j) {
-      double s = B[j];
+      double s = b[j];
       for (int64_t k = j + 1; k < n; ++k) s -= R[j * n + k] * x[k];
       x[j] = s / R[j * n + j];
     }
   }
-  free(M); free(C); free(B);
+  free(M); free(C);
   return OR_OK;
 }
 
@@ -712,6 +734,17 @@ int oracle_residual(const double* A, const double* Q, const double* R, int64_t m
 int oracle_gram_dot2(const double* X, const double* Y, int64_t m, int64_t n, double* G) {
   if (!X || !Y || !G || n < 1 || m < 1) return OR_ERR_ARG;
   gram_dot2(X, Y, m, n, G);
+  return OR_OK;
+}
+
+/* Threads for the parallel loops (1 = the plain serial oracle). */
+int oracle_set_num_threads(int t) {
+#ifdef _OPENMP
+  if (t < 1) return OR_ERR_ARG;
+  omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
   return OR_OK;
 }
 

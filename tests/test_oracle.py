@@ -470,3 +470,24 @@ def test_generators_are_seeded_and_shaped():
     assert np.max(np.abs(V.T @ V - np.eye(7))) <= 1e-14
     s = ti.sigma_conditioned(5, 1e4)
     assert s[0] == 1.0 and abs(s[-1] - 1e-4) <= 1e-18
+
+
+def test_parallel_oracle_is_bit_identical_to_serial():
+    """The all-core oracle (the timed CPU baseline) runs only loops over
+    independent columns or rows in parallel, each iteration doing the serial
+    loop's operations: the results are the same bits at 1 and 4 threads."""
+    A = ti.conditioned(150_000, 12, 1e8, 91)
+    WQ = ti.gaussian(150_000, 12, 92)
+    WR = np.triu(ti.gaussian(12, 12, 93))
+    out = {}
+    prev = oracle.num_threads()
+    try:
+        for t in (1, 4):
+            oracle.set_num_threads(t)
+            Q, R = oracle.householder_qr(A)
+            dA = oracle.qr_backward(Q, R, WQ, WR)
+            out[t] = (Q, R, dA)
+    finally:
+        oracle.set_num_threads(prev)
+    for a, b in zip(out[1], out[4]):
+        assert np.array_equal(a, b)
