@@ -104,7 +104,8 @@ typedef enum tsqr_op {
   TSQR_OP_BACKWARD = 4,
   TSQR_OP_DIRECT_HOST = 5, /* tsqr_direct_host: its own row-block plan (copy chunks) */
   TSQR_OP_R = 6,           /* tsqr_r */
-  TSQR_OP_SVD_VALUES = 7   /* tsqr_svd_values */
+  TSQR_OP_SVD_VALUES = 7,  /* tsqr_svd_values */
+  TSQR_OP_ACCURACY = 8     /* tsqr_accuracy */
 } tsqr_op;
 
 typedef struct tsqr_opts {
@@ -277,6 +278,28 @@ tsqr_status tsqr_direct_static(const void* A, int64_t m, int64_t n, int64_t lda,
 tsqr_status tsqr_direct_host(const void* A, int64_t m, int64_t n, int32_t dtype, void* Q, double* R,
                              void* dbuf, void* work, size_t work_bytes, const tsqr_opts* opts,
                              void* stream, void* copy_stream);
+
+/*
+ * Accuracy of a computed factorisation: the metrics of Sec. I-B,
+ * ||Q^T Q - I||_2 and ||A - Q R||_2 / ||R||_2, and ||A - Q R||_F / ||A||_F,
+ * with every sum over the m rows accumulated in compensated (double-double)
+ * arithmetic -- TwoProduct and TwoSum, Ogita, Rump and Oishi 2005 -- so that
+ * the results hold at the 1e-15 level for any m (a plain binary64 sum over
+ * m rows errs by about sqrt(m) eps).  The n x n results are left on the
+ * device; the 2-norms are the largest |eigenvalue| of the symmetric n x n
+ * matrices, taken by the caller.
+ * In:  Q (m x n, dtype, ld n); A (m x n, dtype) and R (n x n binary64) both
+ *      given or both NULL (orthogonality only).
+ * Out: out, DEVICE, 3 n^2 + 2 binary64, row-major:
+ *      out[0 .. n^2)        E_hi, out[n^2 .. 2 n^2) E_lo: Q^T Q - I = E_hi + E_lo
+ *      out[2 n^2 .. 3 n^2)  F = (A - QR)^T (A - QR)  (zero without A)
+ *      out[3 n^2]           ||A - QR||_F^2, out[3 n^2 + 1] ||A||_F^2
+ * work: tsqr_workspace_size(TSQR_OP_ACCURACY, m, n, dtype, NULL) bytes.
+ * The combination of the per-CTA sums is in a fixed order: the results do
+ * not depend on scheduling.  Errors as tsqr_direct.
+ */
+tsqr_status tsqr_accuracy(const void* A, const void* Q, const double* R, int64_t m, int64_t n, int32_t dtype,
+                          double* out, void* work, size_t work_bytes, void* stream);
 
 /*
  * Number of kernel launches one call of `op` makes for this shape and opts

@@ -26,7 +26,7 @@ import threading
 import torch
 
 __all__ = ["direct", "direct_host", "direct_static", "svd", "r", "svd_values", "cholqr", "indirect_refine", "backward", "QRFunction", "TSQRError",
-           "workspace_size", "launch_count", "plan_info", "library_path", "load", "STATUS"]
+           "workspace_size", "launch_count", "plan_info", "accuracy", "library_path", "load", "STATUS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libtsqr_gb300.so")
@@ -35,7 +35,7 @@ _lib = None
 
 F64, F32 = 0, 1
 PREC = {"native": 0, "df64": 1, "tf32x3": 2, "auto": 3}
-OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD, OP_DIRECT_HOST, OP_R, OP_SVD_VALUES = range(8)
+OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD, OP_DIRECT_HOST, OP_R, OP_SVD_VALUES, OP_ACCURACY = range(9)
 NMAX = 100
 STATUS = {0: "TSQR_OK", 1: "TSQR_ERR_ARG", 2: "TSQR_ERR_SHAPE", 3: "TSQR_ERR_ALIGN",
           4: "TSQR_ERR_WORKSPACE", 5: "TSQR_ERR_CUDA", 6: "TSQR_ERR_NOT_SPD", 7: "TSQR_ERR_SINGULAR",
@@ -90,6 +90,7 @@ def load():
             "tsqr_read_status": [P, P],
             "tsqr_launch_count": [I32, I64, I64, I32, OP, I32, ctypes.POINTER(I32)],
             "tsqr_plan_query": [I32, I64, I64, I32, OP, ctypes.POINTER(PlanInfo)],
+            "tsqr_accuracy": [P, P, P, I64, I64, I32, P, P, SZ, P],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -397,6 +398,42 @@ def backward(Q: torch.Tensor, R: torch.Tensor, dQ: torch.Tensor | None, dR: torc
     _raise(st, "tsqr_backward")
     _status(work, "tsqr_backward", check)
     return dA
+
+
+@_on_device
+def accuracy(Q: torch.Tensor, R: torch.Tensor | None = None, A: torch.Tensor | None = None,
+             work: torch.Tensor | None = None) -> dict:
+    """Accuracy metrics of a factorisation (Sec. I-B) from tsqr_accuracy's
+    compensated device sums: ``orth_2`` = ||Q^T Q - I||_2, ``orth_F``, and with
+    A and R ``res_F`` = ||A - QR||_F/||A||_F and ``res_2`` = ||A - QR||_2/||R||_2.
+    The 2-norms of the symmetric n x n results are taken on the host."""
+    import numpy as np
+    m, n = Q.shape
+    if (A is None) != (R is None):
+        raise ValueError("give both A and R, or neither")
+    Q = Q.contiguous()
+    if A is not None:
+        A = A.to(Q.dtype).contiguous()
+        R = R.to(torch.float64).contiguous()
+    lib = load()
+    out = torch.empty(3 * n * n + 2, dtype=torch.float64, device=Q.device)
+    need = workspace_size(OP_ACCURACY, m, n, Q.dtype)
+    if work is None or work.numel() < need:
+        work = torch.empty(need, dtype=torch.uint8, device=Q.device)
+    st = lib.tsqr_accuracy(_ptr(A), _ptr(Q), _ptr(R), m, n, _dtype_code(Q), _ptr(out), _ptr(work), work.numel(),
+                           _stream(Q.device))
+    _raise(st, "tsqr_accuracy")
+    _status(work, "tsqr_accuracy", True)
+    o = out.cpu().numpy()
+    nn = n * n
+    E = o[:nn].reshape(n, n) + o[nn:2 * nn].reshape(n, n)
+    res = {"orth_2": float(np.max(np.abs(np.linalg.eigvalsh(E)))), "orth_F": float(np.linalg.norm(E))}
+    if A is not None:
+        F = o[2 * nn:3 * nn].reshape(n, n)
+        r2 = float(np.linalg.norm(R.cpu().numpy(), 2))
+        res["res_F"] = float(np.sqrt(o[3 * nn] / o[3 * nn + 1])) if o[3 * nn + 1] > 0 else float(np.sqrt(o[3 * nn]))
+        res["res_2"] = float(np.sqrt(max(np.max(np.linalg.eigvalsh(F)), 0.0)) / r2) if r2 > 0 else float("nan")
+    return res
 
 
 class QRFunction(torch.autograd.Function):

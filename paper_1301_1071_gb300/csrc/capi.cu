@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/tsqr.h"
+#include "check.h"
 #include "launch.h"
 #include "plan.h"
 #include "small.cuh"
@@ -477,6 +478,11 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
   if (esz == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
+  if (op == TSQR_OP_ACCURACY) {
+    if (n < 1 || n > TSQR_NMAX || m < 1) return TSQR_ERR_SHAPE;
+    *launches = 2;  // partial sums, ordered combination
+    return TSQR_OK;
+  }
   const int prec = (opts && op_takes_prec(op)) ? opts->prec : 0;
   Plan P;
   int chunks = 1;
@@ -547,6 +553,11 @@ tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
   if (esz == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
+  if (op == TSQR_OP_ACCURACY) {
+    if (n < 1 || n > TSQR_NMAX || m < 1) return TSQR_ERR_SHAPE;
+    *bytes = kHeaderBytes + accuracy_geom(m, static_cast<int>(n)).part_bytes;
+    return TSQR_OK;
+  }
   if (op < TSQR_OP_DIRECT || op > TSQR_OP_SVD_VALUES) return TSQR_ERR_ARG;
   const int prec = (opts && op_takes_prec(op)) ? opts->prec : 0;
   Plan P;
@@ -729,6 +740,20 @@ tsqr_status tsqr_indirect_refine(const void* A, int64_t m, int64_t n, int64_t ld
   }
   TSQR_TRY(copy_r(R, ldr, R1, n, st));
   return finish(work, opts, st);
+}
+
+tsqr_status tsqr_accuracy(const void* A, const void* Q, const double* R, int64_t m, int64_t n, int32_t dtype,
+                          double* out, void* work, size_t work_bytes, void* stream) {
+  const int esz = esz_of(dtype);
+  if (!Q || !out || esz == 0 || (A == nullptr) != (R == nullptr)) return TSQR_ERR_ARG;
+  if (n < 1 || n > TSQR_NMAX || m < 1) return TSQR_ERR_SHAPE;
+  const size_t need = kHeaderBytes + accuracy_geom(m, static_cast<int>(n)).part_bytes;
+  if (!work || !aligned16(work) || work_bytes < need) return TSQR_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TSQR_CUDA(cudaMemsetAsync(status_ptr(work), 0, sizeof(int32_t), st));
+  double* part = reinterpret_cast<double*>(at(work, kHeaderBytes));
+  TSQR_CUDA(launch_accuracy(esz, Q, A, R, m, static_cast<int>(n), part, out, st));
+  return finish(work, nullptr, st);
 }
 
 tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const double* dR, int64_t m, int64_t n,

@@ -133,7 +133,7 @@ def test_r_only_plans(lib):
         assert _launches(lib, 6, m, n, 0, block_rows=b) == levels + 1
         assert _launches(lib, 7, m, n, 0, block_rows=b) == levels + 2
         assert _ws(lib, 6, m, n, 0, block_rows=b) == _ws(lib, 0, m, n, 0, block_rows=b)
-    assert _ws(lib, 8, 1000, 10, 0)[0] == 1  # unknown op
+    assert _ws(lib, 9, 1000, 10, 0)[0] == 1  # unknown op
 
 
 def _r_fn(lib):
