@@ -182,25 +182,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(A_host: np.ndarray, target_s: float = 12.0, max_rows: int = 8_000_000):
-    """The oracle (plain single-threaded FP64 Householder QR with explicit Q)
-    on a bounded row sample of the same matrix."""
+def _oracle_rate(A_host: np.ndarray, threads: int, target_s: float, max_rows: int):
+    """rows/s of the oracle's thin QR (Q and R) on the first rows of A_host,
+    the sample grown until it takes about target_s seconds."""
     import oracle
-    n = A_host.shape[1]
-    rows = 100_000
-    sample = np.asarray(A_host[:rows], dtype=np.float64)
-    t0 = time.perf_counter()
-    oracle.householder_qr(sample)
-    t = time.perf_counter() - t0
-    if t < target_s / 3:
-        rows = int(min(max_rows, A_host.shape[0], rows * target_s / max(t, 1e-3)))
+    oracle.set_num_threads(threads)
+    rows = min(100_000, A_host.shape[0])
+    while True:
         sample = np.asarray(A_host[:rows], dtype=np.float64)
         t0 = time.perf_counter()
         oracle.householder_qr(sample)
         t = time.perf_counter() - t0
-    return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {rows:,} rows x {n} of the workload matrix, one thin QR (Q and R), "
-                      f"{t:.1f} s"}
+        if t >= target_s / 3 or rows >= min(max_rows, A_host.shape[0]):
+            return rows, t
+        rows = int(min(max_rows, A_host.shape[0], rows * target_s / max(t, 1e-3)))
+
+
+def cpu_baseline(A_host: np.ndarray, target_s: float = 10.0, max_rows: int = 8_000_000):
+    """The oracle (plain FP64 Householder QR with explicit Q) on a bounded row
+    sample of the same matrix: on all host cores (its loops over independent
+    columns in parallel, bit-identical to the serial oracle), and serial."""
+    n = A_host.shape[1]
+    cores = os.cpu_count() or 1
+    rows_p, t_p = _oracle_rate(A_host, cores, target_s, max_rows)
+    rows_s, t_s = _oracle_rate(A_host, 1, target_s, max_rows)
+    return {"value": rows_p / t_p, "unit": "rows/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {rows_p:,} rows x {n} of the workload matrix, one thin QR (Q and R) on "
+                      f"{cores} threads, {t_p:.1f} s",
+            "serial": {"value": rows_s / t_s, "unit": "rows/s", "cores": 1,
+                       "sample": f"first {rows_s:,} rows x {n}, one thread, {t_s:.1f} s"},
+            "host_cores": cores}
 
 
 def run_reference(args, w):
@@ -208,7 +219,9 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     import oracle
-    rows = min(w["m"], 1_000_000)
+    cores = os.cpu_count() or 1
+    oracle.set_num_threads(cores)
+    rows = min(w["m"], 2_000_000)
     sample = np.asarray(make_input(w, rows=rows), dtype=np.float64)
     for _ in range(args.warmup):
         oracle.householder_qr(sample)
@@ -222,8 +235,9 @@ def run_reference(args, w):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w["name"], "m": w["m"], "n": w["n"]},
-        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {rows:,} rows x {w['n']} of the workload matrix per step"},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {rows:,} rows x {w['n']} of the workload matrix per step, "
+                                   f"{cores} threads"},
         "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -325,20 +339,10 @@ def main():
                              "frac": 2 * m * n * elem / (dom_ms * 1e-3) / 1e9 / hbm_peak,
                              "peak_source": peak_src}}
 
-    # ---- accuracy at the stated kappa (library check with torch, FP64)
-    with torch.no_grad():
-        G = torch.zeros(n, n, dtype=torch.float64, device=dev)
-        res = 0.0
-        an = 0.0
-        for r0 in range(0, m, 1 << 21):
-            qb = Q[r0:r0 + (1 << 21)].double()
-            blk = A[r0:r0 + (1 << 21)].double()
-            G += qb.T @ qb
-            res += float(((blk - qb @ R) ** 2).sum())
-            an += float((blk ** 2).sum())
-        G -= torch.eye(n, dtype=G.dtype, device=dev)
-        orth2 = float(torch.linalg.eigvalsh(G.cpu()).abs().max())
-        resF = (res / an) ** 0.5
+    # ---- accuracy at the stated kappa: the library's compensated (Dot2)
+    #      device sums, accurate at the 1e-15 level for any m
+    acc = T.accuracy(Q, R, A)
+    orth2, resF = acc["orth_2"], acc["res_F"]
 
     # ---- end to end through the host-buffer entry point (tsqr_direct_host):
     #      pinned host A in, Q and R back to pinned host buffers, the copies
@@ -381,7 +385,8 @@ def main():
                    "l2": f"inputs ({gb:.1f} GB) larger than L2; no flush" if gb > 0.2
                    else "inputs smaller than L2", "parallelism": f"replicas x{ws}"},
         "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm_peak,
-        "orth_error_2": orth2, "residual_F": resF,
+        "orth_error_2": orth2, "residual_F": resF, "residual_2": acc["res_2"],
+        "accuracy_checker": "tsqr_accuracy (Dot2 device sums)",
         "step_ms": {"step1_local_qr": s1, "step2_tree": s2, "step3_form_q": s3},
         "step_fractions": {"step1": s1 / (s1 + s2 + s3), "step2": s2 / (s1 + s2 + s3),
                            "step3": s3 / (s1 + s2 + s3)},
@@ -392,9 +397,16 @@ def main():
         other = ("native" if args.prec != "native" else ("df64" if elem == 8 else "tf32x3"))
         line["extras"] = extras(T, torch, A, n, m, dev, other_prec=other)
     if not args.no_extras and rank == 0:
-        del A, Q, work, dbuf, work_h
+        del Q, work, dbuf, work_h
         torch.cuda.empty_cache()
-        line["configs"] = config_extras(T, torch, dev)
+        is_sweep = args.workload == "sweep" and not args.m
+        configs = {"small_100kx10": small_config(T, torch, dev)}
+        if is_sweep and args.prec == "native":
+            configs["stability_sweep_8Mx25"] = stability_sweep(T, torch, dev, A15=A)
+        del A
+        torch.cuda.empty_cache()
+        configs.update(config_extras(T, torch, dev))
+        line["configs"] = configs
     if not args.no_extras and rank == 0:
         line["cpu_baseline"] = cpu_baseline(A_host)
     if rank == 0:
@@ -404,11 +416,7 @@ def main():
     return 0
 
 
-def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
-    """fwd+bwd, the other precision mode, and the unstable comparators on the
-    same matrix."""
-    out = {}
-
+def _timer(torch, steps):
     def timed(fn):
         fn()
         torch.cuda.synchronize()
@@ -419,20 +427,22 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
         b.record()
         torch.cuda.synchronize()
         return a.elapsed_time(b) / steps
+    return timed
+
+
+def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
+    """fwd+bwd, the other precision mode, the unstable comparators, the R-only
+    and singular-value-only paths and cuSOLVER on the headline matrix."""
+    out = {}
+    timed = _timer(torch, steps)
 
     def orth(Qx):
-        G = torch.zeros(n, n, dtype=torch.float64, device=dev)
-        for r0 in range(0, Qx.shape[0], 1 << 22):
-            blk = Qx[r0:r0 + (1 << 22)].double()
-            G += blk.T @ blk
-        G -= torch.eye(n, dtype=G.dtype, device=dev)
-        return float(torch.linalg.eigvalsh(G.cpu()).abs().max())
+        return T.accuracy(Qx)["orth_2"]
 
     g = torch.Generator(device=dev)
     g.manual_seed(ti.SEED_GRAD)
     WQ = torch.randn(A.shape, dtype=A.dtype, device=dev, generator=g)
     WR = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
-    Q, R = T.direct(A)
 
     def fb():
         Qx, Rx = T.direct(A, check=False)
@@ -442,24 +452,15 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
     out["fwd_bwd"] = {"rows_s": m / (ms * 1e-3), "ms": ms,
                       "hbm_gbs_algorithmic": (ALG_PASSES["direct"] + ALG_PASSES["backward"]) * m * n *
                       A.element_size() / (ms * 1e-3) / 1e9}
+    del WQ
     Qp, Rp = T.direct(A, prec=other_prec)
     ms = timed(lambda: T.direct(A, check=False, prec=other_prec))
-    out[f"direct_{other_prec}"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Qp),
+    acc = T.accuracy(Qp, Rp, A)
+    out[f"direct_{other_prec}"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": acc["orth_2"],
+                                   "residual_F": acc["res_F"],
                                    "hbm_gbs_algorithmic": ALG_PASSES["direct"] * m * n * A.element_size() /
                                    (ms * 1e-3) / 1e9}
-    for name, fn in [("cholqr", lambda: T.cholqr(A, refine=0, check=False)),
-                     ("cholqr_ir", lambda: T.cholqr(A, refine=1, check=False)),
-                     ("indirect_ir", lambda: T.indirect_refine(A, refine=1, check=False))]:
-        try:
-            ms = timed(fn)
-            Qx, _ = fn()
-            torch.cuda.synchronize()
-            err = orth(Qx)
-        except Exception as e:  # a breakdown is a result, not a crash
-            ms, err = float("nan"), f"{type(e).__name__}: {e}"
-        out[name] = {"rows_s": m / (ms * 1e-3) if ms == ms else None, "ms": ms, "orth_error_2": err,
-                     "hbm_gbs_algorithmic": (ALG_PASSES[name] * m * n * A.element_size() / (ms * 1e-3) / 1e9
-                                             if ms == ms else None)}
+    del Qp
     # R only and singular values only (Steps 1-2, + the SVD of R): one read of A
     for name, fn in [("r_only", lambda: T.r(A, check=False)),
                      ("svd_values", lambda: T.svd_values(A, check=False))]:
@@ -481,40 +482,92 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
     return out
 
 
+KAPPAS = (1.0, 1e4, 1e8, 1e12, 1e15)
+
+
+def stability_sweep(T, torch, dev, A15=None, steps=3, m=8_000_000, n=25):
+    """The stability sweep of Sec. IV at 8,000,000 x 25 FP64: A = G diag(sigma)
+    V^T with sigma log-spaced 1 .. 1/kappa for each kappa, factored by direct
+    TSQR, Cholesky QR, Cholesky QR + one refinement step and indirect TSQR +
+    one refinement step; ||Q^T Q - I||_2 and ||A - QR||_F/||A||_F from the
+    compensated device checker, rows/s and algorithmic HBM GB/s of each."""
+    timed = _timer(torch, steps)
+    methods = [("direct", lambda A: T.direct(A, check=False)),
+               ("cholqr", lambda A: T.cholqr(A, refine=0, check=False)),
+               ("cholqr_ir", lambda A: T.cholqr(A, refine=1, check=False)),
+               ("indirect_ir", lambda A: T.indirect_refine(A, refine=1, check=False))]
+    table = {}
+    for kappa in KAPPAS:
+        if A15 is not None and kappa == 1e15:
+            A = A15
+        else:
+            A = torch.from_numpy(ti.conditioned(m, n, kappa, ti.SEED_SWEEP)).to(dev)
+        row = {}
+        for name, fn in methods:
+            try:
+                Qx, Rx = fn(A)
+                torch.cuda.synchronize()
+                ms = timed(lambda: fn(A))
+                st = 0
+                try:
+                    fn_check = {"direct": lambda: T.direct(A), "cholqr": lambda: T.cholqr(A),
+                                "cholqr_ir": lambda: T.cholqr(A, refine=1),
+                                "indirect_ir": lambda: T.indirect_refine(A, refine=1)}[name]
+                    Qx, Rx = fn_check()
+                except T.TSQRError as e:  # a breakdown is a result (Sec. IV)
+                    st = e.status
+                if st == 0:
+                    acc = T.accuracy(Qx, Rx, A)
+                    row[name] = {"orth_error_2": acc["orth_2"], "residual_F": acc["res_F"], "ms": ms,
+                                 "rows_s": m / (ms * 1e-3),
+                                 "hbm_gbs_algorithmic": ALG_PASSES[name] * m * n * 8 / (ms * 1e-3) / 1e9}
+                else:
+                    row[name] = {"status": T.STATUS.get(st, st), "ms": ms}
+                del Qx
+            except Exception as e:  # reported, not fatal
+                row[name] = {"error": f"{type(e).__name__}: {e}"}
+        table[f"{kappa:.0e}"] = row
+        if A is not A15:
+            del A
+        torch.cuda.empty_cache()
+    return {"workload": "8,000,000x25 FP64, A = G diag(sigma) V^T, sigma log-spaced 1..1/kappa",
+            "checker": "tsqr_accuracy (Dot2 device sums)", "by_kappa": table}
+
+
+def small_config(T, torch, dev, steps=50):
+    """The 100,000 x 10 FP64 workload with row blocks of 1,000 (100 blocks,
+    one stacked-R level of 1,000 x 10): latency-bound, reported but not
+    graded as a roofline fraction."""
+    import oracle
+    m, n = 100_000, 10
+    A_np = ti.gaussian(m, n, ti.SEED_SMALL)
+    A = torch.from_numpy(A_np).to(dev)
+    Q, R = T.direct(A, block_rows=1000)
+    timed = _timer(torch, steps)
+    ms = timed(lambda: T.direct(A, block_rows=1000, check=False))
+    acc = T.accuracy(Q, R, A)
+    Ro = oracle.householder_r(A_np)
+    plan = T.plan_info(T.OP_DIRECT, m, n, torch.float64, block_rows=1000)
+    return {"workload": "100,000x10 FP64 i.i.d. N(0,1), row blocks of 1,000", "ms": ms,
+            "rows_s": m / (ms * 1e-3), "hbm_gbs_algorithmic": ALG_PASSES["direct"] * m * n * 8 / (ms * 1e-3) / 1e9,
+            "orth_error_2": acc["orth_2"], "residual_F": acc["res_F"],
+            "r_error_vs_oracle": float(np.linalg.norm(R.cpu().numpy() - Ro) / np.linalg.norm(Ro)),
+            "plan": plan,
+            "launches": T.launch_count(T.OP_DIRECT, m, n, torch.float64, block_rows=1000)}
+
+
 def config_extras(T, torch, dev, steps=3):
     """The other benchmark configurations (synthetic, generated on the device
     from a seeded generator): the FP32 form on 50,000,000 x 50 against the
-    FP64 form on the same matrix upcast, the SVD variant on 20,000,000 x 100
-    FP32 storage, and forward + backward on 4,000,000 x 64 in FP32 and FP64."""
+    FP64 form on the same matrix upcast, with the row-block height swept; the
+    SVD variant on 20,000,000 x 100 FP32 storage; forward + backward on
+    4,000,000 x 64 in FP32 and FP64."""
     out = {}
+    timed = _timer(torch, steps)
 
-    def timed(fn):
-        fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(steps):
-            fn()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / steps
-
-    def orth(Qx):
-        n = Qx.shape[1]
-        G = torch.zeros(n, n, dtype=torch.float64, device=dev)
-        for r0 in range(0, Qx.shape[0], 1 << 22):
-            blk = Qx[r0:r0 + (1 << 22)].double()
-            G += blk.T @ blk
-        G -= torch.eye(n, dtype=torch.float64, device=dev)
-        return float(torch.linalg.eigvalsh(G.cpu()).abs().max())
-
-    def resid(Ax, Qx, Rx):
-        num = den = 0.0
-        for r0 in range(0, Ax.shape[0], 1 << 22):
-            a = Ax[r0:r0 + (1 << 22)].double()
-            num += float(((a - Qx[r0:r0 + (1 << 22)].double() @ Rx) ** 2).sum())
-            den += float((a ** 2).sum())
-        return (num / den) ** 0.5
+    def acc_of(Ax, Qx, Rx):
+        a = T.accuracy(Qx, Rx, Ax)
+        return {"orth_error_2": a["orth_2"], "residual_F": a["res_F"]}
 
     g = torch.Generator(device=dev)
     # mixed precision: N(0,1) scaled by column factors log-spaced over [1, 1e-4]
@@ -527,16 +580,29 @@ def config_extras(T, torch, dev, steps=3):
         for key, prec in (("fp32", "native"), ("fp32_tf32x3", "tf32x3")):
             Q, R = T.direct(A32, prec=prec)
             ms = timed(lambda: T.direct(A32, check=False, prec=prec))
-            entry[key] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Q),
-                          "residual_F": resid(A32, Q, R),
-                          "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9}
+            entry[key] = {"rows_s": m / (ms * 1e-3), "ms": ms, **acc_of(A32, Q, R),
+                          "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9,
+                          "plan": T.plan_info(T.OP_DIRECT, m, n, torch.float32, prec=prec)}
             del Q
+        # row blocks of 1,024 .. 8,192 rows (and the planner's choice above):
+        # time and tree depth of each
+        sweep = {}
+        for b in (1024, 2048, 4096, 8192):
+            try:
+                plan = T.plan_info(T.OP_DIRECT, m, n, torch.float32, block_rows=b, prec="tf32x3")
+                ms = timed(lambda: T.direct(A32, block_rows=b, check=False, prec="tf32x3"))
+                msn = timed(lambda: T.direct(A32, block_rows=b, check=False))
+                sweep[str(b)] = {"ms_tf32x3": ms, "ms_fp32": msn, "rows_s_tf32x3": m / (ms * 1e-3),
+                                 "tree_levels": plan["tree_levels"], "tree_fanout": plan["tree_fanout"],
+                                 "blocks": plan["blocks"], "tiles_per_block": plan["tiles_per_block"]}
+            except Exception as e:
+                sweep[str(b)] = {"error": f"{type(e).__name__}: {e}"}
+        entry["block_rows_sweep"] = sweep
         A64 = A32.double()
         del A32
         Q, R = T.direct(A64)
         ms = timed(lambda: T.direct(A64, check=False))
-        entry["fp64_upcast"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": orth(Q),
-                                "residual_F": resid(A64, Q, R),
+        entry["fp64_upcast"] = {"rows_s": m / (ms * 1e-3), "ms": ms, **acc_of(A64, Q, R),
                                 "hbm_gbs_algorithmic": 4 * m * n * 8 / (ms * 1e-3) / 1e9}
         del Q, A64
         out["mixed_50Mx50"] = entry
@@ -557,9 +623,12 @@ def config_extras(T, torch, dev, steps=3):
         U, S, Vo = T.svd(A)
         ms = timed(lambda: T.svd(A, check=False))
         out["svd_20Mx100"] = {"workload": "20,000,000x100 FP32 storage, G diag(j^-2) V^T",
-                              "rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2_U": orth(U),
+                              "rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2_U": T.accuracy(U)["orth_2"],
                               "max_rel_sigma_dev": float((S / sig - 1).abs().max()),
                               "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9}
+        for prec in ("tf32x3",):
+            msp = timed(lambda: T.svd(A, check=False, prec=prec))
+            out["svd_20Mx100"][f"ms_{prec}"] = msp
         del U, A
     except Exception as e:
         out["svd_20Mx100"] = {"error": f"{type(e).__name__}: {e}"}
@@ -581,8 +650,10 @@ def config_extras(T, torch, dev, steps=3):
             ms = timed(fb)
             msf = timed(lambda: T.direct(A, block_rows=4096, check=False))
             Q, R = T.direct(A, block_rows=4096)
+            esz = 8 if dt == torch.float64 else 4
             entry[name] = {"fwd_bwd_rows_s": m / (ms * 1e-3), "fwd_bwd_ms": ms, "fwd_rows_s": m / (msf * 1e-3),
-                           "orth_error_2": orth(Q)}
+                           "fwd_ms": msf, "orth_error_2": T.accuracy(Q)["orth_2"],
+                           "fwd_bwd_hbm_gbs_algorithmic": 9 * m * n * esz / (ms * 1e-3) / 1e9}
             if dt == torch.float32:
                 mst = timed(lambda: T.direct(A, block_rows=4096, check=False, prec="tf32x3"))
                 entry[name]["fwd_rows_s_tf32x3"] = m / (mst * 1e-3)
