@@ -253,8 +253,8 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip comparators / fwd+bwd / cpu baseline")
     ap.add_argument("--m", type=int, default=0, help="override the row count (profiling a smaller case)")
-    ap.add_argument("--prec", default="native", choices=["native", "df64", "tf32x3"],
-                    help="arithmetic of Steps 1 and 3 (df64: FP64 data; tf32x3: FP32 data)")
+    ap.add_argument("--prec", default="native", choices=["native", "df64", "tf32x3", "ozaki", "auto"],
+                    help="arithmetic of Steps 1 and 3 (df64, ozaki: FP64 data; tf32x3: FP32 data)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.m:
@@ -378,6 +378,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": ("df64 (binary64 data, pairs of binary32 in Steps 1 and 3, binary64 tree)" if args.prec == "df64"
+                  else "f64 (Step 3 product as an Ozaki split on the tensor cores, exact accumulation)"
+                  if args.prec == "ozaki"
                   else "f32 (Step 3 product as 3xTF32 on the tensor cores)" if args.prec == "tf32x3"
                   else ("f64" if elem == 8 else "f32")),
         "data": "synthetic",
@@ -394,8 +396,8 @@ def main():
     }
 
     if not args.no_extras and rank == 0:
-        other = ("native" if args.prec != "native" else ("df64" if elem == 8 else "tf32x3"))
-        line["extras"] = extras(T, torch, A, n, m, dev, other_prec=other)
+        others = [p for p in (("native", "df64", "ozaki") if elem == 8 else ("native", "tf32x3")) if p != args.prec]
+        line["extras"] = extras(T, torch, A, n, m, dev, other_precs=others)
     if not args.no_extras and rank == 0:
         del Q, work, dbuf, work_h
         torch.cuda.empty_cache()
@@ -430,7 +432,7 @@ def _timer(torch, steps):
     return timed
 
 
-def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
+def extras(T, torch, A, n, m, dev, steps=3, other_precs=("df64",)):
     """fwd+bwd, the other precision mode, the unstable comparators, the R-only
     and singular-value-only paths and cuSOLVER on the headline matrix."""
     out = {}
@@ -453,14 +455,23 @@ def extras(T, torch, A, n, m, dev, steps=3, other_prec="df64"):
                       "hbm_gbs_algorithmic": (ALG_PASSES["direct"] + ALG_PASSES["backward"]) * m * n *
                       A.element_size() / (ms * 1e-3) / 1e9}
     del WQ
-    Qp, Rp = T.direct(A, prec=other_prec)
-    ms = timed(lambda: T.direct(A, check=False, prec=other_prec))
-    acc = T.accuracy(Qp, Rp, A)
-    out[f"direct_{other_prec}"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": acc["orth_2"],
-                                   "residual_F": acc["res_F"],
-                                   "hbm_gbs_algorithmic": ALG_PASSES["direct"] * m * n * A.element_size() /
-                                   (ms * 1e-3) / 1e9}
-    del Qp
+    for other_prec in other_precs:
+        Qp, Rp = T.direct(A, prec=other_prec)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for e in evs:
+            e.record()
+        T.direct(A, check=False, prec=other_prec, stage_events=evs)
+        torch.cuda.synchronize()
+        ms = timed(lambda: T.direct(A, check=False, prec=other_prec))
+        acc = T.accuracy(Qp, Rp, A)
+        out[f"direct_{other_prec}"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2": acc["orth_2"],
+                                       "residual_F": acc["res_F"],
+                                       "step_ms": {"step1": evs[0].elapsed_time(evs[1]),
+                                                   "step2": evs[1].elapsed_time(evs[2]),
+                                                   "step3": evs[2].elapsed_time(evs[3])},
+                                       "hbm_gbs_algorithmic": ALG_PASSES["direct"] * m * n * A.element_size() /
+                                       (ms * 1e-3) / 1e9}
+        del Qp
     # R only and singular values only (Steps 1-2, + the SVD of R): one read of A
     for name, fn in [("r_only", lambda: T.r(A, check=False)),
                      ("svd_values", lambda: T.svd_values(A, check=False))]:

@@ -87,12 +87,20 @@ typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
  *         (Y = Yh + Yl, W = Wh + Wl rounded to TF32; Y W ~ Yh Wh + Yh Wl +
  *         Yl Wh, binary32 accumulation) for n <= 64 (NATIVE Step 3 above).
  * AUTO:   the library's choice for the data: TSQR_F32 data takes TF32X3 at
- *         n >= 64 and NATIVE below; TSQR_F64 data takes NATIVE. */
+ *         n >= 64 and NATIVE below; TSQR_F64 data takes NATIVE.
+ * OZAKI:  TSQR_F64 data only.  Step 1 as NATIVE (binary64); for n <= 32 the
+ *         Step-3 product Y_i W_i runs on the tensor cores as an error-free
+ *         split product (Ozaki, Ogita, Oishi, Rump 2012): each row of Y and
+ *         column of W is cut into 7 digits of 8 bits (56 bits) against its
+ *         largest exponent, the digit products are accumulated exactly in
+ *         binary32 (binary16 operands), recombined in 64-bit integers and
+ *         rounded once to binary64.  Above n = 32, NATIVE Step 3. */
 typedef enum tsqr_prec {
   TSQR_PREC_NATIVE = 0,
   TSQR_PREC_DF64 = 1,
   TSQR_PREC_TF32X3 = 2,
-  TSQR_PREC_AUTO = 3
+  TSQR_PREC_AUTO = 3,
+  TSQR_PREC_OZAKI = 4
 } tsqr_prec;
 
 /* Which computation a workspace is sized for. */

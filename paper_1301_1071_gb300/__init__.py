@@ -34,7 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 F64, F32 = 0, 1
-PREC = {"native": 0, "df64": 1, "tf32x3": 2, "auto": 3}
+PREC = {"native": 0, "df64": 1, "tf32x3": 2, "auto": 3, "ozaki": 4}
 OP_DIRECT, OP_SVD, OP_CHOLQR, OP_INDIRECT, OP_BACKWARD, OP_DIRECT_HOST, OP_R, OP_SVD_VALUES, OP_ACCURACY = range(9)
 NMAX = 100
 STATUS = {0: "TSQR_OK", 1: "TSQR_ERR_ARG", 2: "TSQR_ERR_SHAPE", 3: "TSQR_ERR_ALIGN",

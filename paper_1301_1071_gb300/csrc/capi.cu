@@ -110,7 +110,7 @@ int esz_of(int32_t dtype) { return dtype == TSQR_F64 ? 8 : (dtype == TSQR_F32 ? 
 tsqr_status check_opts(const tsqr_opts* o) {
   if (!o) return TSQR_OK;
   if (o->reserved != 0) return TSQR_ERR_ARG;
-  if (o->prec < TSQR_PREC_NATIVE || o->prec > TSQR_PREC_AUTO) return TSQR_ERR_ARG;
+  if (o->prec < TSQR_PREC_NATIVE || o->prec > TSQR_PREC_OZAKI) return TSQR_ERR_ARG;
   if (o->block_rows < 0 || o->tree_fanout < 0 || o->tree_fanout == 1) return TSQR_ERR_ARG;
   return TSQR_OK;
 }
@@ -300,9 +300,11 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   const double* C0 = (L == 1) ? ctop : S(0);
   const int64_t cb0 = (L == 1) ? 1 : l0.p;
   const cudaError_t e3 =
-      P.tc3 ? launch_form_q_tc(static_cast<float*>(Q), P.m, n, l0.b, P.cfg0.B, l0.bt, l0.kt, l0.p, T(0), C0, cb0,
-                               status, st)
-            : launch_form_q(P.cfg0, Q, P.m, n, l0.b, l0.bt, l0.kt, l0.p, T(0), C0, cb0, Q, status, st);
+      P.oz3   ? launch_form_q_oz(static_cast<double*>(Q), P.m, n, l0.b, P.cfg0.B, l0.bt, l0.kt, l0.p, T(0), C0, cb0,
+                                 status, st)
+      : P.tc3 ? launch_form_q_tc(static_cast<float*>(Q), P.m, n, l0.b, P.cfg0.B, l0.bt, l0.kt, l0.p, T(0), C0, cb0,
+                                 status, st)
+              : launch_form_q(P.cfg0, Q, P.m, n, l0.b, l0.bt, l0.kt, l0.p, T(0), C0, cb0, Q, status, st);
   if (e3 != cudaSuccess) return TSQR_ERR_CUDA;
   return mark(o, 3, st);
 }
@@ -424,10 +426,12 @@ tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, 
     const double* Cc = (L == 1) ? C0 : C0 + b0 * nn;
     const int64_t cb = (L == 1) ? 1 : pcnt;
     char* Y = dbuf + r0 * row_bytes;
-    TSQR_CUDA(P.tc3 ? launch_form_q_tc(reinterpret_cast<float*>(Y), rows, n, l0.b, P.cfg0.B, l0.bt, l0.kt, pcnt,
-                                       T0 + b0 * l0.kt * nn, Cc, cb, status, st)
-                    : launch_form_q(P.cfg0, Y, rows, n, l0.b, l0.bt, l0.kt, pcnt, T0 + b0 * l0.kt * nn, Cc, cb, Y,
-                                    status, st));
+    TSQR_CUDA(P.oz3   ? launch_form_q_oz(reinterpret_cast<double*>(Y), rows, n, l0.b, P.cfg0.B, l0.bt, l0.kt, pcnt,
+                                         T0 + b0 * l0.kt * nn, Cc, cb, status, st)
+              : P.tc3 ? launch_form_q_tc(reinterpret_cast<float*>(Y), rows, n, l0.b, P.cfg0.B, l0.bt, l0.kt, pcnt,
+                                         T0 + b0 * l0.kt * nn, Cc, cb, status, st)
+                      : launch_form_q(P.cfg0, Y, rows, n, l0.b, l0.bt, l0.kt, pcnt, T0 + b0 * l0.kt * nn, Cc, cb, Y,
+                                      status, st));
     TSQR_CUDA(cudaEventRecord(ev_q[c], st));
     TSQR_CUDA(cudaStreamWaitEvent(cst, ev_q[c], 0));
     TSQR_CUDA(cudaMemcpyAsync(Qh + r0 * row_bytes, Y, rows * row_bytes, cudaMemcpyDeviceToHost, cst));
@@ -532,7 +536,7 @@ tsqr_status tsqr_plan_query(int32_t op, int64_t m, int64_t n, int32_t dtype, con
   info->tree_fanout = P.levels.size() > 1 ? static_cast<int32_t>(P.levels[1].b / n) : 0;
   info->prec = P.prec;
   const bool q_pass = op == TSQR_OP_DIRECT || op == TSQR_OP_SVD || op == TSQR_OP_DIRECT_HOST;
-  info->step3_tensor = (q_pass && P.tc3) ? 1 : 0;
+  info->step3_tensor = (q_pass && (P.tc3 || P.oz3)) ? 1 : 0;
   return TSQR_OK;
 }
 

@@ -42,6 +42,12 @@ cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, c
 cudaError_t launch_form_q_tc(float* Y, int64_t m, int n, int64_t b, int B, int64_t bt, int kt, int64_t p,
                              const double* T, const double* C, int64_t cblocks, int32_t* status, cudaStream_t st);
 
+// Step 3 for binary64 data with the product Y W on the tensor cores by
+// Ozaki splitting (binary16 digits, exact binary32 accumulation), n <= 32;
+// the block and tile geometry of Step 1.
+cudaError_t launch_form_q_oz(double* Y, int64_t m, int n, int64_t b, int B, int64_t bt, int kt, int64_t p,
+                             const double* T, const double* C, int64_t cblocks, int32_t* status, cudaStream_t st);
+
 // out_r = X_r M1 + Y_r M2 over p blocks of b rows (X or Y may be NULL).
 cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, const void* Y,
                           const double* M2, int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,

@@ -7,6 +7,7 @@
 #include "../../include/tsqr.h"
 #include "launch.h"
 #include "layout.cuh"
+#include "oz_kernels.cuh"
 #include "tc_kernels.cuh"
 
 namespace tsqr {
@@ -148,7 +149,8 @@ int resolve_prec(int prec, int esz, int64_t n) {
 int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec, int sms) {
   if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
   prec = resolve_prec(prec, esz, n);
-  if (prec != TSQR_PREC_NATIVE && !(prec == TSQR_PREC_DF64 && esz == 8) && !(prec == TSQR_PREC_TF32X3 && esz == 4))
+  if (prec != TSQR_PREC_NATIVE && !(prec == TSQR_PREC_DF64 && esz == 8) && !(prec == TSQR_PREC_TF32X3 && esz == 4) &&
+      !(prec == TSQR_PREC_OZAKI && esz == 8))
     return TSQR_ERR_ARG;
   Plan P;
   P.m = m;
@@ -199,6 +201,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
 
   P.prec = prec;
   P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcMaxN;
+  P.oz3 = prec == TSQR_PREC_OZAKI && n <= kOzMaxN;
   {
     const int kind_rm = esz == 4 ? kKindF32 : kKindF64;
     // the coefficient blocks' padded width: the wider of the two tile widths'

@@ -71,6 +71,7 @@ struct Plan {
   KernelCfg cfg64;       // tree kernel config (binary64)
   int prec = 0;          // the resolved tsqr_prec (TSQR_PREC_AUTO taken)
   bool tc3 = false;      // Step 3 on the tensor cores (3xTF32, binary32 data, n <= 64)
+  bool oz3 = false;      // Step 3 on the tensor cores (Ozaki split, binary64 data, n <= 32)
   // k_rowmul with two inputs (the adjoint): a register tile close to the
   // b_rm2 rows per block whose two inputs fit in shared memory together
   KernelCfg cfg_rm2;

@@ -291,5 +291,18 @@ def test_auto_precision_plan(lib, dt, n, want_prec, want_tc):
 def test_plan_query_rejects(lib):
     assert _plan(lib, 0, 10, 20, 0)[0] == 2          # m < n
     assert _plan(lib, 9, 1000, 10, 0)[0] == 1        # unknown op
-    assert _plan(lib, 0, 1000, 10, 0, prec=4)[0] == 1  # unknown precision mode
+    assert _plan(lib, 0, 1000, 10, 0, prec=5)[0] == 1  # unknown precision mode
+    assert _plan(lib, 0, 1000, 10, 1, prec=4)[0] == 1  # OZAKI on binary32 data
     assert _plan(lib, 0, 1000, 10, 0, prec=2)[0] == 1  # TF32X3 on binary64 data
+
+
+@pytest.mark.parametrize("n,want_tc", [(10, 1), (25, 1), (32, 1), (33, 0), (64, 0)])
+def test_ozaki_plan(lib, n, want_tc):
+    """TSQR_PREC_OZAKI: binary64 data; Step 3 on the tensor cores for n <= 32
+    (the exact-accumulation bound of the split), the binary64 FMA Step 3
+    above; the row blocks and tree are those of the native plan."""
+    st, info = _plan(lib, 0, 1_000_000, n, 0, prec=4)
+    assert st == 0 and info.prec == 4 and info.step3_tensor == want_tc
+    st, nat = _plan(lib, 0, 1_000_000, n, 0, prec=0)
+    assert st == 0
+    assert (info.block_rows, info.blocks, info.tree_levels) == (nat.block_rows, nat.blocks, nat.tree_levels)
