@@ -31,6 +31,8 @@ cudaError_t launch_local_r_f64(const KernelCfg&, const void*, int64_t, int, int6
                                int32_t*, cudaStream_t);
 cudaError_t launch_local_r_f32(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t, double*,
                                int32_t*, cudaStream_t);
+cudaError_t launch_local_qr_nogram_f64(const KernelCfg&, const void*, int64_t, int, int64_t, int64_t, int, int64_t,
+                                       void*, double*, double*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f64(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
                               int, int64_t, int64_t, void*, int32_t*, cudaStream_t);
 cudaError_t launch_rowmul_f32(const KernelCfg&, const void*, const double*, const void*, const double*, int64_t,
@@ -71,6 +73,19 @@ cudaError_t launch_local_qr(const KernelCfg& k, const void* A, int64_t m, int n,
     case kKindDF64: return launch_local_qr_df64(k, A, m, n, b, bt, kt, p, Y, Rst, Tst, status, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Step 1 of direct TSQR: Y_i, R_i and the T slots' tau and Gram entries (the
+// Ozaki form: the Gram entries on the tensor cores after a Step 1 without
+// them).
+cudaError_t launch_step1(const Plan& P, const void* A, int64_t m, int64_t b, int64_t p, void* Y, double* Rst,
+                         double* Tst, int32_t* status, cudaStream_t st) {
+  const Level& l0 = P.levels[0];
+  const int n = static_cast<int>(P.n);
+  if (!P.gram_oz) return launch_local_qr(P.cfg0, A, m, n, b, l0.bt, l0.kt, p, Y, Rst, Tst, status, st);
+  cudaError_t e = launch_local_qr_nogram_f64(P.cfg0, A, m, n, b, l0.bt, l0.kt, p, Y, Rst, Tst, status, st);
+  if (e != cudaSuccess) return e;
+  return launch_gram_oz(static_cast<const double*>(Y), m, n, b, P.cfg0.B, l0.bt, l0.kt, p, Tst, status, st);
 }
 
 cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, int64_t b, int64_t bt, int kt,
@@ -274,8 +289,7 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   // Step 1: local QR of every row block; Y_0 is written into Q's storage.
   const Level& l0 = P.levels[0];
   if (mark(o, 0, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  if (launch_local_qr(P.cfg0, A, P.m, n, l0.b, l0.bt, l0.kt, l0.p, Q, S(0), T(0), status, st) != cudaSuccess)
-    return TSQR_ERR_CUDA;
+  if (launch_step1(P, A, P.m, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess) return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
   // The row blocks' T factors are read only by Step 3 and the tree reads only
   // the stack of R factors, so for a large T build the tree runs on a side
@@ -410,8 +424,8 @@ tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, 
                               cst));
     TSQR_CUDA(cudaEventRecord(ev_in[c], cst));
     TSQR_CUDA(cudaStreamWaitEvent(st, ev_in[c], 0));
-    TSQR_CUDA(launch_local_qr(P.cfg0, dbuf + r0 * row_bytes, rows, n, l0.b, l0.bt, l0.kt, pcnt,
-                              dbuf + r0 * row_bytes, S0 + b0 * nn, T0 + b0 * l0.kt * nn, status, st));
+    TSQR_CUDA(launch_step1(P, dbuf + r0 * row_bytes, rows, l0.b, pcnt, dbuf + r0 * row_bytes, S0 + b0 * nn,
+                           T0 + b0 * l0.kt * nn, status, st));
     TSQR_CUDA(launch_build_t(T0 + b0 * l0.kt * nn, pcnt * l0.kt, n, P.esz == 4, st));
   }
   // Step 2, then R back to the host
@@ -497,10 +511,11 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
                            device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   const int L = static_cast<int>(P.levels.size());
+  const int g = P.gram_oz ? 1 : 0;  // the tensor-core Gram after Step 1
   switch (op) {
-    case TSQR_OP_DIRECT_HOST: *launches = 3 * chunks + 3 * (L - 1) + 1; break;  // chunks x (Step 1, T, Step 3)
-    case TSQR_OP_DIRECT: *launches = 3 * L + 1; break;        // L up (+ T build), sign fix, L down
-    case TSQR_OP_SVD: *launches = 3 * L + 2; break;           // + Jacobi SVD
+    case TSQR_OP_DIRECT_HOST: *launches = (3 + g) * chunks + 3 * (L - 1) + 1; break;  // chunks x (Step 1, T, Step 3)
+    case TSQR_OP_DIRECT: *launches = 3 * L + 1 + g; break;    // L up (+ T build), sign fix, L down
+    case TSQR_OP_SVD: *launches = 3 * L + 2 + g; break;       // + Jacobi SVD
     case TSQR_OP_CHOLQR: *launches = 4 * (1 + refine_steps) + refine_steps; break;  // gram, reduce, chol, rowmul (+ combine)
     case TSQR_OP_INDIRECT: *launches = (L + 3) * (1 + refine_steps) + refine_steps; break;
     case TSQR_OP_BACKWARD: *launches = 4; break;              // gram, reduce, prep, rowmul

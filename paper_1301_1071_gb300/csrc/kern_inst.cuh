@@ -106,6 +106,38 @@ cudaError_t TSQR_LOCAL_R_NAME(const KernelCfg& k, const void* A, int64_t m, int 
 }
 #endif  // TSQR_LOCAL_R_NAME
 
+#ifdef TSQR_LOCAL_QR_NOGRAM_NAME
+// Y, R and tau without the Gram dot products (the same kernel instantiation
+// as the R-only form, given Y and the T slots): the one-row-group tiles.
+template <int R, int MAXT, int NPC>
+static cudaError_t local_qr_ng_R(const KernelCfg& k, const TSQR_S* A, int64_t m, int n, int64_t b, int64_t bt, int kt,
+                                 int64_t p, TSQR_S* Y, double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+  if (k.NT > MAXT || k.NRG != 1) return cudaErrorInvalidConfiguration;
+  auto fn = k_local_qr<TSQR_S, TSQR_T, NPC, R, MAXT, true, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem_qr);
+  if (e != cudaSuccess) return e;
+  fn<<<(unsigned)p, k.NT, k.smem_qr, st>>>(A, m, n, (int)b, (int)bt, kt, k.CS, k.NRG, Y, Rst, Tst, status);
+  return cudaGetLastError();
+}
+
+cudaError_t TSQR_LOCAL_QR_NOGRAM_NAME(const KernelCfg& k, const void* A, int64_t m, int n, int64_t b, int64_t bt,
+                                      int kt, int64_t p, void* Y, double* Rst, double* Tst, int32_t* status,
+                                      cudaStream_t st) {
+  const TSQR_S* a = static_cast<const TSQR_S*>(A);
+  TSQR_S* y = static_cast<TSQR_S*>(Y);
+  switch (k.tile) {
+    case 0: return local_qr_ng_R<TSQR_R0, TSQR_T0, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 1: return local_qr_ng_R<TSQR_R1, TSQR_T1, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 2: return local_qr_ng_R<TSQR_R2, TSQR_T2, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 3: return local_qr_ng_R<TSQR_R3, TSQR_T3, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 4: return local_qr_ng_R<TSQR_R4, TSQR_T4, kNpc>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 5: return local_qr_ng_R<TSQR_R5, TSQR_T5, TSQR_N5>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    case 6: return local_qr_ng_R<TSQR_R6, TSQR_T6, TSQR_N6>(k, a, m, n, b, bt, kt, p, y, Rst, Tst, status, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+#endif  // TSQR_LOCAL_QR_NOGRAM_NAME
+
 #ifdef TSQR_ROWMUL_NAME
 template <int R, int MAXT, int NPC>
 static cudaError_t rowmul_R(const KernelCfg& k, const TSQR_S* X, const double* M1, const TSQR_S* Y,

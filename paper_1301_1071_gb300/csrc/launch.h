@@ -48,6 +48,13 @@ cudaError_t launch_form_q_tc(float* Y, int64_t m, int n, int64_t b, int B, int64
 cudaError_t launch_form_q_oz(double* Y, int64_t m, int n, int64_t b, int B, int64_t bt, int kt, int64_t p,
                              const double* T, const double* C, int64_t cblocks, int32_t* status, cudaStream_t st);
 
+// The Gram entries v_i^T v_c (i < c) of every tile's Householder vectors
+// into the T slots' strictly upper triangles (binary64 data, n <= 32), on the
+// tensor cores by Ozaki splitting; Step 1 ran without its Gram dot products
+// (launch_local_qr_nogram_f64, which writes Y, R and tau).
+cudaError_t launch_gram_oz(const double* Y, int64_t m, int n, int64_t b, int B, int64_t bt, int kt, int64_t p,
+                           double* T, int32_t* status, cudaStream_t st);
+
 // out_r = X_r M1 + Y_r M2 over p blocks of b rows (X or Y may be NULL).
 cudaError_t launch_rowmul(const KernelCfg& k, const void* X, const double* M1, const void* Y,
                           const double* M2, int64_t m, int n, int64_t b, int64_t p, void* out, int32_t* status,

@@ -202,6 +202,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   P.prec = prec;
   P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcMaxN;
   P.oz3 = prec == TSQR_PREC_OZAKI && n <= kOzMaxN;
+  P.gram_oz = P.oz3 && n <= kGmMaxN && P.cfg0.kind == kKindF64 && P.cfg0.NRG == 1;
   {
     const int kind_rm = esz == 4 ? kKindF32 : kKindF64;
     // the coefficient blocks' padded width: the wider of the two tile widths'

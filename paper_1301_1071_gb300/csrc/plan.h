@@ -72,6 +72,9 @@ struct Plan {
   int prec = 0;          // the resolved tsqr_prec (TSQR_PREC_AUTO taken)
   bool tc3 = false;      // Step 3 on the tensor cores (3xTF32, binary32 data, n <= 64)
   bool oz3 = false;      // Step 3 on the tensor cores (Ozaki split, binary64 data, n <= 32)
+  // Step 1 without its Gram dot products and the T factors' Gram entries on
+  // the tensor cores (k_gram_oz): the Ozaki form with a one-row-group tile
+  bool gram_oz = false;
   // k_rowmul with two inputs (the adjoint): a register tile close to the
   // b_rm2 rows per block whose two inputs fit in shared memory together
   KernelCfg cfg_rm2;

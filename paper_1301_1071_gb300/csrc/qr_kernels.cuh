@@ -350,9 +350,11 @@ using YStore = typename std::conditional<std::is_same<T, df64>::value, df64, S>:
 // zero, so the Householder vectors of tile t are [I; V_t] and only V_t is
 // stored (over A_t's rows of Y).
 // LA (look-ahead form) is launched exactly when NRG == 1.
-// GRAM = false (look-ahead form, binary64 / binary32 compute, Y == NULL):
-// the R-only form skips the dot products that only give Gram entries (about
-// a third of the column loop's FMAs); R is the same bit for bit.
+// GRAM = false (look-ahead form, binary64 / binary32 compute): the dot
+// products that only give Gram entries (about a third of the column loop's
+// FMAs) are skipped; R is the same bit for bit.  With Y == NULL this is the
+// R-only form; with Y, the vectors and tau are written and the Gram entries
+// are left to k_gram_oz (the tensor-core Gram of the Ozaki form).
 // Launch: blockDim = 32*CS*NRG <= MAXT, gridDim = p, dynamic smem = LocalQrSmem.
 // ---------------------------------------------------------------------------
 template <class S, class T, int NPC, int R, int MAXT, bool LA, bool GRAM = true>
@@ -710,15 +712,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       }
     }
 
-    if (GRAM && Y != nullptr) {
+    if (Y != nullptr) {
       // ---- the Gram entries v_i^T v_j (i < j) and tau_j of the compact-WY
       //      form, binary64, into the upper triangle of the tile's T slot (the
-      //      strictly lower part is never read); k_build_t turns them into T
+      //      strictly lower part is never read); k_build_t turns them into T.
+      //      Without the Gram dot products (GRAM = false) only tau_j is
+      //      written: the Gram entries come from k_gram_oz.
       {
         double* Tout = Tst + (static_cast<int64_t>(blockIdx.x) * kt + t) * n * n;
         for (int idx = tid; idx < n * n; idx += NT) {
           const int i = idx / n, kk = idx % n;
-          if (kk >= i) Tout[idx] = static_cast<double>(kk > i ? gram[idx] : taus[i]);
+          if (GRAM ? kk >= i : kk == i) Tout[idx] = static_cast<double>(kk > i ? gram[idx] : taus[i]);
         }
       }
       __syncthreads();

@@ -306,3 +306,22 @@ def test_ozaki_plan(lib, n, want_tc):
     st, nat = _plan(lib, 0, 1_000_000, n, 0, prec=0)
     assert st == 0
     assert (info.block_rows, info.blocks, info.tree_levels) == (nat.block_rows, nat.blocks, nat.tree_levels)
+
+
+def test_ozaki_launches_include_the_tensor_core_gram(lib):
+    """In the Ozaki form Step 1 leaves out its Gram dot products and one more
+    launch forms the T factors' Gram entries on the tensor cores (n <= 32
+    with a one-row-group Step-1 tile, as at 8,000,000 x 25)."""
+    f = lib.tsqr_launch_count
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Opts),
+                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    f.restype = ctypes.c_int
+
+    def count(prec, n):
+        o = Opts(0, 0, 0, None, prec, 0)
+        out = ctypes.c_int32(0)
+        assert f(0, 8_000_000, n, 0, ctypes.byref(o), 0, ctypes.byref(out)) == 0
+        return out.value
+
+    assert count(4, 25) == count(0, 25) + 1
+    assert count(4, 50) == count(0, 50)  # above n = 32: the native binary64 form
