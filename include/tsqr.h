@@ -85,7 +85,7 @@ typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
  * TF32X3: TSQR_F32 data only.  Step 1 as NATIVE; the Step-3 product
  *         Y_i W_i runs on the tensor cores as 3xTF32 split precision
  *         (Y = Yh + Yl, W = Wh + Wl rounded to TF32; Y W ~ Yh Wh + Yh Wl +
- *         Yl Wh, binary32 accumulation) for n <= 64 (NATIVE Step 3 above).
+ *         Yl Wh, binary32 accumulation), for every n.
  * AUTO:   the library's choice for the data: TSQR_F32 data takes TF32X3 at
  *         n >= 64 and NATIVE below; TSQR_F64 data takes NATIVE.
  * OZAKI:  TSQR_F64 data only.  Step 1 as NATIVE (binary64); for n <= 32 the

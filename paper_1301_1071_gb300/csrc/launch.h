@@ -37,7 +37,7 @@ cudaError_t launch_tree_up(const double* X, int64_t rows, int n, int f, int64_t 
 cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, const double* T, const double* C,
                              int64_t cblocks, cudaStream_t st);
 
-// Step 3 for binary32 data on the tensor cores (3xTF32), n <= 64; the block
+// Step 3 for binary32 data on the tensor cores (3xTF32), n <= 100; the block
 // and tile geometry (b, B = the Step-1 register tile, bt, kt) of Step 1.
 cudaError_t launch_form_q_tc(float* Y, int64_t m, int n, int64_t b, int B, int64_t bt, int kt, int64_t p,
                              const double* T, const double* C, int64_t cblocks, int32_t* status, cudaStream_t st);

@@ -200,7 +200,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   if (f < 2 || f > fmax) return TSQR_ERR_SHAPE;
 
   P.prec = prec;
-  P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcMaxN;
+  P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcwMaxN;
   P.oz3 = prec == TSQR_PREC_OZAKI && n <= kOzMaxN;
   P.gram_oz = P.oz3 && n <= kGmMaxN && P.cfg0.kind == kKindF64 && P.cfg0.NRG == 1;
   {

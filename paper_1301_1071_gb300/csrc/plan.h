@@ -70,7 +70,7 @@ struct Plan {
   KernelCfg cfg0;        // Step-1 kernel config (dtype of A)
   KernelCfg cfg64;       // tree kernel config (binary64)
   int prec = 0;          // the resolved tsqr_prec (TSQR_PREC_AUTO taken)
-  bool tc3 = false;      // Step 3 on the tensor cores (3xTF32, binary32 data, n <= 64)
+  bool tc3 = false;      // Step 3 on the tensor cores (3xTF32, binary32 data)
   bool oz3 = false;      // Step 3 on the tensor cores (Ozaki split, binary64 data, n <= 32)
   // Step 1 without its Gram dot products and the T factors' Gram entries on
   // the tensor cores (k_gram_oz): the Ozaki form with a one-row-group tile

@@ -270,6 +270,7 @@ def _launches_dt(lib, op, m, n, dt, block_rows):
 @pytest.mark.parametrize("dt,n,want_prec,want_tc", [
     (1, 50, 0, 0),   # binary32 below n = 64: native binary32 Step 3
     (1, 64, 2, 1),   # binary32 at n = 64: 3xTF32 Step 3 on the tensor cores
+    (1, 100, 2, 1),  # ... up to n = 100 (the wide form)
     (0, 64, 0, 0),   # binary64 data: native binary64
     (0, 25, 0, 0),
 ])

@@ -4,8 +4,9 @@ Step 1 and the tree are those of the FP32 form; the Step-3 product Y_i W_i
 runs on the tensor cores (tcgen05, kind::tf32) with Y and W split into TF32
 high and low parts (three products, binary32 accumulation).  Bars: the FP32
 form's (||Q^TQ - I||_2 <= 1e-5, ||A - QR||_F/||A||_F <= 1e-5, R and Q within
-10 n kappa 2^-23 of the FP64 oracle on the upcast input).  n > 64 falls back
-to the binary32 FMA path and must give the same bars.
+10 n kappa 2^-23 of the FP64 oracle on the upcast input).  n > 64 takes the
+wide form (the running coefficient in binary64 in the workspace, the A
+operands in two K halves), with the same bars.
 """
 import numpy as np
 import pytest
@@ -35,8 +36,14 @@ def _run(A, **kw):
     (37, 37, 0, 0),            # square
     (20_000, 50, 0, 0),
     (60_000, 50, 2999, 0),     # blocks of several register tiles
-    (12_000, 64, 0, 0),        # largest n on the tensor-core path
-    (3000, 100, 0, 0),         # above it: binary32 FMA fallback
+    (12_000, 64, 0, 0),        # largest n of the double-buffered form
+    (3000, 100, 0, 0),         # the wide form (n > 64), one block
+    (20_000, 65, 0, 0),        # smallest wide n
+    (40_000, 77, 3000, 0),     # wide, blocks of several tiles, odd n
+    (30_000, 80, 0, 0),        # K = n, the Q stage at stride n + 1 exceeds the two K halves
+    (25_000, 96, 2000, 0),     # wide, several tiles
+    (60_000, 100, 0, 0),       # the largest n
+    (30_001, 100, 4099, 0),    # ragged last block and last tile
 ])
 def test_tf32x3_parity(m, n, b, f):
     A = ti.gaussian(m, n, 3000 + m + n).astype(np.float32)
@@ -115,3 +122,27 @@ def test_auto_precision_f64_is_binary64():
     Qa, Ra = T.direct(A, prec="auto")
     Qn, Rn = T.direct(A)
     assert torch.equal(Qa, Qn) and torch.equal(Ra, Rn)
+
+
+def test_tf32x3_wide_svd():
+    """The SVD variant at n = 100 (the benchmark's SVD width) with U formed
+    by the wide tensor-core Step 3."""
+    import paper_1301_1071_gb300 as T
+    A = ti.power_spectrum(60_000, 100, 19).astype(np.float32)
+    U, S, V = T.svd(torch.tensor(A, device="cuda"), prec="tf32x3")
+    _, So, _ = oracle.svd(A.astype(np.float64))
+    assert np.max(np.abs(S.cpu().numpy() - So) / So[0]) <= 1e-5
+    e2, _ = oracle.orth_error(U.double().cpu().numpy())
+    assert e2 <= 1e-5
+
+
+def test_tf32x3_wide_host_buffers_match_device():
+    """tsqr_direct_host with the wide tensor-core Step 3 (the coefficient
+    updated in place chunk by chunk) equals tsqr_direct bit for bit."""
+    import paper_1301_1071_gb300 as T
+    m, n, b = 200_000, 90, 2500
+    A = torch.tensor(ti.gaussian(m, n, 33).astype(np.float32))
+    Qh, Rh = T.direct_host(A.pin_memory(), block_rows=b, prec="tf32x3")
+    Qd, Rd = T.direct(A.cuda(), block_rows=b, prec="tf32x3")
+    torch.cuda.synchronize()
+    assert torch.equal(Qh, Qd.cpu()) and torch.equal(Rh, Rd.cpu())
