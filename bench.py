@@ -42,7 +42,7 @@ FP32_PEAK_GFLOPS = 80540.0  # nominal GB300 FP32 CUDA-core rate (152 SMs x 128 F
 # TSQR read A twice and write Q once; refinement repeats the method; the
 # adjoint reads Q and dQ for the Gram, then Q and dQ again and writes dA.
 # The R-only and singular-value-only paths read A once.
-ALG_PASSES = {"direct": 4, "cholqr": 3, "cholqr_ir": 6, "indirect": 3, "indirect_ir": 6, "backward": 5,
+ALG_PASSES = {"direct": 4, "direct_native": 4, "cholqr": 3, "cholqr_ir": 6, "indirect": 3, "indirect_ir": 6, "backward": 5,
               "r_only": 1, "svd_values": 1}
 
 WORKLOADS = {
@@ -253,8 +253,9 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip comparators / fwd+bwd / cpu baseline")
     ap.add_argument("--m", type=int, default=0, help="override the row count (profiling a smaller case)")
-    ap.add_argument("--prec", default="native", choices=["native", "df64", "tf32x3", "ozaki", "auto"],
-                    help="arithmetic of Steps 1 and 3 (df64, ozaki: FP64 data; tf32x3: FP32 data)")
+    ap.add_argument("--prec", default="auto", choices=["native", "df64", "tf32x3", "ozaki", "auto"],
+                    help="arithmetic of Steps 1 and 3 (df64, ozaki: FP64 data; tf32x3: FP32 data; auto: the "
+                         "library's choice, the Ozaki form for FP64 data at n <= 32)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.m:
@@ -322,13 +323,14 @@ def main():
     gbs = alg_bytes / (ms_step * 1e-3) / 1e9
     hbm_peak, peak_src = load_peaks()
 
+    resolved = T.plan_info(T.OP_DIRECT, m, n, A.dtype, w["block_rows"], prec=args.prec)["prec"]
     # dominant kernel: Step 1 (k_local_qr) or Step 3 (k_form_q); both are
     # FMA-bound (binary64 unit for FP64 data, binary32 for FP32 and for
     # double-float compute): 2 m n^2 algorithmic flops per launch
     dom, dom_ms = ("k_local_qr", s1) if s1 >= s3 else ("k_form_q", s3)
     flops = 2.0 * m * n * n
     achieved = flops / (dom_ms * 1e-3) / 1e9
-    if elem == 8 and args.prec == "native":
+    if elem == 8 and args.prec in ("native", "ozaki", "auto"):
         peak, alu_src = FP64_PEAK_GFLOPS, "nominal FP64 rate (recipe table); probe measured 1196 GFLOP/s"
     else:
         peak, alu_src = FP32_PEAK_GFLOPS, "nominal FP32 CUDA-core rate; probe measured 74.8 TFLOP/s"
@@ -377,13 +379,16 @@ def main():
         "metric": METRIC, "value": rows_s, "unit": "rows/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("df64 (binary64 data, pairs of binary32 in Steps 1 and 3, binary64 tree)" if args.prec == "df64"
-                  else "f64 (Step 3 product as an Ozaki split on the tensor cores, exact accumulation)"
-                  if args.prec == "ozaki"
-                  else "f32 (Step 3 product as 3xTF32 on the tensor cores)" if args.prec == "tf32x3"
+        "dtype": ("df64 (binary64 data, pairs of binary32 in Steps 1 and 3, binary64 tree)" if resolved == "df64"
+                  else "f64 (binary64 Householder and tree; the Step-3 product and the T factors' Gram as "
+                       "error-free Ozaki splits on tcgen05: 56/64-bit fixed point, exact binary32 accumulation, "
+                       "one rounding to binary64)" if resolved == "ozaki"
+                  else "f32 (Step 3 product as 3xTF32 on the tensor cores)" if resolved == "tf32x3"
                   else ("f64" if elem == 8 else "f32")),
         "data": "synthetic",
         "config": {"workload": w["name"], "m": m, "n": n, "block_rows": w["block_rows"] or "auto",
+                   "prec": args.prec,
+                   "plan": T.plan_info(T.OP_DIRECT, m, n, A.dtype, w["block_rows"], prec=args.prec),
                    "l2": f"inputs ({gb:.1f} GB) larger than L2; no flush" if gb > 0.2
                    else "inputs smaller than L2", "parallelism": f"replicas x{ws}"},
         "hbm_gbs_algorithmic": gbs, "hbm_frac": gbs / hbm_peak,
@@ -396,15 +401,16 @@ def main():
     }
 
     if not args.no_extras and rank == 0:
-        others = [p for p in (("native", "df64", "ozaki") if elem == 8 else ("native", "tf32x3")) if p != args.prec]
+        others = [p for p in (("native", "df64", "ozaki") if elem == 8 else ("native", "tf32x3"))
+                  if p != resolved]
         line["extras"] = extras(T, torch, A, n, m, dev, other_precs=others)
     if not args.no_extras and rank == 0:
         del Q, work, dbuf, work_h
         torch.cuda.empty_cache()
         is_sweep = args.workload == "sweep" and not args.m
         configs = {"small_100kx10": small_config(T, torch, dev)}
-        if is_sweep and args.prec == "native":
-            configs["stability_sweep_8Mx25"] = stability_sweep(T, torch, dev, A15=A)
+        if is_sweep:
+            configs["stability_sweep_8Mx25"] = stability_sweep(T, torch, dev, A15=A, prec=args.prec)
         del A
         torch.cuda.empty_cache()
         configs.update(config_extras(T, torch, dev))
@@ -496,14 +502,16 @@ def extras(T, torch, A, n, m, dev, steps=3, other_precs=("df64",)):
 KAPPAS = (1.0, 1e4, 1e8, 1e12, 1e15)
 
 
-def stability_sweep(T, torch, dev, A15=None, steps=3, m=8_000_000, n=25):
+def stability_sweep(T, torch, dev, A15=None, steps=3, m=8_000_000, n=25, prec="auto"):
     """The stability sweep of Sec. IV at 8,000,000 x 25 FP64: A = G diag(sigma)
     V^T with sigma log-spaced 1 .. 1/kappa for each kappa, factored by direct
-    TSQR, Cholesky QR, Cholesky QR + one refinement step and indirect TSQR +
-    one refinement step; ||Q^T Q - I||_2 and ||A - QR||_F/||A||_F from the
-    compensated device checker, rows/s and algorithmic HBM GB/s of each."""
+    TSQR (the benchmarked mode and plain binary64), Cholesky QR, Cholesky QR +
+    one refinement step and indirect TSQR + one refinement step;
+    ||Q^T Q - I||_2 and ||A - QR||_F/||A||_F from the compensated device
+    checker, rows/s and algorithmic HBM GB/s of each."""
     timed = _timer(torch, steps)
-    methods = [("direct", lambda A: T.direct(A, check=False)),
+    methods = [("direct", lambda A: T.direct(A, check=False, prec=prec)),
+               ("direct_native", lambda A: T.direct(A, check=False)),
                ("cholqr", lambda A: T.cholqr(A, refine=0, check=False)),
                ("cholqr_ir", lambda A: T.cholqr(A, refine=1, check=False)),
                ("indirect_ir", lambda A: T.indirect_refine(A, refine=1, check=False))]
@@ -521,7 +529,8 @@ def stability_sweep(T, torch, dev, A15=None, steps=3, m=8_000_000, n=25):
                 ms = timed(lambda: fn(A))
                 st = 0
                 try:
-                    fn_check = {"direct": lambda: T.direct(A), "cholqr": lambda: T.cholqr(A),
+                    fn_check = {"direct": lambda: T.direct(A, prec=prec), "direct_native": lambda: T.direct(A),
+                                "cholqr": lambda: T.cholqr(A),
                                 "cholqr_ir": lambda: T.cholqr(A, refine=1),
                                 "indirect_ir": lambda: T.indirect_refine(A, refine=1)}[name]
                     Qx, Rx = fn_check()
@@ -542,7 +551,7 @@ def stability_sweep(T, torch, dev, A15=None, steps=3, m=8_000_000, n=25):
             del A
         torch.cuda.empty_cache()
     return {"workload": "8,000,000x25 FP64, A = G diag(sigma) V^T, sigma log-spaced 1..1/kappa",
-            "checker": "tsqr_accuracy (Dot2 device sums)", "by_kappa": table}
+            "checker": "tsqr_accuracy (Dot2 device sums)", "direct_prec": prec, "by_kappa": table}
 
 
 def small_config(T, torch, dev, steps=50):

@@ -87,14 +87,18 @@ typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
  *         (Y = Yh + Yl, W = Wh + Wl rounded to TF32; Y W ~ Yh Wh + Yh Wl +
  *         Yl Wh, binary32 accumulation), for every n.
  * AUTO:   the library's choice for the data: TSQR_F32 data takes TF32X3 at
- *         n >= 64 and NATIVE below; TSQR_F64 data takes NATIVE.
- * OZAKI:  TSQR_F64 data only.  Step 1 as NATIVE (binary64); for n <= 32 the
- *         Step-3 product Y_i W_i runs on the tensor cores as an error-free
- *         split product (Ozaki, Ogita, Oishi, Rump 2012): each row of Y and
- *         column of W is cut into 7 digits of 8 bits (56 bits) against its
- *         largest exponent, the digit products are accumulated exactly in
- *         binary32 (binary16 operands), recombined in 64-bit integers and
- *         rounded once to binary64.  Above n = 32, NATIVE Step 3. */
+ *         n >= 64 and NATIVE below; TSQR_F64 data takes OZAKI at n <= 32
+ *         and NATIVE above.
+ * OZAKI:  TSQR_F64 data only.  Step 1's Householder factorisation and the
+ *         tree in binary64; for n <= 32 the two products of the method run on
+ *         the tensor cores as error-free split products (Ozaki, Ogita, Oishi,
+ *         Rump 2012): the Step-3 product Y_i W_i (each row of Y and column of
+ *         W cut into 7 digits of 8 bits, 56 bits, against its largest
+ *         exponent) and the Gram entries V^T V of the compact-WY T factors
+ *         (8 digits, 64 bits; Step 1 then leaves them out of its column
+ *         loop).  The digit products accumulate exactly in binary32
+ *         (binary16 operands), are recombined in 64-bit integers and rounded
+ *         once to binary64.  Above n = 32, NATIVE. */
 typedef enum tsqr_prec {
   TSQR_PREC_NATIVE = 0,
   TSQR_PREC_DF64 = 1,
@@ -123,8 +127,9 @@ typedef struct tsqr_opts {
   int32_t tree_fanout; /* R factors merged per Step-2 tree node; 0 = automatic (>= 2) */
   int32_t sync;        /* 1 = synchronise the stream and return the device status */
   /* Optional stage timing (tsqr_direct, tsqr_svd): NULL, or 4 cudaEvent_t
-     handles (as void*) recorded on the stream at the start, after Step 1,
-     after Step 2 (tree up, top QR, SVD, tree down) and after Step 3. */
+     handles (as void*) recorded on the stream at the start, after Step 1's
+     Householder kernel, after Step 2 (the T factors' build, tree up, top QR,
+     SVD, tree down) and after Step 3. */
   void* const* stage_events;
   int32_t prec;        /* tsqr_prec (default 0 = NATIVE) */
   int32_t reserved;    /* must be zero */

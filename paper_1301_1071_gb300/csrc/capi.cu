@@ -78,13 +78,22 @@ cudaError_t launch_local_qr(const KernelCfg& k, const void* A, int64_t m, int n,
 // Step 1 of direct TSQR: Y_i, R_i and the T slots' tau and Gram entries (the
 // Ozaki form: the Gram entries on the tensor cores after a Step 1 without
 // them).
+// The Householder kernel of Step 1 alone (without its Gram dot products in
+// the Ozaki form).
+cudaError_t launch_local_qr_step1(const Plan& P, const void* A, int64_t m, int64_t b, int64_t p, void* Y,
+                                  double* Rst, double* Tst, int32_t* status, cudaStream_t st) {
+  const Level& l0 = P.levels[0];
+  const int n = static_cast<int>(P.n);
+  if (!P.gram_oz) return launch_local_qr(P.cfg0, A, m, n, b, l0.bt, l0.kt, p, Y, Rst, Tst, status, st);
+  return launch_local_qr_nogram_f64(P.cfg0, A, m, n, b, l0.bt, l0.kt, p, Y, Rst, Tst, status, st);
+}
+
 cudaError_t launch_step1(const Plan& P, const void* A, int64_t m, int64_t b, int64_t p, void* Y, double* Rst,
                          double* Tst, int32_t* status, cudaStream_t st) {
   const Level& l0 = P.levels[0];
   const int n = static_cast<int>(P.n);
-  if (!P.gram_oz) return launch_local_qr(P.cfg0, A, m, n, b, l0.bt, l0.kt, p, Y, Rst, Tst, status, st);
-  cudaError_t e = launch_local_qr_nogram_f64(P.cfg0, A, m, n, b, l0.bt, l0.kt, p, Y, Rst, Tst, status, st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = launch_local_qr_step1(P, A, m, b, p, Y, Rst, Tst, status, st);
+  if (e != cudaSuccess || !P.gram_oz) return e;
   return launch_gram_oz(static_cast<const double*>(Y), m, n, b, P.cfg0.B, l0.bt, l0.kt, p, Tst, status, st);
 }
 
@@ -289,8 +298,13 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   // Step 1: local QR of every row block; Y_0 is written into Q's storage.
   const Level& l0 = P.levels[0];
   if (mark(o, 0, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  if (launch_step1(P, A, P.m, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess) return TSQR_ERR_CUDA;
+  if (launch_local_qr_step1(P, A, P.m, l0.b, l0.p, Q, S(0), T(0), status, st) != cudaSuccess) return TSQR_ERR_CUDA;
   if (mark(o, 1, st) != TSQR_OK) return TSQR_ERR_CUDA;
+  // the T factors' Gram entries on the tensor cores (Ozaki form); like the T
+  // build below, it is part of the Step-2 interval of the stage events
+  if (P.gram_oz && launch_gram_oz(static_cast<const double*>(Q), P.m, n, l0.b, P.cfg0.B, l0.bt, l0.kt, l0.p, T(0),
+                                  status, st) != cudaSuccess)
+    return TSQR_ERR_CUDA;
   // The row blocks' T factors are read only by Step 3 and the tree reads only
   // the stack of R factors, so for a large T build the tree runs on a side
   // stream of the device's highest priority beside it: the block scheduler

@@ -142,8 +142,10 @@ size_t op_bytes(const Plan& P, int op) {
 int resolve_prec(int prec, int esz, int64_t n) {
   if (prec != TSQR_PREC_AUTO) return prec;
   // binary32 data: the Step-3 product on the tensor cores from n = 64 up,
-  // where its share of the pass outgrows the split's overhead
-  return (esz == 4 && n >= kAutoTf32MinN) ? TSQR_PREC_TF32X3 : TSQR_PREC_NATIVE;
+  // where its share of the pass outgrows the split's overhead; binary64 data:
+  // the error-free (Ozaki) tensor-core products where they apply (n <= 32)
+  if (esz == 4) return n >= kAutoTf32MinN ? TSQR_PREC_TF32X3 : TSQR_PREC_NATIVE;
+  return n <= kOzMaxN ? TSQR_PREC_OZAKI : TSQR_PREC_NATIVE;
 }
 
 int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec, int sms) {

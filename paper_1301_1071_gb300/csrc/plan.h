@@ -106,7 +106,8 @@ constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM
 
 // TSQR_PREC_AUTO -> the concrete mode for this dtype and n (other modes
 // are returned unchanged): binary32 data at n >= kAutoTf32MinN takes the
-// 3xTF32 Step 3, everything else the data's own arithmetic.
+// 3xTF32 Step 3, binary64 data at n <= 32 the Ozaki form, everything else
+// the data's own arithmetic.
 constexpr int kAutoTf32MinN = 64;
 int resolve_prec(int prec, int esz, int64_t n);
 

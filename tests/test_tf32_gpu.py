@@ -116,12 +116,15 @@ def test_auto_precision_parity(n):
     assert oracle.orth_error(Q)[0] <= 1e-5
 
 
-def test_auto_precision_f64_is_binary64():
+@pytest.mark.parametrize("n,mode", [(30, "ozaki"), (50, "native")])
+def test_auto_precision_f64(n, mode):
+    """Binary64 data: AUTO is the Ozaki form at n <= 32 and binary64 above,
+    bit for bit."""
     import paper_1301_1071_gb300 as T
-    A = torch.tensor(ti.gaussian(20_000, 30, 3200), device="cuda")
+    A = torch.tensor(ti.gaussian(20_000, n, 3200 + n), device="cuda")
     Qa, Ra = T.direct(A, prec="auto")
-    Qn, Rn = T.direct(A)
-    assert torch.equal(Qa, Qn) and torch.equal(Ra, Rn)
+    Qx, Rx = T.direct(A, prec=mode)
+    assert torch.equal(Qa, Qx) and torch.equal(Ra, Rx)
 
 
 def test_tf32x3_wide_svd():
