@@ -404,7 +404,7 @@ def main():
     if not args.no_extras and rank == 0:
         others = [p for p in (("native", "df64", "ozaki") if elem == 8 else ("native", "tf32x3"))
                   if p != resolved]
-        line["extras"] = extras(T, torch, A, n, m, dev, other_precs=others)
+        line["extras"] = extras(T, torch, A, n, m, dev, other_precs=others, prec=args.prec)
     if not args.no_extras and rank == 0:
         del Q, work, dbuf, work_h
         torch.cuda.empty_cache()
@@ -439,7 +439,7 @@ def _timer(torch, steps):
     return timed
 
 
-def extras(T, torch, A, n, m, dev, steps=3, other_precs=("df64",)):
+def extras(T, torch, A, n, m, dev, steps=3, other_precs=("df64",), prec="auto"):
     """fwd+bwd, the other precision mode, the unstable comparators, the R-only
     and singular-value-only paths and cuSOLVER on the headline matrix."""
     out = {}
@@ -454,11 +454,11 @@ def extras(T, torch, A, n, m, dev, steps=3, other_precs=("df64",)):
     WR = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
 
     def fb():
-        Qx, Rx = T.direct(A, check=False)
+        Qx, Rx = T.direct(A, check=False, prec=prec)
         T.backward(Qx, Rx, WQ, WR, check=False)
 
     ms = timed(fb)
-    out["fwd_bwd"] = {"rows_s": m / (ms * 1e-3), "ms": ms,
+    out["fwd_bwd"] = {"rows_s": m / (ms * 1e-3), "ms": ms, "forward_prec": prec,
                       "hbm_gbs_algorithmic": (ALG_PASSES["direct"] + ALG_PASSES["backward"]) * m * n *
                       A.element_size() / (ms * 1e-3) / 1e9}
     del WQ
@@ -563,18 +563,19 @@ def small_config(T, torch, dev, steps=50):
     m, n = 100_000, 10
     A_np = ti.gaussian(m, n, ti.SEED_SMALL)
     A = torch.from_numpy(A_np).to(dev)
-    Q, R = T.direct(A, block_rows=1000)
+    Q, R = T.direct(A, block_rows=1000, prec="auto")
     timed = _timer(torch, steps)
-    ms = timed(lambda: T.direct(A, block_rows=1000, check=False))
+    ms = timed(lambda: T.direct(A, block_rows=1000, check=False, prec="auto"))
+    ms_native = timed(lambda: T.direct(A, block_rows=1000, check=False))
     acc = T.accuracy(Q, R, A)
     Ro = oracle.householder_r(A_np)
-    plan = T.plan_info(T.OP_DIRECT, m, n, torch.float64, block_rows=1000)
-    return {"workload": "100,000x10 FP64 i.i.d. N(0,1), row blocks of 1,000", "ms": ms,
+    plan = T.plan_info(T.OP_DIRECT, m, n, torch.float64, block_rows=1000, prec="auto")
+    return {"workload": "100,000x10 FP64 i.i.d. N(0,1), row blocks of 1,000", "ms": ms, "ms_native": ms_native,
             "rows_s": m / (ms * 1e-3), "hbm_gbs_algorithmic": ALG_PASSES["direct"] * m * n * 8 / (ms * 1e-3) / 1e9,
             "orth_error_2": acc["orth_2"], "residual_F": acc["res_F"],
             "r_error_vs_oracle": float(np.linalg.norm(R.cpu().numpy() - Ro) / np.linalg.norm(Ro)),
             "plan": plan,
-            "launches": T.launch_count(T.OP_DIRECT, m, n, torch.float64, block_rows=1000)}
+            "launches": T.launch_count(T.OP_DIRECT, m, n, torch.float64, block_rows=1000, prec="auto")}
 
 
 def config_extras(T, torch, dev, steps=3):
@@ -641,16 +642,19 @@ def config_extras(T, torch, dev, steps=3):
         for r0 in range(0, m, 1 << 22):
             rows = min(1 << 22, m - r0)
             A[r0:r0 + rows] = (torch.randn(rows, n, dtype=torch.float64, device=dev, generator=g) @ M).float()
-        U, S, Vo = T.svd(A)
-        ms = timed(lambda: T.svd(A, check=False))
+        U, S, Vo = T.svd(A, prec="auto")
+        ms = timed(lambda: T.svd(A, check=False, prec="auto"))
         out["svd_20Mx100"] = {"workload": "20,000,000x100 FP32 storage, G diag(j^-2) V^T",
+                              "prec": T.plan_info(T.OP_SVD, m, n, torch.float32, prec="auto")["prec"],
                               "rows_s": m / (ms * 1e-3), "ms": ms, "orth_error_2_U": T.accuracy(U)["orth_2"],
                               "max_rel_sigma_dev": float((S / sig - 1).abs().max()),
                               "hbm_gbs_algorithmic": 4 * m * n * 4 / (ms * 1e-3) / 1e9}
-        for prec in ("tf32x3",):
-            msp = timed(lambda: T.svd(A, check=False, prec=prec))
-            out["svd_20Mx100"][f"ms_{prec}"] = msp
-        del U, A
+        del U
+        Un, _, _ = T.svd(A)
+        out["svd_20Mx100"]["native"] = {"ms": timed(lambda: T.svd(A, check=False)),
+                                        "orth_error_2_U": T.accuracy(Un)["orth_2"]}
+        del Un
+        del A
     except Exception as e:
         out["svd_20Mx100"] = {"error": f"{type(e).__name__}: {e}"}
     torch.cuda.empty_cache()
