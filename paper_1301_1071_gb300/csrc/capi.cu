@@ -11,6 +11,7 @@
 #include "launch.h"
 #include "plan.h"
 #include "small.cuh"
+#include "tc_kernels.cuh"
 
 namespace tsqr {
 
@@ -325,7 +326,7 @@ tsqr_status run_direct(const Plan& P, const void* A, void* Q, double* R, int64_t
   TSQR_CUDA(side.rejoin());
   // Step 3: Q_i = Q1_i Q2_i over the Y_i held in Q.
   if (mark(o, 2, st) != TSQR_OK) return TSQR_ERR_CUDA;
-  const double* C0 = (L == 1) ? ctop : S(0);
+  double* C0 = (L == 1) ? ctop : S(0);
   const int64_t cb0 = (L == 1) ? 1 : l0.p;
   const cudaError_t e3 =
       P.oz3   ? launch_form_q_oz(static_cast<double*>(Q), P.m, n, l0.b, P.cfg0.B, l0.bt, l0.kt, l0.p, T(0), C0, cb0,
@@ -446,12 +447,12 @@ tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, 
   TSQR_TRY(run_tree(P, Rd, n, work, st, [](double*, cudaStream_t) { return TSQR_OK; }));
   TSQR_CUDA(cudaMemcpyAsync(Rh, Rd, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
   // Step 3, chunk by chunk, each chunk of Q copied back behind the next
-  const double* C0 = (L == 1) ? ctop : S0;
+  double* C0 = (L == 1) ? ctop : S0;
   for (int c = 0; c < chunks; ++c) {
     int64_t b0, pcnt, r0, rows;
     chunk_rows(c, &b0, &pcnt, &r0, &rows);
     if (pcnt <= 0) continue;
-    const double* Cc = (L == 1) ? C0 : C0 + b0 * nn;
+    double* Cc = (L == 1) ? C0 : C0 + b0 * nn;
     const int64_t cb = (L == 1) ? 1 : pcnt;
     char* Y = dbuf + r0 * row_bytes;
     TSQR_CUDA(P.oz3   ? launch_form_q_oz(reinterpret_cast<double*>(Y), rows, n, l0.b, P.cfg0.B, l0.bt, l0.kt, pcnt,
@@ -525,11 +526,12 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
                            device_sms());
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   const int L = static_cast<int>(P.levels.size());
-  const int g = P.gram_oz ? 1 : 0;  // the tensor-core Gram after Step 1
+  const int g = P.gram_oz ? 1 : 0;                     // the tensor-core Gram after Step 1
+  const int w = (P.tc3 && P.n <= kTcMaxN) ? 1 : 0;     // the W chain before the 3xTF32 stream
   switch (op) {
-    case TSQR_OP_DIRECT_HOST: *launches = (3 + g) * chunks + 3 * (L - 1) + 1; break;  // chunks x (Step 1, T, Step 3)
-    case TSQR_OP_DIRECT: *launches = 3 * L + 1 + g; break;    // L up (+ T build), sign fix, L down
-    case TSQR_OP_SVD: *launches = 3 * L + 2 + g; break;       // + Jacobi SVD
+    case TSQR_OP_DIRECT_HOST: *launches = (3 + g + w) * chunks + 3 * (L - 1) + 1; break;  // chunks x (Step 1, T, Step 3)
+    case TSQR_OP_DIRECT: *launches = 3 * L + 1 + g + w; break;    // L up (+ T build), sign fix, L down
+    case TSQR_OP_SVD: *launches = 3 * L + 2 + g + w; break;       // + Jacobi SVD
     case TSQR_OP_CHOLQR: *launches = 4 * (1 + refine_steps) + refine_steps; break;  // gram, reduce, chol, rowmul (+ combine)
     case TSQR_OP_INDIRECT: *launches = (L + 3) * (1 + refine_steps) + refine_steps; break;
     case TSQR_OP_BACKWARD: *launches = 4; break;              // gram, reduce, prep, rowmul

@@ -38,9 +38,10 @@ cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, c
                              int64_t cblocks, cudaStream_t st);
 
 // Step 3 for binary32 data on the tensor cores (3xTF32), n <= 100; the block
-// and tile geometry (b, B = the Step-1 register tile, bt, kt) of Step 1.
+// and tile geometry (b, B = the Step-1 register tile, bt, kt) of Step 1.  For
+// n <= 64 the T slots and C are overwritten (with W and X_0).
 cudaError_t launch_form_q_tc(float* Y, int64_t m, int n, int64_t b, int B, int64_t bt, int kt, int64_t p,
-                             const double* T, const double* C, int64_t cblocks, int32_t* status, cudaStream_t st);
+                             double* T, double* C, int64_t cblocks, int32_t* status, cudaStream_t st);
 
 // Step 3 for binary64 data with the product Y W on the tensor cores by
 // Ozaki splitting (binary16 digits, exact binary32 accumulation), n <= 32;

@@ -1,22 +1,34 @@
 // tc_kernels.cuh -- Step 3 (Sec. III-B) for binary32 data with the product
-// Y_i W_i on the 5th-generation tensor cores: tcgen05.mma kind::tf32, operands
-// in shared memory, the 128 x N accumulator in tensor memory.  3xTF32 split
-// precision: Y = Yh + Yl and W = Wh + Wl with Yh, Yl, Wh, Wl rounded to TF32,
-// Y W ~ Yh Wh + Yh Wl + Yl Wh (the dropped Yl Wl is below binary32 rounding).
+// Y_i W_i on the 5th-generation tensor cores: tcgen05.mma kind::tf32, the
+// accumulator in tensor memory.  3xTF32 split precision: Y = Yh + Yl and
+// W = Wh + Wl with Yh, Yl, Wh, Wl rounded to TF32, Y W ~ Yh Wh + Yh Wl + Yl Wh
+// (the dropped Yl Wl is below binary32 rounding).
 //
-// One CTA per row block (as k_form_q): the tiles of the block are taken last
-// to first with X = C (see k_form_q); W of each tile is formed on the CUDA
-// cores in binary32, split into the B operands, and the tile's rows are
-// processed in chunks of 128 rows: each chunk arrives by bulk copy (TMA) into
-// one of two Y buffers while the previous chunk is processed, is split into
-// the A operands, multiplied by one MMA chain (K/8 steps x 3 products) that
-// completes on an mbarrier, read back from tensor memory with tcgen05.ld, and
-// Q = [X; 0] - D (tile 0) or -D is written over Y through the same buffer.
+// n <= kTcMaxN, two launches.  A row block's Q is H_0 H_1 .. H_{k-1} [C; 0],
+// H_t = I - Y_t T_t Y_t^T the compact-WY factor of its tile t.  Applied last
+// to first, every tile t > 0 meets the running coefficient X only in its
+// carried triangle (Y_t = [I; V_t] there), so its W_t = T_t X and the update
+// X -= W_t involve n x n matrices alone; tile 0 adds Y_top^T.  k_w_chain runs
+// that chain per block on the CUDA cores and leaves -W_t, split into TF32
+// hi and lo parts, in T slot t and X_0 in the block's C.  Every 128-row
+// chunk of every tile is then an independent product Q = Y (-W_t) (+ X_0 on
+// the block's first n rows), which k_form_q_tc streams: a persistent CTA per
+// SM takes a contiguous run of chunks; two groups of four warps take
+// alternate chunks, so one group's TF32 split and write-back overlap the
+// other's MMA.  A thread owns one row of a chunk (its tensor-memory lane): it
+// splits the row staged by the bulk copy into A_hi / A_lo columns of tensor
+// memory (tcgen05.st), and after the MMA chain reads its row of the
+// accumulator back (tcgen05.ld) into the same staging row, which one bulk
+// copy then writes over Y.
 //
-// Operand layout: no swizzle, K-major: core matrices of 8 rows x 16 bytes
-// (4 TF32 values); element (r, k) at ((r/8) * K/4 + k/4) * 128 + (r%8) * 16 +
-// (k%4) * 4 bytes, so the descriptor's leading-dimension offset (next core
-// along K) is 128 bytes and its stride offset (next 8-row group) K/4 * 128.
+// The wide form (n > kTcMaxN, k_form_q_tcw) keeps one CTA per block, forms W
+// per tile on the CUDA cores and stages A in shared memory.
+//
+// B operand layout (shared memory): no swizzle, K-major: core matrices of 8
+// rows x 16 bytes (4 TF32 values); element (c, k) at ((c/8) * K/4 + k/4) *
+// 128 + (c%8) * 16 + (k%4) * 4 bytes, so the descriptor's leading-dimension
+// offset (next core along K) is 128 bytes and its stride offset (next 8-row
+// group) K/4 * 128.
 #pragma once
 
 #include <cstdint>
@@ -28,37 +40,59 @@
 namespace tsqr {
 
 constexpr int kTcM = 128;        // rows per MMA chunk (TMEM lanes)
-constexpr int kTcThreads = 512;  // 16 warps: warp w reads TMEM lanes 32 (w % 4) ..
-constexpr int kTcMaxN = 64;      // largest n on this path
-constexpr int kTcMaxE = (kTcMaxN * kTcMaxN + kTcThreads - 1) / kTcThreads;  // W entries per thread
+constexpr int kTcThreads = 512;  // the wide form: 16 warps, warp w reads TMEM lanes 32 (w % 4) ..
+constexpr int kTcMaxN = 64;      // largest n of the streaming form
 
 TSQR_HD constexpr int tc_k(int n) { return (n + 7) / 8 * 8; }     // K: MMA K step is 8
 TSQR_HD constexpr int tc_n(int n) { return (n + 15) / 16 * 16; }  // N: multiple of 16 at M = 128
 TSQR_HD constexpr int tc_cols(int n) { return tc_n(n) <= 32 ? 32 : (tc_n(n) <= 64 ? 64 : 128); }  // TMEM alloc
 
-// Shared-memory layout of k_form_q_tc.  The A buffers double as the stage of
-// the n x n operands in the prologue and of the Q rows in the epilogue.
-// Y chunks are double-buffered: the bulk copy of the next chunk runs while
-// the current one is converted, multiplied and written back.  A Y buffer
-// holds 128 rows at row stride n (bulk copy) and later the Q rows at the odd
-// stride n + 1 (conflict-free epilogue).
+// ---- the streaming form (n <= kTcMaxN)
+constexpr int kTqGroupWarps = 8;                          // a row group: 2 warps per 32-row lane quarter
+constexpr int kTqGroupThreads = 32 * kTqGroupWarps;
+constexpr int kTqBuildWarps = 2;                         // B operand builders
+constexpr int kTqThreads = (2 * kTqGroupWarps + 2 + kTqBuildWarps) * 32;  // row groups, MMA, copy, builders
+constexpr int kWcThreads = 256;  // k_w_chain
+constexpr int kWcMaxE = (kTcMaxN * kTcMaxN + kWcThreads - 1) / kWcThreads;  // T entries per thread
+constexpr int kTqMinSmem = 120 * 1024;  // one CTA per SM (tensor memory is sized for one)
+// tensor-memory columns of one group: A_hi (K), A_lo (K), D (N), as a power of two
+TSQR_HD constexpr int tq_gcols(int n) {
+  return 2 * tc_k(n) + tc_n(n) <= 32 ? 32
+       : (2 * tc_k(n) + tc_n(n) <= 64 ? 64 : (2 * tc_k(n) + tc_n(n) <= 128 ? 128 : 256));
+}
+
+// Shared memory of k_form_q_tc: 2 nb Y buffers (a chunk as one contiguous
+// copy, row stride n, after a head offset below 16 bytes), the B operands of
+// two tiles (by ordinal parity), the mbarriers (full[6], aready[2], dfull[2],
+// qstaged[2], bready[2], bfree[2]) and the chunk descriptors (one per Y
+// buffer, 48 bytes each).
 struct FormQTcSmem {
-  size_t a_hi, a_lo, b_hi, b_lo, xm, wm, ybuf0, ybuf1, bar, lbar, tslot, total;
+  size_t ybuf, ybytes, bop, bbytes, bars, desc, tslot, total;
+  int nb;  // Y buffers per group (3 where they fit, else 2)
   TSQR_HD FormQTcSmem(int n) {
     const size_t K = tc_k(n), N = tc_n(n);
+    ybytes = align_up((size_t)kTcM * n * 4 + 16, 128);
+    bbytes = 2 * N * K * 4;  // hi, then lo
+    nb = 6 * ybytes + 2 * bbytes + 1536 <= 232448 ? 3 : 2;
     size_t o = 0;
-    a_hi = o; o = align_up(o + kTcM * K * 4, 128);
-    a_lo = o; o = align_up(o + kTcM * K * 4, 128);
-    b_hi = o; o = align_up(o + N * K * 4, 128);
-    b_lo = o; o = align_up(o + N * K * 4, 128);
-    xm = o; o = align_up(o + (size_t)n * n * 4, 16);
-    wm = o; o = align_up(o + (size_t)n * n * 4, 16);
-    ybuf0 = o; o = align_up(o + (size_t)kTcM * (n + 1) * 4, 128);
-    ybuf1 = o; o = align_up(o + (size_t)kTcM * (n + 1) * 4, 128);
-    bar = o; o = align_up(o + 8, 8);
-    lbar = o; o = align_up(o + 16, 8);
+    ybuf = o; o += 2 * (size_t)nb * ybytes;
+    bop = o; o = align_up(o + 2 * bbytes, 128);
+    bars = o; o += 16 * 8;
+    desc = o; o += 6 * 48;
     tslot = o; o = align_up(o + 8, 16);
     total = o;
+  }
+};
+
+// k_w_chain: T_t^T, X and Z (binary32, n x n each)
+struct WChainSmem {
+  size_t ts, xs, zs, total;
+  TSQR_HD WChainSmem(int n) {
+    const size_t nn4 = (size_t)n * n * 4;
+    ts = 0;
+    xs = align_up(nn4, 16);
+    zs = xs + align_up(nn4, 16);
+    total = zs + align_up(nn4, 16);
   }
 };
 
@@ -97,302 +131,636 @@ struct FormQTcwSmem {
 // (kern_tc.cu); the planner includes this header for the geometry above.
 #if defined(__CUDACC__) && defined(TSQR_TC_KERNELS)
 
+// x rounded to TF32 (10 fraction bits), to nearest with ties away from
+// zero: half of the dropped 13 bits' weight is added to the magnitude bits,
+// which are then cut (finite x, two integer operations).
 __device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 
-// Step 3, binary32 data, tensor-core product.
-//   Yg : m x n (binary32), Y as written by k_local_qr; Q is written over it.
-//   Tg : kt slots of n x n binary64 per block (upper triangle).
-//   Cg : cblocks blocks of n x n binary64 (cblocks == 1: one C for all).
-// Launch: gridDim = p, blockDim = kTcThreads, dynamic smem = FormQTcSmem(n).
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_form_q_tc(float* Yg, int64_t m, int n, int b, int B, int bt, int kt, const double* __restrict__ Tg,
-                const double* __restrict__ Cg, int64_t cblocks, int32_t* status) {
+// The W chain of Step 3 for one row block per CTA (binary32, CUDA cores):
+//   X = C;  for t = k-1 .. 1: W_t = T_t X, X -= W_t;  W_0 = T_0 (Y_top^T X)
+// with Y_top the block's first min(rows, n) rows of Y (unit lower
+// triangular).  Writes -W_t split into TF32 parts, hi then lo (n x n each,
+// row-major, binary32), over T slot t, and X_0 = X (binary32) over the first
+// half of the block's C; T_t and C are read before they are written.  W = T src runs as 4 x 5 register blocks (rows kk0 ..,
+// columns c0b ..), T staged transposed so a warp's row block is one broadcast.
+// Launch: gridDim = p, blockDim = kWcThreads, dynamic smem = WChainSmem(n).
+__global__ void __launch_bounds__(kWcThreads, 3)
+    k_w_chain(const float* __restrict__ Yg, int64_t m, int n, int64_t b, int B, int bt, int kt, double* Tg,
+              double* Cg, int64_t cblocks) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const FormQTcSmem L(n);
-  float* a_hi = reinterpret_cast<float*>(smem + L.a_hi);
-  float* a_lo = reinterpret_cast<float*>(smem + L.a_lo);
-  float* b_hi = reinterpret_cast<float*>(smem + L.b_hi);
-  float* b_lo = reinterpret_cast<float*>(smem + L.b_lo);
-  float* xm = reinterpret_cast<float*>(smem + L.xm);
-  float* wm = reinterpret_cast<float*>(smem + L.wm);
-  float* stage = a_hi;  // n x n operands of the prologue; spans a_hi and a_lo
-  float* ybuf[2] = {reinterpret_cast<float*>(smem + L.ybuf0), reinterpret_cast<float*>(smem + L.ybuf1)};
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);    // MMA completion
-  uint64_t* lbar = reinterpret_cast<uint64_t*>(smem + L.lbar);  // Y chunk arrival, one per buffer
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int K = tc_k(n), N = tc_n(n), NC = tc_cols(n);
-  const int nn = n * n;
-  const int64_t row0 = static_cast<int64_t>(blockIdx.x) * b;
+  const WChainSmem L(n);
+  float* ts = reinterpret_cast<float*>(smem + L.ts);
+  float* xs = reinterpret_cast<float*>(smem + L.xs);
+  float* zs = reinterpret_cast<float*>(smem + L.zs);
+  const int tid = threadIdx.x, nn = n * n;
+  const int64_t blk = blockIdx.x, row0 = blk * b;
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
   const int ntiles = rows <= B ? 1 : 1 + (rows - B + bt - 1) / bt;
   const int ntop = rows < n ? rows : n;
-  const uint32_t idesc = tc_idesc_tf32(kTcM, N);
-  const int KQ = K / 4;  // core matrices along K
-  const uint32_t lbo = 128, sbo = static_cast<uint32_t>(KQ) * 128;
-
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    mbar_init(lbar, 1);
-    mbar_init(lbar + 1, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(NC)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  const int64_t cb = cblocks == 1 ? 0 : static_cast<int64_t>(blockIdx.x);
-  for (int idx = tid; idx < nn; idx += kTcThreads) xm[idx] = static_cast<float>(Cg[cb * nn + idx]);  // X = C
-  // this thread's entries of an n x n product: idx = tid + e kTcThreads = kk n + c
-  int ekk[kTcMaxE], ec[kTcMaxE];
-  {
-    int kk = tid / n, c = tid % n;
-    const int dk = kTcThreads / n, dc = kTcThreads % n;
+  const int64_t cb = cblocks == 1 ? 0 : blk;
+  for (int idx = tid; idx < nn; idx += kWcThreads) xs[idx] = static_cast<float>(Cg[cb * nn + idx]);
+  const int nrb = (n + kTcwRB - 1) / kTcwRB, ncb = (n + kTcwCB - 1) / kTcwCB;
+  const bool wblk = tid < nrb * ncb;
+  const int kk0 = (tid / ncb) * kTcwRB, c0b = (tid % ncb) * kTcwCB;
+  double tp[kWcMaxE];  // T of the next tile, fetched one step ahead
+  auto fetch_t = [&](int t) {
+    const double* Tb = Tg + (blk * kt + t) * nn;
 #pragma unroll
-    for (int e = 0; e < kTcMaxE; ++e) {
-      ekk[e] = kk;
-      ec[e] = c;
-      kk += dk;
-      c += dc;
-      if (c >= n) {
-        c -= n;
-        ++kk;
+    for (int e = 0; e < kWcMaxE; ++e) {
+      const int idx = tid + e * kWcThreads;
+      tp[e] = idx < nn ? Tb[idx] : 0.0;
+    }
+  };
+  fetch_t(ntiles - 1);
+  for (int t = ntiles - 1; t >= 0; --t) {
+    const float* src = xs;
+    if (t == 0) {
+      // Z = Y_top^T X: Z[kk] = X[kk] + sum_{kk < r < ntop} Y[r][kk] X[r] (zero for kk >= ntop)
+      for (int idx = tid; idx < ntop * n; idx += kWcThreads) ts[idx] = Yg[row0 * n + idx];
+      __syncthreads();
+      if (wblk) {
+        float zb[kTcwRB][kTcwCB];
+#pragma unroll
+        for (int r = 0; r < kTcwRB; ++r)
+#pragma unroll
+          for (int c = 0; c < kTcwCB; ++c)
+            zb[r][c] = (kk0 + r < ntop && c0b + c < n) ? xs[(kk0 + r) * n + c0b + c] : 0.0f;
+        for (int i = kk0 + 1; i < ntop; ++i) {
+          float yv[kTcwRB], xv[kTcwCB];
+#pragma unroll
+          for (int r = 0; r < kTcwRB; ++r) yv[r] = (i > kk0 + r && kk0 + r < n) ? ts[i * n + kk0 + r] : 0.0f;
+#pragma unroll
+          for (int c = 0; c < kTcwCB; ++c) xv[c] = c0b + c < n ? xs[i * n + c0b + c] : 0.0f;
+#pragma unroll
+          for (int r = 0; r < kTcwRB; ++r)
+#pragma unroll
+            for (int c = 0; c < kTcwCB; ++c) zb[r][c] = fmaf(yv[r], xv[c], zb[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < kTcwRB; ++r)
+#pragma unroll
+          for (int c = 0; c < kTcwCB; ++c)
+            if (kk0 + r < n && c0b + c < n) zs[(kk0 + r) * n + c0b + c] = zb[r][c];
+      }
+      __syncthreads();  // Y_top's reads of ts are done before T_0 is staged
+      src = zs;
+    }
+    // T_t transposed into ts (upper triangle; binary64 rounded to binary32)
+#pragma unroll
+    for (int e = 0; e < kWcMaxE; ++e) {
+      const int idx = tid + e * kWcThreads;
+      if (idx < nn) {
+        const int kk = idx / n, i = idx % n;
+        ts[i * n + kk] = i >= kk ? static_cast<float>(tp[e]) : 0.0f;
+      }
+    }
+    if (t > 0) fetch_t(t - 1);
+    __syncthreads();
+    float wb[kTcwRB][kTcwCB];
+#pragma unroll
+    for (int r = 0; r < kTcwRB; ++r)
+#pragma unroll
+      for (int c = 0; c < kTcwCB; ++c) wb[r][c] = 0.0f;
+    if (wblk) {
+      for (int i = kk0; i < n; ++i) {
+        float tv[kTcwRB], sv[kTcwCB];
+#pragma unroll
+        for (int r = 0; r < kTcwRB; ++r) tv[r] = kk0 + r < n ? ts[i * n + kk0 + r] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < kTcwCB; ++c) sv[c] = c0b + c < n ? src[i * n + c0b + c] : 0.0f;
+#pragma unroll
+        for (int r = 0; r < kTcwRB; ++r)
+#pragma unroll
+          for (int c = 0; c < kTcwCB; ++c) wb[r][c] = fmaf(tv[r], sv[c], wb[r][c]);
+      }
+    }
+    __syncthreads();  // every read of ts and src is done
+    float* Wout = reinterpret_cast<float*>(Tg + (blk * kt + t) * nn);
+    if (t == 0) {
+      float* X0 = reinterpret_cast<float*>(Cg + cb * nn);  // C was read into xs
+      for (int idx = tid; idx < nn; idx += kWcThreads) X0[idx] = xs[idx];
+    }
+    if (wblk) {
+#pragma unroll
+      for (int r = 0; r < kTcwRB; ++r)
+#pragma unroll
+        for (int c = 0; c < kTcwCB; ++c) {
+          const int kk = kk0 + r, cc = c0b + c;
+          if (kk < n && cc < n) {
+            const float hv = tf32_round(-wb[r][c]);
+            Wout[kk * n + cc] = hv;
+            Wout[nn + kk * n + cc] = tf32_round(-wb[r][c] - hv);
+            if (t > 0) xs[kk * n + cc] -= wb[r][c];
+          }
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// The chunks of Step 3: tile t of a block of `rows` rows holds rows
+// [0, min(rows, B)) (t = 0) or [B + (t-1) bt, ..) (at most bt rows); each
+// tile is cut into chunks of kTcM rows, taken block by block, tile by tile.
+struct TqGeom {
+  int64_t m, b, p;
+  int n, B, bt;
+  int64_t cpb_full, cpb_last, nfull;  // chunks per full block, of the last block; chunks of the full blocks
+  TSQR_HD static int64_t tiles_of(int64_t rows, int B, int bt) { return rows <= B ? 1 : 1 + (rows - B + bt - 1) / bt; }
+  TSQR_HD static int64_t chunks_of(int64_t rows, int B, int bt) {
+    const int64_t r0 = rows < B ? rows : B;
+    int64_t c = (r0 + kTcM - 1) / kTcM;
+    if (rows > B) {
+      const int64_t kt = tiles_of(rows, B, bt);
+      const int64_t last = rows - B - (kt - 2) * bt;
+      c += (kt - 2) * ((bt + kTcM - 1) / kTcM) + (last + kTcM - 1) / kTcM;
+    }
+    return c;
+  }
+  TSQR_HD TqGeom(int64_t m_, int n_, int64_t b_, int B_, int bt_, int64_t p_)
+      : m(m_), b(b_), p(p_), n(n_), B(B_), bt(bt_) {
+    cpb_full = chunks_of(b, B, bt);
+    cpb_last = chunks_of(m - (p - 1) * b, B, bt);
+    nfull = (p - 1) * cpb_full;
+  }
+  TSQR_HD int64_t total() const { return nfull + cpb_last; }
+  TSQR_HD int64_t rows_of(int64_t blk) const { return blk == p - 1 ? m - (p - 1) * b : b; }
+};
+
+// A position in the chunk sequence: set() places it (divisions), next()
+// moves it one chunk on (no division but at a block change).
+struct TqCursor {
+  int64_t blk, rows_b;  // block and its rows
+  int64_t off;          // element offset of the chunk in Y (its first row times n)
+  int64_t slot;         // T slot of the chunk's tile (blk kt + t)
+  int kt_b, t, cnt, c0;  // tiles of the block, tile, its rows, chunk offset in the tile
+  __device__ void tile(const TqGeom& G, int kt) {
+    const int64_t tr0 = t == 0 ? 0 : G.B + static_cast<int64_t>(t - 1) * G.bt;
+    const int64_t left = rows_b - tr0;
+    cnt = static_cast<int>(t == 0 ? (rows_b < G.B ? rows_b : G.B) : (left < G.bt ? left : G.bt));
+    off = (blk * G.b + tr0 + c0) * G.n;
+    slot = blk * kt + t;
+  }
+  __device__ void block(const TqGeom& G) {
+    rows_b = G.rows_of(blk);
+    kt_b = static_cast<int>(TqGeom::tiles_of(rows_b, G.B, G.bt));
+  }
+  __device__ void set(const TqGeom& G, int kt, int64_t j) {
+    int64_t jj;
+    if (j < G.nfull) {
+      blk = j / G.cpb_full;
+      jj = j - blk * G.cpb_full;
+    } else {
+      blk = G.p - 1;
+      jj = j - G.nfull;
+    }
+    block(G);
+    const int64_t r0 = rows_b < G.B ? rows_b : G.B;
+    const int64_t ch0 = (r0 + kTcM - 1) / kTcM, chb = (G.bt + kTcM - 1) / kTcM;
+    if (jj < ch0) {
+      t = 0;
+      c0 = static_cast<int>(jj) * kTcM;
+    } else {
+      t = 1 + static_cast<int>((jj - ch0) / chb);
+      c0 = static_cast<int>((jj - ch0) % chb) * kTcM;
+    }
+    tile(G, kt);
+  }
+  __device__ void next(const TqGeom& G, int kt) {
+    c0 += kTcM;
+    off += static_cast<int64_t>(kTcM) * G.n;
+    if (c0 >= cnt) {
+      c0 = 0;
+      if (++t >= kt_b) {
+        t = 0;
+        if (++blk < G.p) block(G);
+      }
+      if (blk < G.p) tile(G, kt);
+    }
+  }
+  __device__ int crows() const { return cnt - c0 < kTcM ? cnt - c0 : kTcM; }
+  __device__ int ntop(int n) const { return (t == 0 && c0 == 0) ? static_cast<int>(rows_b < n ? rows_b : n) : 0; }
+};
+
+// What the copy warp tells the row groups and the MMA thread about the chunk
+// in a Y buffer.  The chunk's elements [0, crows n) outside its
+// 16-byte-aligned body are [0, nh) and [t0, crows n); its first element sits
+// at float hoff of the buffer.
+struct TqDesc {
+  int64_t off;   // element offset of the chunk in Y
+  int64_t slot;  // T slot of its tile
+  int64_t blk;   // its block
+  int hoff, nh, t0, crows, ntop, pad;
+};
+
+// 8 values of a staged row from column k0 (k0 + 8 <= n), VW-wide shared loads.
+template <int VW>
+__device__ __forceinline__ void tq_ld8(const float* p, float (&y)[8]) {
+  if constexpr (VW == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    y[0] = a.x; y[1] = a.y; y[2] = a.z; y[3] = a.w; y[4] = b.x; y[5] = b.y; y[6] = b.z; y[7] = b.w;
+  } else if constexpr (VW == 2) {
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) {
+      const float2 a = *reinterpret_cast<const float2*>(p + i);
+      y[i] = a.x;
+      y[i + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) y[i] = p[i];
+  }
+}
+template <int VW>
+__device__ __forceinline__ void tq_st8(float* p, const float (&x)[8]) {
+  if constexpr (VW == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    *reinterpret_cast<float4*>(p + 4) = make_float4(x[4], x[5], x[6], x[7]);
+  } else if constexpr (VW == 2) {
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) *reinterpret_cast<float2*>(p + i) = make_float2(x[i], x[i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) p[i] = x[i];
+  }
+}
+
+// The TF32 split of one thread's staged row `ys` (valid: rv) into tensor
+// memory: its half h of the 8-column pieces (at most four, K <= 64), A_hi at
+// column k0, A_lo at K + k0; columns n .. K-1 are zero.
+template <int VW>
+__device__ __forceinline__ void tq_split(const float* ys, bool rv, int n, int K, int h, uint32_t tl) {
+  float y[4][8];  // all pieces first, so the shared loads overlap
+#pragma unroll
+  for (int pc = 0; pc < 4; ++pc) {
+    const int k0 = 8 * (h + 2 * pc);
+    if (k0 < K) {
+      if (rv && k0 + 8 <= n) {
+        tq_ld8<VW>(ys + k0, y[pc]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) y[pc][i] = (rv && k0 + i < n) ? ys[k0 + i] : 0.0f;
       }
     }
   }
+#pragma unroll
+  for (int pc = 0; pc < 4; ++pc) {
+    const int k0 = 8 * (h + 2 * pc);
+    if (k0 < K) {
+      uint32_t hv[8], lv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float hf = tf32_round(y[pc][i]);
+        hv[i] = __float_as_uint(hf);
+        lv[i] = __float_as_uint(tf32_round(y[pc][i] - hf));
+      }
+      tc_st_x8(tl + static_cast<uint32_t>(k0), hv);
+      tc_st_x8(tl + static_cast<uint32_t>(K + k0), lv);
+    }
+  }
+}
+
+// Q of one thread's row, its half h of the 8-column pieces of the
+// accumulator (tensor-memory columns 2K ..), into its staging row yw.
+template <int VW>
+__device__ __forceinline__ void tq_epi(float* yw, bool rv, int n, int K, int h, uint32_t tl) {
+  uint32_t v[4][8];
+#pragma unroll
+  for (int pc = 0; pc < 4; ++pc) {
+    const int c0 = 8 * (h + 2 * pc);
+    if (c0 < n) tc_ld_x8(tl + static_cast<uint32_t>(2 * K + c0), v[pc]);
+  }
+  tc_wait_ld();
+  if (!rv) return;
+#pragma unroll
+  for (int pc = 0; pc < 4; ++pc) {
+    const int c0 = 8 * (h + 2 * pc);
+    if (c0 < n) {
+      float x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = __uint_as_float(v[pc][i]);
+      if (c0 + 8 <= n) {
+        tq_st8<VW>(yw + c0, x);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (c0 + i < n) yw[c0 + i] = x[i];
+      }
+    }
+  }
+}
+
+// Step 3, binary32 data, n <= kTcMaxN: Q = Y (-W_t) (+ X_0), the chunks of
+// all blocks streamed by a persistent grid (see the file comment).
+//   Yg : m x n (binary32), Y as written by k_local_qr; Q is written over it.
+//   Tg : the T slots after k_w_chain (-W_t as TF32 hi and lo parts).
+//   Cg : the blocks' C after k_w_chain (X_0 in binary32).
+// Warp roles:
+//   0-7, 8-15  the two row groups (warp w of a group: TMEM lanes 32 (w % 4)
+//              .., half w / 4 of the 8-column pieces): TF32 split of the
+//              staged rows into tensor memory, then Q from the accumulator;
+//   16         lane 0 issues the MMA chains;
+//   17         lane 0 issues the bulk copies in and out and describes each
+//              chunk in desc[s];
+//   18-19      build the B operands of the CTA's tiles in turn (two buffers,
+//              by the tile's ordinal in the CTA's run), by cp.async.
+// Hand-offs are mbarriers: full[s] (copy into Y buffer s landed, desc[s]
+// written), aready[g] (group g's A operands are in tensor memory), dfull[g]
+// (its MMA chain completed), qstaged[g] (its Q rows are staged for the copy
+// out), bready[x] / bfree[x] (B buffer x built / no longer read).  Chunk i of
+// a CTA's run goes to group i % 2 and Y buffer i % (2 nb).
+// Launch: gridDim <= the SM count, blockDim = kTqThreads, dynamic smem =
+// max(FormQTcSmem(n).total, kTqMinSmem).
+template <int VW>
+__global__ void __launch_bounds__(kTqThreads, 1)
+    k_form_q_tc(float* Yg, int64_t m, int n, int64_t b, int B, int bt, int kt, int64_t p,
+                const double* __restrict__ Tg, const double* __restrict__ Cg, int32_t* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const FormQTcSmem L(n);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = tc_k(n), N = tc_n(n), KQ = K / 4, nn = n * n, nbuf = 2 * L.nb;
+  const int GC = tq_gcols(n);
+  float* ybase = reinterpret_cast<float*>(smem + L.ybuf);
+  const int ystride = static_cast<int>(L.ybytes / 4);  // floats per Y buffer
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
+  uint64_t* aready = full + 6;
+  uint64_t* dfull = full + 8;
+  uint64_t* qstaged = full + 10;
+  uint64_t* bready = full + 12;
+  uint64_t* bfree = full + 14;
+  TqDesc* desc = reinterpret_cast<TqDesc*>(smem + L.desc);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
+  const uintptr_t yaddr = reinterpret_cast<uintptr_t>(Yg);  // VW: the widest row vector Y's alignment allows
+
+  const TqGeom G(m, n, b, B, bt, p);
+  const int64_t total = G.total();
+  const int64_t lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
+  const int nloc = static_cast<int>(hi - lo);  // chunks of this CTA (a few thousand at most)
+
+  if (tid == 0) {
+    for (int s = 0; s < nbuf; ++s) mbar_init(full + s, 1);
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(aready + g, kTqGroupWarps);
+      mbar_init(dfull + g, 1);
+      mbar_init(qstaged + g, kTqGroupWarps);
+      mbar_init(bready + g, 1);
+      mbar_init(bfree + g, 1);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 0) tc_alloc(tslot, static_cast<uint32_t>(2 * GC));
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-
-  // chunk (t, c0): rows [c0, c0 + 128) of tile t; tiles are taken last to
-  // first, so the sequence starts at tile ntiles - 1
-  auto tile_rows = [&](int t, int& tr0, int& cnt) {
-    tr0 = t == 0 ? 0 : B + (t - 1) * bt;
-    cnt = t == 0 ? (rows < B ? rows : B) : (rows - tr0 < bt ? rows - tr0 : bt);
-  };
-  // Issue (thread 0) the bulk copy of the 16-byte-aligned body of chunk
-  // (t, c0) into Y buffer s; the rest is read with plain loads on arrival.
-  auto issue = [&](int t, int c0, int s) {
-    int tr0, cnt;
-    tile_rows(t, tr0, cnt);
-    const int crows = cnt - c0 < kTcM ? cnt - c0 : kTcM;
-    const float* src = Yg + (row0 + tr0 + c0) * n;
-    const uint32_t bytes = static_cast<uint32_t>(crows) * n * 4;
-    const uint32_t body = (reinterpret_cast<uintptr_t>(src) & 15) == 0 ? (bytes & ~15u) : 0u;
-    if (tid == 0 && body > 0) {
-      mbar_arrive_expect_tx(lbar + s, body);
-      for (uint32_t off = 0; off < body; off += kBulkChunk) {
-        const uint32_t len = body - off < kBulkChunk ? body - off : kBulkChunk;
-        bulk_g2s(reinterpret_cast<char*>(ybuf[s]) + off, reinterpret_cast<const char*>(src) + off, len, lbar + s);
-      }
-    }
-    return body;
-  };
-
-  uint32_t parity = 0, lph[2] = {0u, 0u};
-  bool pend[2] = {false, false};  // a bulk copy into the buffer has not been waited for
   bool ok = true;
-  int t = ntiles - 1, c0 = 0, cur_tile = -1;
-  uint32_t body_cur = issue(t, c0, 0), body_next = 0;
-  pend[0] = body_cur > 0;
-  for (int ci = 0;; ++ci) {
-    const int s = ci & 1;
-    int tr0, cnt;
-    tile_rows(t, tr0, cnt);
-    const int crows = cnt - c0 < kTcM ? cnt - c0 : kTcM;
-    float* yq = Yg + (row0 + tr0 + c0) * n;  // first row of the chunk (Y in, Q out)
-    const bool top = (t == 0);
-    if (t != cur_tile) {
-      // ---- prologue of tile t: W, and the B operands
-      cur_tile = t;
-      const double* Tb = Tg + (static_cast<int64_t>(blockIdx.x) * kt + t) * nn;
-      const float* src = xm;
-      float w[kTcMaxE];
-      if (t == 0) {
-        // Z = Y_top^T X (Y_top unit lower triangular, rows < ntop of the block)
-        for (int idx = tid; idx < ntop * n; idx += kTcThreads) stage[idx] = Yg[row0 * n + idx];
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < kTcMaxE; ++e) {
-          const int kk = ekk[e], c = ec[e];
-          float acc = 0.0f;
-          if (kk < ntop) {
-            acc = xm[kk * n + c];
-            for (int r = kk + 1; r < ntop; ++r) acc = fmaf(stage[r * n + kk], xm[r * n + c], acc);
-          }
-          w[e] = acc;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < kTcMaxE; ++e)
-          if (ekk[e] < n) wm[ekk[e] * n + ec[e]] = w[e];
-        __syncthreads();
-        src = wm;
-      }
-      // W = T src (T upper triangular, binary64 slot rounded to binary32)
-      for (int i = warp; i < n; i += kTcThreads / 32)
-        for (int col = lane; col < n; col += 32)
-          stage[i * n + col] = col >= i ? static_cast<float>(Tb[i * n + col]) : 0.0f;
-      __syncthreads();
-#pragma unroll
-      for (int e = 0; e < kTcMaxE; ++e) {
-        const int kk = ekk[e], c = ec[e];
-        float acc = 0.0f;
-        if (kk < n)
-          for (int i = kk; i < n; ++i) acc = fmaf(stage[kk * n + i], src[i * n + c], acc);
-        w[e] = acc;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int e = 0; e < kTcMaxE; ++e) {
-        if (ekk[e] < n) {
-          const int idx = ekk[e] * n + ec[e];
-          wm[idx] = w[e];
-          if (t > 0) xm[idx] -= w[e];  // coefficient of tile t-1
-        }
-      }
-      __syncthreads();
-      // B operands: element (c, k) of B^T = W[k][c], split into TF32 hi + lo;
-      // warp iteration `it` fills core matrix it (8 rows x 4 values) lane by lane
-      for (int gc = warp; gc < N / 8; gc += kTcThreads / 32)
-        for (int kq = 0; kq < KQ; ++kq) {
-          const int it = gc * KQ + kq;
-          const int c = gc * 8 + (lane >> 2), k = kq * 4 + (lane & 3);
-          const float x = (c < n && k < n) ? wm[k * n + c] : 0.0f;
-          const float h = tf32_round(x);
-          b_hi[it * 32 + lane] = h;
-          b_lo[it * 32 + lane] = tf32_round(x - h);
-        }
 
-    }
-    // ---- prefetch the next chunk into the other buffer (its last readers
-    //      finished before the barrier that ended the previous chunk)
-    int nt = t, nc0 = c0 + kTcM;
-    if (nc0 >= cnt) {
-      nt = t - 1;
-      nc0 = 0;
-    }
-    body_next = nt >= 0 ? issue(nt, nc0, s ^ 1) : 0u;
-    pend[s ^ 1] = body_next > 0;
-    // ---- this chunk's Y: bulk body, then the plain-load remainder
-    if (body_cur > 0) {
-      ok = mbar_wait_bounded(lbar + s, lph[s]);
-      if (ok) {
-        lph[s] ^= 1u;
-        pend[s] = false;
+  if (warp < 2 * kTqGroupWarps) {
+    // ================= a row group =================
+    const int g = warp / kTqGroupWarps, gw = warp % kTqGroupWarps, q = gw & 3, h = gw >> 2;
+    const int gt = tid % kTqGroupThreads;  // thread within the group
+    const int r = 32 * q + lane;  // my row of the chunk (tensor-memory lane)
+    const uint32_t tl = tmem + static_cast<uint32_t>(g * GC) + (static_cast<uint32_t>(32 * q) << 16);
+    const int e0 = r * n;  // my row's first element in a chunk
+    uint32_t fpar = 0, ph = 0;  // Y buffer parities (bit per buffer); the group's barrier parity
+    int s = g;
+    for (int i = g; i < nloc; i += 2) {
+      float* yb = ybase + s * ystride;
+      // group-uniform outcomes of the bounded waits (the group meets at named
+      // barriers below, so no warp may leave alone)
+      if (!named_bar_and(2 + g, kTqGroupThreads, mbar_wait_bounded(full + s, (fpar >> s) & 1u))) {
+        ok = false;
+        break;
       }
-    }
-    for (int e = static_cast<int>(body_cur / 4) + tid; e < crows * n; e += kTcThreads) ybuf[s][e] = yq[e];
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
-    if (!ok) {
-      if (tid == 0) set_status(status, TSQR_ERR_TIMEOUT);
-      break;
-    }
-    // ---- A operands from the staged rows, split into TF32: warp iteration
-    //      `it` fills core matrix it (rows 8 (it / KQ) .., values 4 (it % KQ) ..)
-    //      with one value per lane
-    {
-      const float* ys = ybuf[s];
-      for (int gr = warp; gr < kTcM / 8; gr += kTcThreads / 32) {
-        const int r = gr * 8 + (lane >> 2);
-        const float* yr = ys + r * n + (lane & 3);
-        for (int kq = 0; kq < KQ; ++kq) {
-          const int it = gr * KQ + kq, k = kq * 4 + (lane & 3);
-          float y = 0.0f;
-          if (r < crows && k < n) {
-            y = yr[kq * 4];
-            if (top && c0 + r < n && k >= c0 + r) y = (k == c0 + r) ? 1.0f : 0.0f;  // unit lower Y_top
-          }
-          const float h = tf32_round(y);
-          a_hi[it * 32 + lane] = h;
-          a_lo[it * 32 + lane] = tf32_round(y - h);
+      fpar ^= 1u << s;
+      const TqDesc& dc = desc[s];
+      const int hoff = dc.hoff, nh = dc.nh, t0 = dc.t0, ntop = dc.ntop, ne = dc.crows * n;
+      float* ys = yb + hoff;  // the chunk's staged elements
+      const bool rv = r < dc.crows;
+      // chunks with unaligned edges or the block's first rows are patched in
+      // the staging buffer first (few: a block's first chunk, tile ends)
+      const bool plain = ntop == 0 && nh == 0 && t0 == ne;
+      if (!plain) {
+        const float* yc = Yg + dc.off;
+        for (int e = gt; e < nh; e += kTqGroupThreads) ys[e] = yc[e];
+        for (int e = t0 + gt; e < ne; e += kTqGroupThreads) ys[e] = yc[e];
+        // Y_top is unit lower triangular: its upper part is not Y's
+        for (int e = gt; e < ntop * n; e += kTqGroupThreads) {
+          const int rr = e / n, k = e - rr * n;
+          if (k >= rr) ys[e] = k == rr ? 1.0f : 0.0f;
         }
+        named_bar_sync(2 + g, kTqGroupThreads);
       }
-    }
-    fence_proxy_async_smem();  // generic writes of A (and B) -> tensor-core reads
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) {
-      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-      for (int kb = 0; kb < K / 8; ++kb) {
-        const uint32_t ko = static_cast<uint32_t>(kb) * 256;
-        const uint64_t dah = tc_smem_desc(ah + ko, lbo, sbo), dal = tc_smem_desc(al + ko, lbo, sbo);
-        const uint64_t dbh = tc_smem_desc(bh + ko, lbo, sbo), dbl = tc_smem_desc(bl + ko, lbo, sbo);
-        tc_mma_tf32(tmem, dah, dbh, idesc, kb > 0);
-        tc_mma_tf32(tmem, dah, dbl, idesc, 1);
-        tc_mma_tf32(tmem, dal, dbh, idesc, 1);
+      tq_split<VW>(ys + e0, rv, n, K, h, tl);
+      tc_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(aready + g);
+      // ---- Q rows from the accumulator into the staging rows
+      if (!named_bar_and(2 + g, kTqGroupThreads, mbar_wait_bounded(dfull + g, ph))) {
+        ok = false;
+        break;
       }
-      tc_commit(bar);
+      ph ^= 1u;
+      tc_fence_after();
+      tq_epi<VW>(ys + e0, rv, n, K, h, tl);
+      if (!plain) {
+        named_bar_sync(2 + g, kTqGroupThreads);
+        const float* x0 = reinterpret_cast<const float*>(Cg + dc.blk * nn);
+        for (int e = gt; e < ntop * n; e += kTqGroupThreads) ys[e] += x0[e];  // Q = [X_0; 0] - Y W
+        named_bar_sync(2 + g, kTqGroupThreads);
+        float* qc = Yg + dc.off;  // the edges go to Y directly (the copy out takes the body)
+        for (int e = gt; e < nh; e += kTqGroupThreads) qc[e] = ys[e];
+        for (int e = t0 + gt; e < ne; e += kTqGroupThreads) qc[e] = ys[e];
+      }
+      fence_proxy_async_smem();  // staging rows -> the bulk copy out
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(qstaged + g);
+      s += 2;
+      if (s >= nbuf) s -= nbuf;
     }
-    ok = __syncthreads_and(mbar_wait_bounded(bar, parity) ? 1 : 0) != 0;  // uniform over the CTA
-    parity ^= 1u;
-    tc_fence_after();
-    if (!ok) {
-      if (tid == 0) set_status(status, TSQR_ERR_TIMEOUT);
-      break;
-    }
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows of the chunk)
-    //      and the h = w / 4 th group of cw columns (cw a multiple of 8: some
-    //      groups are empty for small N); Q rows into the chunk's Y buffer at
-    //      stride n + 1
-    {
-      float* qs = ybuf[s];
-      const int q = warp & 3, h = warp >> 2;
-      const int cw = ((N / 4 + 7) / 8) * 8;
-      const int cend = (h + 1) * cw < N ? (h + 1) * cw : N;
-      const int r = 32 * q + lane;
-      const int rt = c0 + r;  // row within the tile
-      for (int col0 = h * cw; col0 < cend; col0 += 8) {
-        uint32_t v[8];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-            : "r"(tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(col0)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int col = col0 + i;
-          if (col < n && r < crows) {
-            float x = -__uint_as_float(v[i]);
-            if (top && rt < ntop) x += xm[rt * n + col];
-            qs[r * (n + 1) + col] = x;
+  } else if (warp == 2 * kTqGroupWarps) {
+    // ================= the MMA thread =================
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc_tf32(kTcM, N);
+      const uint32_t lbo = 128, sbo = static_cast<uint32_t>(KQ) * 128;
+      const uint32_t b0 = smem_u32(smem + L.bop);
+      int64_t cur = -1;
+      int tk = -1;  // ordinal of the current tile in this CTA's run
+      int s = 0;
+      for (int i = 0; i < nloc; ++i) {
+        const int g = i & 1;
+        if (!mbar_wait_bounded(aready + g, static_cast<uint32_t>(i >> 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        const int64_t slot = desc[s].slot;  // written before full[s], which group g waited on
+        if (slot != cur) {
+          if (tk >= 0) tc_commit(bfree + (tk & 1));  // B buffer of the tile before: free once its chains complete
+          ++tk;
+          cur = slot;
+          if (!mbar_wait_bounded(bready + (tk & 1), static_cast<uint32_t>(tk >> 1) & 1u)) {
+            ok = false;
+            break;
           }
         }
+        tc_fence_after();
+        const uint32_t ta = tmem + static_cast<uint32_t>(g * GC);
+        const uint32_t d = ta + static_cast<uint32_t>(2 * K);
+        const uint32_t bb = b0 + static_cast<uint32_t>(tk & 1) * static_cast<uint32_t>(L.bbytes);
+        const uint64_t dbh = tc_smem_desc(bb, lbo, sbo);
+        const uint64_t dbl = tc_smem_desc(bb + static_cast<uint32_t>(N * K * 4), lbo, sbo);
+        for (int kb = 0; kb < K / 8; ++kb) {
+          const uint64_t ko = static_cast<uint64_t>(kb) * 16;  // 256 bytes >> 4
+          const uint32_t ah = ta + static_cast<uint32_t>(kb * 8), al = ah + static_cast<uint32_t>(K);
+          tc_mma_tf32_ta(d, ah, dbh + ko, idesc, kb > 0);
+          tc_mma_tf32_ta(d, ah, dbl + ko, idesc, 1);
+          tc_mma_tf32_ta(d, al, dbh + ko, idesc, 1);
+        }
+        tc_commit(dfull + g);
+        if (++s == nbuf) s = 0;
       }
     }
-    tc_fence_before();
-    __syncthreads();
-    {
-      const float* qs = ybuf[s];
-      for (int r = warp; r < crows; r += kTcThreads / 32)
-        for (int col = lane; col < n; col += 32) yq[r * n + col] = qs[r * (n + 1) + col];
+  } else if (warp == 2 * kTqGroupWarps + 1) {
+    // ================= the copy thread =================
+    if (lane == 0) {
+      // describe chunk c (cursor cl) in desc[s] and start its copy in; then
+      // copies out in chunk order, each freeing the buffer of the chunk
+      // before it for the next copy in
+      auto issue = [&](const TqCursor& cl, int s) {
+        TqDesc& dd = desc[s];
+        const int crows = cl.crows();
+        const uintptr_t a = yaddr + static_cast<uintptr_t>(cl.off) * 4;
+        const uintptr_t e = a + static_cast<uintptr_t>(crows) * n * 4;
+        uintptr_t bs = (a + 15) & ~static_cast<uintptr_t>(15), be = e & ~static_cast<uintptr_t>(15);
+        if (be <= bs) be = bs;  // no aligned body
+        dd.off = cl.off;
+        dd.slot = cl.slot;
+        dd.blk = cl.blk;
+        dd.hoff = static_cast<int>((a & 15) / 4);
+        dd.nh = be > bs ? static_cast<int>((bs - a) / 4) : crows * n;
+        dd.t0 = be > bs ? static_cast<int>((be - a) / 4) : crows * n;
+        dd.crows = crows;
+        dd.ntop = cl.ntop(n);
+        const uint32_t body = static_cast<uint32_t>(be - bs);
+        mbar_arrive_expect_tx(full + s, body);  // releases desc[s]; body 0: the phase completes now
+        char* dst = reinterpret_cast<char*>(ybase + s * ystride) + (bs - (a & ~static_cast<uintptr_t>(15)));
+        for (uint32_t o = 0; o < body; o += kBulkChunk) {
+          const uint32_t len = body - o < kBulkChunk ? body - o : kBulkChunk;
+          bulk_g2s(dst + o, reinterpret_cast<const char*>(bs) + o, len, full + s);
+        }
+      };
+      uint32_t pend = 0, fpar = 0;  // copies in not yet consumed (bit per buffer); their phase parities
+      TqCursor cl;
+      if (nloc > 0) cl.set(G, kt, lo);
+      int nload = 0, sl = 0;
+      for (; nload < nloc && nload < nbuf; ++nload) {
+        issue(cl, sl);
+        pend |= 1u << sl;
+        cl.next(G, kt);
+        if (++sl == nbuf) sl = 0;
+      }
+      int ss = 0;  // buffer of chunk i
+      for (int i = 0; i < nloc; ++i) {
+        if (!mbar_wait_bounded(qstaged + (i & 1), static_cast<uint32_t>(i >> 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        // chunk i was consumed (its group staged Q): its copy in completed
+        pend &= ~(1u << ss);
+        fpar ^= 1u << ss;
+        {
+          const TqDesc& dd = desc[ss];
+          const uintptr_t a = yaddr + static_cast<uintptr_t>(dd.off) * 4;
+          const uintptr_t bs = a + static_cast<uintptr_t>(dd.nh) * 4, be = a + static_cast<uintptr_t>(dd.t0) * 4;
+          const char* sp =
+              reinterpret_cast<const char*>(ybase + ss * ystride) + (bs - (a & ~static_cast<uintptr_t>(15)));
+          for (uintptr_t o = 0; o < be - bs; o += kBulkChunk) {
+            const uint32_t len = static_cast<uint32_t>(be - bs - o < kBulkChunk ? be - bs - o : kBulkChunk);
+            bulk_s2g(reinterpret_cast<char*>(bs) + o, sp + o, len);
+          }
+          bulk_commit();  // one group per chunk (possibly empty)
+        }
+        if (i >= 1 && nload < nloc) {
+          bulk_wait_read_1();  // chunk i - 1's copy out has read its buffer (sl)
+          issue(cl, sl);
+          pend |= 1u << sl;
+          cl.next(G, kt);
+          ++nload;
+          if (++sl == nbuf) sl = 0;
+        }
+        if (++ss == nbuf) ss = 0;
+      }
+      // copies in flight after an error: wait for them (bounded) before the
+      // shared memory is released; the copies out complete in any case
+      for (int s = 0; s < nbuf; ++s)
+        if (pend & (1u << s)) mbar_wait_bounded(full + s, (fpar >> s) & 1u);
+      bulk_wait_all();
     }
-    fence_proxy_async_smem();  // generic reads of this buffer before its next bulk copy
-    __syncthreads();
-    if (nt < 0) break;
-    t = nt;
-    c0 = nc0;
-    body_cur = body_next;
+  } else {
+    // ================= the B builders =================
+    // element x of a part (hi or lo) in the core layout: core row it = x / 32,
+    // c = (it / KQ) 8 + (x % 32) / 4, k = (it % KQ) 4 + x % 4; builder thread
+    // bt takes x = bt + 32 kTqBuildWarps e (so x % 32 is its lane)
+    const int btid = tid - (2 * kTqGroupWarps + 2) * 32;
+    float* bufs = reinterpret_cast<float*>(smem + L.bop);
+    TqCursor ct;  // the CTA's tiles in order: the first chunk's, then one tile on each time
+    if (nloc > 0) ct.set(G, kt, lo);
+    int64_t last_slot = -1;
+    {
+      TqCursor ce;  // the tile of the CTA's last chunk
+      if (nloc > 0) {
+        ce.set(G, kt, hi - 1);
+        last_slot = ce.slot;
+      }
+    }
+    const int nx = N * K;
+    for (int tk = 0; nloc > 0; ++tk) {
+      const int x = tk & 1;
+      if (!named_bar_and(1, 32 * kTqBuildWarps,
+                         tk < 2 || mbar_wait_bounded(bfree + x, static_cast<uint32_t>((tk - 2) >> 1) & 1u))) {
+        ok = false;  // the builders leave together
+        break;
+      }
+      float* bh = bufs + static_cast<size_t>(x) * (L.bbytes / 4);
+      float* bl = bh + nx;
+      const float* Ws = reinterpret_cast<const float*>(Tg + ct.slot * nn);
+      int it = btid >> 5, gc = it / KQ, kq = it % KQ;
+      const int cl = lane >> 2, kl = lane & 3;
+      for (int xx = btid; xx < nx; xx += 32 * kTqBuildWarps) {
+        const int c = gc * 8 + cl, k = kq * 4 + kl;
+        if (c < n && k < n) {
+          cp_async_4(bh + xx, Ws + k * n + c);
+          cp_async_4(bl + xx, Ws + nn + k * n + c);
+        } else {
+          bh[xx] = 0.0f;
+          bl[xx] = 0.0f;
+        }
+        kq += kTqBuildWarps;  // <= KQ (K >= 8)
+        if (kq >= KQ) {
+          kq -= KQ;
+          ++gc;
+        }
+      }
+      cp_async_wait_all();
+      fence_proxy_async_smem();  // generic and cp.async writes -> tensor-core reads
+      named_bar_sync(1, 32 * kTqBuildWarps);
+      if (btid == 0) mbar_arrive(bready + x);
+      if (ct.slot == last_slot) break;
+      // one tile on
+      ct.c0 = ct.cnt;  // skip to the tile's end, so next() starts the next tile
+      ct.off = 0;
+      ct.next(G, kt);
+    }
   }
-  // copies still in flight after an error: wait for them (bounded) before
-  // the shared memory is released
-  for (int s = 0; s < 2; ++s)
-    if (!ok && pend[s]) mbar_wait_bounded(lbar + s, lph[s]);
+  if (!ok) set_status(status, TSQR_ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NC) : "memory");
+  if (warp == 0) tc_dealloc(tmem, static_cast<uint32_t>(2 * GC));
 }
-
 
 // Step 3, binary32 data, tensor-core product, 64 < n <= kTcwMaxN.
 //   Yg : m x n (binary32), Y as written by k_local_qr; Q is written over it.

@@ -1,7 +1,8 @@
 // tcgen05.cuh -- inline-PTX helpers of the 5th-generation tensor cores
 // (sm_103a): shared-memory matrix descriptors, instruction descriptors,
-// tcgen05.mma issue and commit, the tcgen05 thread-sync fences, and the
-// 32-lane x 32-bit tensor-memory loads.  Device code only.
+// tcgen05.mma issue (A in shared or tensor memory) and commit, the tcgen05
+// thread-sync fences, and the 32-lane x 32-bit tensor-memory loads and
+// stores.  Device code only.
 #pragma once
 
 #include <cstdint>
@@ -33,6 +34,16 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t a, uint64_
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// The same with A in tensor memory: lane r holds row r of A, K consecutive
+// 32-bit columns from `a_tmem` (one TF32 value each).
+__device__ __forceinline__ void tc_mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                               int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
@@ -67,6 +78,16 @@ __device__ __forceinline__ void tc_ld_x8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 8 consecutive 32-bit columns into this warp's 32 lanes (one row per lane),
+// completed by tc_wait_st.  It touches tensor memory only, so it carries no
+// memory clobber: shared and global accesses may move across it (ordering
+// against the tensor-core reads comes from tc_wait_st and the fences).
+__device__ __forceinline__ void tc_st_x8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_alloc(uint32_t* slot_smem, uint32_t cols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot_smem)),
