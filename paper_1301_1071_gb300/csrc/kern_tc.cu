@@ -24,7 +24,10 @@ cudaError_t launch_form_q_tc(float* Y, int64_t m, int n, int64_t b, int B, int64
     // rows are read and written with the widest vector Y's alignment allows
     const uintptr_t ya = reinterpret_cast<uintptr_t>(Y);
     const int vw = (n % 4 == 0 && (ya & 15) == 0) ? 4 : ((n % 2 == 0 && (ya & 7) == 0) ? 2 : 1);
-    auto kern = vw == 4 ? k_form_q_tc<4> : (vw == 2 ? k_form_q_tc<2> : k_form_q_tc<1>);
+    // n % 8 == 0: rows at stride n would start on the same banks; they are
+    // staged in 16-row groups 16 bytes apart instead (rows 16-byte aligned)
+    auto kern = vw == 4 ? (n % 8 == 0 ? k_form_q_tc<4, true> : k_form_q_tc<4, false>)
+                        : (vw == 2 ? k_form_q_tc<2, false> : k_form_q_tc<1, false>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;

@@ -62,22 +62,23 @@ TSQR_HD constexpr int tq_gcols(int n) {
 }
 
 // Shared memory of k_form_q_tc: 2 nb Y buffers (a chunk as one contiguous
-// copy, row stride n, after a head offset below 16 bytes), the B operands of
+// copy, row stride n, after a head offset below 16 bytes; for n % 8 == 0 as
+// 16-row groups 16 bytes apart, see tq_sidx), the B operands of
 // two tiles (by ordinal parity), the mbarriers (full[6], aready[2], dfull[2],
-// qstaged[2], bready[2], bfree[2]) and the chunk descriptors (one per Y
+// qstaged[6], bready[2], bfree[2]) and the chunk descriptors (one per Y
 // buffer, 48 bytes each).
 struct FormQTcSmem {
   size_t ybuf, ybytes, bop, bbytes, bars, desc, tslot, total;
   int nb;  // Y buffers per group (3 where they fit, else 2)
   TSQR_HD FormQTcSmem(int n) {
     const size_t K = tc_k(n), N = tc_n(n);
-    ybytes = align_up((size_t)kTcM * n * 4 + 16, 128);
+    ybytes = align_up((size_t)kTcM * n * 4 + 128, 128);  // + a head offset or the 16-row groups' stagger
     bbytes = 2 * N * K * 4;  // hi, then lo
     nb = 6 * ybytes + 2 * bbytes + 1536 <= 232448 ? 3 : 2;
     size_t o = 0;
     ybuf = o; o += 2 * (size_t)nb * ybytes;
     bop = o; o = align_up(o + 2 * bbytes, 128);
-    bars = o; o += 16 * 8;
+    bars = o; o += 20 * 8;
     desc = o; o += 6 * 48;
     tslot = o; o = align_up(o + 8, 16);
     total = o;
@@ -354,6 +355,14 @@ struct TqDesc {
   int hoff, nh, t0, crows, ntop, pad;
 };
 
+// Float offset of row r of a staged chunk: row-major at stride n, or (STAG,
+// n % 8 == 0) in 16-row groups each 16 bytes further on, so that rows
+// 16 apart start 4 banks apart.
+template <bool STAG>
+__device__ __forceinline__ int tq_sidx(int r, int n) {
+  return STAG ? (r >> 4) * (16 * n + 4) + (r & 15) * n : r * n;
+}
+
 // 8 values of a staged row from column k0 (k0 + 8 <= n), VW-wide shared loads.
 template <int VW>
 __device__ __forceinline__ void tq_ld8(const float* p, float (&y)[8]) {
@@ -467,12 +476,17 @@ __device__ __forceinline__ void tq_epi(float* yw, bool rv, int n, int K, int h, 
 //              by the tile's ordinal in the CTA's run), by cp.async.
 // Hand-offs are mbarriers: full[s] (copy into Y buffer s landed, desc[s]
 // written), aready[g] (group g's A operands are in tensor memory), dfull[g]
-// (its MMA chain completed), qstaged[g] (its Q rows are staged for the copy
-// out), bready[x] / bfree[x] (B buffer x built / no longer read).  Chunk i of
-// a CTA's run goes to group i % 2 and Y buffer i % (2 nb).
+// (its MMA chain completed), qstaged[s] (the Q rows in Y buffer s are staged
+// for the copy out), bready[x] / bfree[x] (B buffer x built / no longer
+// read).  Chunk i of a CTA's run goes to group i % 2 and Y buffer i % (2 nb).
+// No waiter may fall two phases behind a barrier (the parity would alias):
+// every barrier's next phase needs a step its waiter takes after observing
+// the current one -- which is why qstaged is per buffer (a group reaches its
+// next use of buffer s only after the copy out of s, which follows the wait),
+// not per group (a group can stage two chunks before the copy thread looks).
 // Launch: gridDim <= the SM count, blockDim = kTqThreads, dynamic smem =
 // max(FormQTcSmem(n).total, kTqMinSmem).
-template <int VW>
+template <int VW, bool STAG>
 __global__ void __launch_bounds__(kTqThreads, 1)
     k_form_q_tc(float* Yg, int64_t m, int n, int64_t b, int B, int bt, int kt, int64_t p,
                 const double* __restrict__ Tg, const double* __restrict__ Cg, int32_t* status) {
@@ -486,9 +500,9 @@ __global__ void __launch_bounds__(kTqThreads, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.bars);
   uint64_t* aready = full + 6;
   uint64_t* dfull = full + 8;
-  uint64_t* qstaged = full + 10;
-  uint64_t* bready = full + 12;
-  uint64_t* bfree = full + 14;
+  uint64_t* qstaged = full + 10;  // one per Y buffer (see below)
+  uint64_t* bready = full + 16;
+  uint64_t* bfree = full + 18;
   TqDesc* desc = reinterpret_cast<TqDesc*>(smem + L.desc);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
   const uintptr_t yaddr = reinterpret_cast<uintptr_t>(Yg);  // VW: the widest row vector Y's alignment allows
@@ -499,11 +513,13 @@ __global__ void __launch_bounds__(kTqThreads, 1)
   const int nloc = static_cast<int>(hi - lo);  // chunks of this CTA (a few thousand at most)
 
   if (tid == 0) {
-    for (int s = 0; s < nbuf; ++s) mbar_init(full + s, 1);
+    for (int s = 0; s < nbuf; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(qstaged + s, kTqGroupWarps);
+    }
     for (int g = 0; g < 2; ++g) {
       mbar_init(aready + g, kTqGroupWarps);
       mbar_init(dfull + g, 1);
-      mbar_init(qstaged + g, kTqGroupWarps);
       mbar_init(bready + g, 1);
       mbar_init(bfree + g, 1);
     }
@@ -520,9 +536,13 @@ __global__ void __launch_bounds__(kTqThreads, 1)
     // ================= a row group =================
     const int g = warp / kTqGroupWarps, gw = warp % kTqGroupWarps, q = gw & 3, h = gw >> 2;
     const int gt = tid % kTqGroupThreads;  // thread within the group
-    const int r = 32 * q + lane;  // my row of the chunk (tensor-memory lane)
+    // my row of the chunk: tensor-memory lane L = 32 q + lane holds row L, or
+    // with the staggered staging row 16 (L % 8) + L / 8, so that a quarter
+    // warp's eight rows lie in eight different 16-row groups
+    const int L = 32 * q + lane;
+    const int r = STAG ? 16 * (L & 7) + (L >> 3) : L;
     const uint32_t tl = tmem + static_cast<uint32_t>(g * GC) + (static_cast<uint32_t>(32 * q) << 16);
-    const int e0 = r * n;  // my row's first element in a chunk
+    const int e0 = tq_sidx<STAG>(r, n);  // my row's first element in the staging buffer
     uint32_t fpar = 0, ph = 0;  // Y buffer parities (bit per buffer); the group's barrier parity
     int s = g;
     for (int i = g; i < nloc; i += 2) {
@@ -548,7 +568,7 @@ __global__ void __launch_bounds__(kTqThreads, 1)
         // Y_top is unit lower triangular: its upper part is not Y's
         for (int e = gt; e < ntop * n; e += kTqGroupThreads) {
           const int rr = e / n, k = e - rr * n;
-          if (k >= rr) ys[e] = k == rr ? 1.0f : 0.0f;
+          if (k >= rr) ys[tq_sidx<STAG>(rr, n) + k] = k == rr ? 1.0f : 0.0f;
         }
         named_bar_sync(2 + g, kTqGroupThreads);
       }
@@ -568,7 +588,10 @@ __global__ void __launch_bounds__(kTqThreads, 1)
       if (!plain) {
         named_bar_sync(2 + g, kTqGroupThreads);
         const float* x0 = reinterpret_cast<const float*>(Cg + dc.blk * nn);
-        for (int e = gt; e < ntop * n; e += kTqGroupThreads) ys[e] += x0[e];  // Q = [X_0; 0] - Y W
+        for (int e = gt; e < ntop * n; e += kTqGroupThreads) {  // Q = [X_0; 0] - Y W
+          const int rr = e / n;
+          ys[tq_sidx<STAG>(rr, n) + e - rr * n] += x0[e];
+        }
         named_bar_sync(2 + g, kTqGroupThreads);
         float* qc = Yg + dc.off;  // the edges go to Y directly (the copy out takes the body)
         for (int e = gt; e < nh; e += kTqGroupThreads) qc[e] = ys[e];
@@ -577,7 +600,7 @@ __global__ void __launch_bounds__(kTqThreads, 1)
       fence_proxy_async_smem();  // staging rows -> the bulk copy out
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(qstaged + g);
+      if (lane == 0) mbar_arrive(qstaged + s);
       s += 2;
       if (s >= nbuf) s -= nbuf;
     }
@@ -646,10 +669,19 @@ __global__ void __launch_bounds__(kTqThreads, 1)
         dd.ntop = cl.ntop(n);
         const uint32_t body = static_cast<uint32_t>(be - bs);
         mbar_arrive_expect_tx(full + s, body);  // releases desc[s]; body 0: the phase completes now
-        char* dst = reinterpret_cast<char*>(ybase + s * ystride) + (bs - (a & ~static_cast<uintptr_t>(15)));
-        for (uint32_t o = 0; o < body; o += kBulkChunk) {
-          const uint32_t len = body - o < kBulkChunk ? body - o : kBulkChunk;
-          bulk_g2s(dst + o, reinterpret_cast<const char*>(bs) + o, len, full + s);
+        if constexpr (STAG) {  // rows 16-byte aligned (no edges): one copy per 16-row group
+          float* dst = ybase + s * ystride;
+          for (int r0 = 0; r0 < crows; r0 += 16) {
+            const int nr = crows - r0 < 16 ? crows - r0 : 16;
+            bulk_g2s(dst + tq_sidx<true>(r0, n), Yg + cl.off + static_cast<int64_t>(r0) * n,
+                     static_cast<uint32_t>(nr) * n * 4, full + s);
+          }
+        } else {
+          char* dst = reinterpret_cast<char*>(ybase + s * ystride) + (bs - (a & ~static_cast<uintptr_t>(15)));
+          for (uint32_t o = 0; o < body; o += kBulkChunk) {
+            const uint32_t len = body - o < kBulkChunk ? body - o : kBulkChunk;
+            bulk_g2s(dst + o, reinterpret_cast<const char*>(bs) + o, len, full + s);
+          }
         }
       };
       uint32_t pend = 0, fpar = 0;  // copies in not yet consumed (bit per buffer); their phase parities
@@ -662,24 +694,35 @@ __global__ void __launch_bounds__(kTqThreads, 1)
         cl.next(G, kt);
         if (++sl == nbuf) sl = 0;
       }
-      int ss = 0;  // buffer of chunk i
+      int ss = 0;        // buffer of chunk i
+      uint32_t qpar = 0;  // qstaged parities, bit per buffer
       for (int i = 0; i < nloc; ++i) {
-        if (!mbar_wait_bounded(qstaged + (i & 1), static_cast<uint32_t>(i >> 1) & 1u)) {
+        if (!mbar_wait_bounded(qstaged + ss, (qpar >> ss) & 1u)) {
           ok = false;
           break;
         }
+        qpar ^= 1u << ss;
         // chunk i was consumed (its group staged Q): its copy in completed
         pend &= ~(1u << ss);
         fpar ^= 1u << ss;
         {
           const TqDesc& dd = desc[ss];
-          const uintptr_t a = yaddr + static_cast<uintptr_t>(dd.off) * 4;
-          const uintptr_t bs = a + static_cast<uintptr_t>(dd.nh) * 4, be = a + static_cast<uintptr_t>(dd.t0) * 4;
-          const char* sp =
-              reinterpret_cast<const char*>(ybase + ss * ystride) + (bs - (a & ~static_cast<uintptr_t>(15)));
-          for (uintptr_t o = 0; o < be - bs; o += kBulkChunk) {
-            const uint32_t len = static_cast<uint32_t>(be - bs - o < kBulkChunk ? be - bs - o : kBulkChunk);
-            bulk_s2g(reinterpret_cast<char*>(bs) + o, sp + o, len);
+          if constexpr (STAG) {
+            const float* sp = ybase + ss * ystride;
+            for (int r0 = 0; r0 < dd.crows; r0 += 16) {
+              const int nr = dd.crows - r0 < 16 ? dd.crows - r0 : 16;
+              bulk_s2g(Yg + dd.off + static_cast<int64_t>(r0) * n, sp + tq_sidx<true>(r0, n),
+                       static_cast<uint32_t>(nr) * n * 4);
+            }
+          } else {
+            const uintptr_t a = yaddr + static_cast<uintptr_t>(dd.off) * 4;
+            const uintptr_t bs = a + static_cast<uintptr_t>(dd.nh) * 4, be = a + static_cast<uintptr_t>(dd.t0) * 4;
+            const char* sp =
+                reinterpret_cast<const char*>(ybase + ss * ystride) + (bs - (a & ~static_cast<uintptr_t>(15)));
+            for (uintptr_t o = 0; o < be - bs; o += kBulkChunk) {
+              const uint32_t len = static_cast<uint32_t>(be - bs - o < kBulkChunk ? be - bs - o : kBulkChunk);
+              bulk_s2g(reinterpret_cast<char*>(bs) + o, sp + o, len);
+            }
           }
           bulk_commit();  // one group per chunk (possibly empty)
         }

@@ -36,7 +36,17 @@ def _run(A, **kw):
     (37, 37, 0, 0),            # square
     (20_000, 50, 0, 0),
     (60_000, 50, 2999, 0),     # blocks of several register tiles
-    (12_000, 64, 0, 0),        # largest n of the double-buffered form
+    (12_000, 64, 0, 0),        # largest n of the streaming form (16-row staggered staging)
+    (50_000, 32, 0, 0),        # n % 8 == 0: staggered staging
+    (1_000_000, 32, 0, 0),     # 50+ chunks per CTA: the copy warp trails the row groups by several chunks
+    (30_000, 16, 1500, 0),     # n % 8 == 0, small n, blocks of several tiles
+    (40_000, 8, 0, 0),
+    (30_000, 48, 2500, 0),
+    (25_000, 56, 0, 0),        # three Y buffers per group
+    (30_000, 12, 0, 0),        # n % 8 == 4: 16-byte rows, row-major staging
+    (20_000, 60, 0, 0),
+    (30_000, 33, 0, 0),        # odd n: chunks with unaligned edges
+    (100_003, 10, 1000, 0),    # last block of 3 rows (< n)
     (3000, 100, 0, 0),         # the wide form (n > 64), one block
     (20_000, 65, 0, 0),        # smallest wide n
     (40_000, 77, 3000, 0),     # wide, blocks of several tiles, odd n
@@ -145,6 +155,33 @@ def test_tf32x3_wide_host_buffers_match_device():
     import paper_1301_1071_gb300 as T
     m, n, b = 200_000, 90, 2500
     A = torch.tensor(ti.gaussian(m, n, 33).astype(np.float32))
+    Qh, Rh = T.direct_host(A.pin_memory(), block_rows=b, prec="tf32x3")
+    Qd, Rd = T.direct(A.cuda(), block_rows=b, prec="tf32x3")
+    torch.cuda.synchronize()
+    assert torch.equal(Qh, Qd.cpu()) and torch.equal(Rh, Rd.cpu())
+
+
+def test_tf32x3_misaligned_q_rejected():
+    """Q must start on a 16-byte boundary (the chunk stream's bulk copies and
+    vector row accesses rely on it): a pointer 4 bytes past one is refused
+    on the host with TSQR_ERR_ALIGN, before any launch."""
+    import paper_1301_1071_gb300 as T
+    m, n = 5000, 24
+    A = torch.tensor(ti.gaussian(m, n, 64).astype(np.float32), device="cuda")
+    Qm = torch.empty(m * n + 1, dtype=torch.float32, device="cuda")[1:].view(m, n)
+    Rm = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    assert Qm.data_ptr() % 16 == 4
+    with pytest.raises(T.TSQRError, match="ALIGN"):
+        T.direct(A, prec="tf32x3", out=(Qm, Rm))
+
+
+@pytest.mark.parametrize("n", [25, 64])
+def test_tf32x3_host_buffers_match_device(n):
+    """tsqr_direct_host with the n <= 64 chunk stream (the W chain and the
+    stream per batch of blocks) equals tsqr_direct bit for bit."""
+    import paper_1301_1071_gb300 as T
+    m, b = 300_000, 3000
+    A = torch.tensor(ti.gaussian(m, n, 35 + n).astype(np.float32))
     Qh, Rh = T.direct_host(A.pin_memory(), block_rows=b, prec="tf32x3")
     Qd, Rd = T.direct(A.cuda(), block_rows=b, prec="tf32x3")
     torch.cuda.synchronize()
