@@ -87,8 +87,8 @@ typedef enum tsqr_dtype { TSQR_F64 = 0, TSQR_F32 = 1 } tsqr_dtype;
  *         (Y = Yh + Yl, W = Wh + Wl rounded to TF32; Y W ~ Yh Wh + Yh Wl +
  *         Yl Wh, binary32 accumulation), for every n.
  * AUTO:   the library's choice for the data: TSQR_F32 data takes TF32X3 at
- *         n >= 64 and NATIVE below; TSQR_F64 data takes OZAKI at n <= 32
- *         and NATIVE above.
+ *         n >= 20 (where it is the faster Step 3) and NATIVE below;
+ *         TSQR_F64 data takes OZAKI at n <= 32 and NATIVE above.
  * OZAKI:  TSQR_F64 data only.  Step 1's Householder factorisation and the
  *         tree in binary64; for n <= 32 the two products of the method run on
  *         the tensor cores as error-free split products (Ozaki, Ogita, Oishi,

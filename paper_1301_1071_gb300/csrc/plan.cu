@@ -141,8 +141,8 @@ size_t op_bytes(const Plan& P, int op) {
 
 int resolve_prec(int prec, int esz, int64_t n) {
   if (prec != TSQR_PREC_AUTO) return prec;
-  // binary32 data: the Step-3 product on the tensor cores from n = 64 up,
-  // where its share of the pass outgrows the split's overhead; binary64 data:
+  // binary32 data: the Step-3 product on the tensor cores from n = 20 up,
+  // where it outruns the FMA form; binary64 data:
   // the error-free (Ozaki) tensor-core products where they apply (n <= 32)
   if (esz == 4) return n >= kAutoTf32MinN ? TSQR_PREC_TF32X3 : TSQR_PREC_NATIVE;
   return n <= kOzMaxN ? TSQR_PREC_OZAKI : TSQR_PREC_NATIVE;

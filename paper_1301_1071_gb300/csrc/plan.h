@@ -106,9 +106,10 @@ constexpr int kMaxGramParts = 304;  // at most this many partial Grams (2 per SM
 
 // TSQR_PREC_AUTO -> the concrete mode for this dtype and n (other modes
 // are returned unchanged): binary32 data at n >= kAutoTf32MinN takes the
-// 3xTF32 Step 3, binary64 data at n <= 32 the Ozaki form, everything else
-// the data's own arithmetic.
-constexpr int kAutoTf32MinN = 64;
+// 3xTF32 Step 3 (measured faster than the binary32 FMA Step 3 from about
+// n = 16 on; below, the chunk stream's per-chunk cost dominates), binary64
+// data at n <= 32 the Ozaki form, everything else the data's own arithmetic.
+constexpr int kAutoTf32MinN = 20;
 int resolve_prec(int prec, int esz, int64_t n);
 
 // Workspace bytes of `op` (tsqr_op) under a built plan.

@@ -85,15 +85,17 @@ struct FormQTcSmem {
   }
 };
 
-// k_w_chain: T_t^T, X and Z (binary32, n x n each)
+// k_w_chain: T_t^T, X and Z (binary32, n x n each at row stride n rounded up
+// to 4, contiguous)
+TSQR_HD constexpr int wc_stride(int n) { return (n + 3) / 4 * 4; }
 struct WChainSmem {
   size_t ts, xs, zs, total;
   TSQR_HD WChainSmem(int n) {
-    const size_t nn4 = (size_t)n * n * 4;
+    const size_t sz = (size_t)n * wc_stride(n) * 4;  // a multiple of 16
     ts = 0;
-    xs = align_up(nn4, 16);
-    zs = xs + align_up(nn4, 16);
-    total = zs + align_up(nn4, 16);
+    xs = sz;
+    zs = 2 * sz;
+    total = 3 * sz;
   }
 };
 
@@ -144,8 +146,10 @@ __device__ __forceinline__ float tf32_round(float x) {
 // with Y_top the block's first min(rows, n) rows of Y (unit lower
 // triangular).  Writes -W_t split into TF32 parts, hi then lo (n x n each,
 // row-major, binary32), over T slot t, and X_0 = X (binary32) over the first
-// half of the block's C; T_t and C are read before they are written.  W = T src runs as 4 x 5 register blocks (rows kk0 ..,
-// columns c0b ..), T staged transposed so a warp's row block is one broadcast.
+// half of the block's C; T_t and C are read before they are written.
+// W = T src runs as 4 x 4 register blocks (rows kk0 .., columns c0 ..) read
+// with 16-byte shared loads: T is staged transposed and every n x n operand
+// at row stride np = n rounded up to 4, the padding zero.
 // Launch: gridDim = p, blockDim = kWcThreads, dynamic smem = WChainSmem(n).
 __global__ void __launch_bounds__(kWcThreads, 3)
     k_w_chain(const float* __restrict__ Yg, int64_t m, int n, int64_t b, int B, int bt, int kt, double* Tg,
@@ -155,16 +159,17 @@ __global__ void __launch_bounds__(kWcThreads, 3)
   float* ts = reinterpret_cast<float*>(smem + L.ts);
   float* xs = reinterpret_cast<float*>(smem + L.xs);
   float* zs = reinterpret_cast<float*>(smem + L.zs);
-  const int tid = threadIdx.x, nn = n * n;
+  const int tid = threadIdx.x, nn = n * n, np = wc_stride(n), nq = np / 4;
   const int64_t blk = blockIdx.x, row0 = blk * b;
   const int rows = static_cast<int>(m - row0 < b ? m - row0 : b);
   const int ntiles = rows <= B ? 1 : 1 + (rows - B + bt - 1) / bt;
   const int ntop = rows < n ? rows : n;
   const int64_t cb = cblocks == 1 ? 0 : blk;
-  for (int idx = tid; idx < nn; idx += kWcThreads) xs[idx] = static_cast<float>(Cg[cb * nn + idx]);
-  const int nrb = (n + kTcwRB - 1) / kTcwRB, ncb = (n + kTcwCB - 1) / kTcwCB;
-  const bool wblk = tid < nrb * ncb;
-  const int kk0 = (tid / ncb) * kTcwRB, c0b = (tid % ncb) * kTcwCB;
+  for (int idx = tid; idx < 3 * n * np; idx += kWcThreads) ts[idx] = 0.0f;  // ts, xs, zs and their padding
+  __syncthreads();
+  for (int idx = tid; idx < nn; idx += kWcThreads) xs[(idx / n) * np + idx % n] = static_cast<float>(Cg[cb * nn + idx]);
+  const bool wblk = tid < nq * nq;
+  const int kk0 = (tid / nq) * 4, c0 = (tid % nq) * 4;
   double tp[kWcMaxE];  // T of the next tile, fetched one step ahead
   auto fetch_t = [&](int t) {
     const double* Tb = Tg + (blk * kt + t) * nn;
@@ -179,31 +184,34 @@ __global__ void __launch_bounds__(kWcThreads, 3)
     const float* src = xs;
     if (t == 0) {
       // Z = Y_top^T X: Z[kk] = X[kk] + sum_{kk < r < ntop} Y[r][kk] X[r] (zero for kk >= ntop)
-      for (int idx = tid; idx < ntop * n; idx += kWcThreads) ts[idx] = Yg[row0 * n + idx];
+      for (int idx = tid; idx < ntop * n; idx += kWcThreads) ts[(idx / n) * np + idx % n] = Yg[row0 * n + idx];
       __syncthreads();
       if (wblk) {
-        float zb[kTcwRB][kTcwCB];
+        float zb[4][4];
 #pragma unroll
-        for (int r = 0; r < kTcwRB; ++r)
-#pragma unroll
-          for (int c = 0; c < kTcwCB; ++c)
-            zb[r][c] = (kk0 + r < ntop && c0b + c < n) ? xs[(kk0 + r) * n + c0b + c] : 0.0f;
+        for (int r = 0; r < 4; ++r) {
+          const float4 x = *reinterpret_cast<const float4*>(xs + (kk0 + r < n ? kk0 + r : 0) * np + c0);
+          const bool in = kk0 + r < ntop;
+          zb[r][0] = in ? x.x : 0.0f;
+          zb[r][1] = in ? x.y : 0.0f;
+          zb[r][2] = in ? x.z : 0.0f;
+          zb[r][3] = in ? x.w : 0.0f;
+        }
         for (int i = kk0 + 1; i < ntop; ++i) {
-          float yv[kTcwRB], xv[kTcwCB];
+          const float4 y4 = *reinterpret_cast<const float4*>(ts + i * np + kk0);
+          const float4 x4 = *reinterpret_cast<const float4*>(xs + i * np + c0);
+          const float yv[4] = {i > kk0 ? y4.x : 0.0f, i > kk0 + 1 ? y4.y : 0.0f, i > kk0 + 2 ? y4.z : 0.0f,
+                               i > kk0 + 3 ? y4.w : 0.0f};
+          const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-          for (int r = 0; r < kTcwRB; ++r) yv[r] = (i > kk0 + r && kk0 + r < n) ? ts[i * n + kk0 + r] : 0.0f;
+          for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int c = 0; c < kTcwCB; ++c) xv[c] = c0b + c < n ? xs[i * n + c0b + c] : 0.0f;
-#pragma unroll
-          for (int r = 0; r < kTcwRB; ++r)
-#pragma unroll
-            for (int c = 0; c < kTcwCB; ++c) zb[r][c] = fmaf(yv[r], xv[c], zb[r][c]);
+            for (int c = 0; c < 4; ++c) zb[r][c] = fmaf(yv[r], xv[c], zb[r][c]);
         }
 #pragma unroll
-        for (int r = 0; r < kTcwRB; ++r)
-#pragma unroll
-          for (int c = 0; c < kTcwCB; ++c)
-            if (kk0 + r < n && c0b + c < n) zs[(kk0 + r) * n + c0b + c] = zb[r][c];
+        for (int r = 0; r < 4; ++r)
+          if (kk0 + r < n)
+            *reinterpret_cast<float4*>(zs + (kk0 + r) * np + c0) = make_float4(zb[r][0], zb[r][1], zb[r][2], zb[r][3]);
       }
       __syncthreads();  // Y_top's reads of ts are done before T_0 is staged
       src = zs;
@@ -213,47 +221,45 @@ __global__ void __launch_bounds__(kWcThreads, 3)
     for (int e = 0; e < kWcMaxE; ++e) {
       const int idx = tid + e * kWcThreads;
       if (idx < nn) {
-        const int kk = idx / n, i = idx % n;
-        ts[i * n + kk] = i >= kk ? static_cast<float>(tp[e]) : 0.0f;
+        const int kk = idx / n, i = idx - kk * n;
+        ts[i * np + kk] = i >= kk ? static_cast<float>(tp[e]) : 0.0f;
       }
     }
     if (t > 0) fetch_t(t - 1);
     __syncthreads();
-    float wb[kTcwRB][kTcwCB];
+    float wb[4][4];
 #pragma unroll
-    for (int r = 0; r < kTcwRB; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int c = 0; c < kTcwCB; ++c) wb[r][c] = 0.0f;
+      for (int c = 0; c < 4; ++c) wb[r][c] = 0.0f;
     if (wblk) {
       for (int i = kk0; i < n; ++i) {
-        float tv[kTcwRB], sv[kTcwCB];
+        const float4 t4 = *reinterpret_cast<const float4*>(ts + i * np + kk0);
+        const float4 s4 = *reinterpret_cast<const float4*>(src + i * np + c0);
+        const float tv[4] = {t4.x, t4.y, t4.z, t4.w}, sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-        for (int r = 0; r < kTcwRB; ++r) tv[r] = kk0 + r < n ? ts[i * n + kk0 + r] : 0.0f;
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < kTcwCB; ++c) sv[c] = c0b + c < n ? src[i * n + c0b + c] : 0.0f;
-#pragma unroll
-        for (int r = 0; r < kTcwRB; ++r)
-#pragma unroll
-          for (int c = 0; c < kTcwCB; ++c) wb[r][c] = fmaf(tv[r], sv[c], wb[r][c]);
+          for (int c = 0; c < 4; ++c) wb[r][c] = fmaf(tv[r], sv[c], wb[r][c]);
       }
     }
     __syncthreads();  // every read of ts and src is done
     float* Wout = reinterpret_cast<float*>(Tg + (blk * kt + t) * nn);
     if (t == 0) {
       float* X0 = reinterpret_cast<float*>(Cg + cb * nn);  // C was read into xs
-      for (int idx = tid; idx < nn; idx += kWcThreads) X0[idx] = xs[idx];
+      for (int idx = tid; idx < nn; idx += kWcThreads) X0[idx] = xs[(idx / n) * np + idx % n];
     }
     if (wblk) {
 #pragma unroll
-      for (int r = 0; r < kTcwRB; ++r)
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < kTcwCB; ++c) {
-          const int kk = kk0 + r, cc = c0b + c;
+        for (int c = 0; c < 4; ++c) {
+          const int kk = kk0 + r, cc = c0 + c;
           if (kk < n && cc < n) {
             const float hv = tf32_round(-wb[r][c]);
             Wout[kk * n + cc] = hv;
             Wout[nn + kk * n + cc] = tf32_round(-wb[r][c] - hv);
-            if (t > 0) xs[kk * n + cc] -= wb[r][c];
+            if (t > 0) xs[kk * np + cc] -= wb[r][c];
           }
         }
     }

@@ -268,15 +268,17 @@ def _launches_dt(lib, op, m, n, dt, block_rows):
 
 
 @pytest.mark.parametrize("dt,n,want_prec,want_tc", [
-    (1, 50, 0, 0),   # binary32 below n = 64: native binary32 Step 3
-    (1, 64, 2, 1),   # binary32 at n = 64: 3xTF32 Step 3 on the tensor cores
+    (1, 10, 0, 0),   # binary32 below n = 20: native binary32 Step 3
+    (1, 50, 2, 1),   # binary32 from n = 20: 3xTF32 Step 3 on the tensor cores (the chunk stream)
+    (1, 64, 2, 1),
     (1, 100, 2, 1),  # ... up to n = 100 (the wide form)
     (0, 64, 0, 0),   # binary64 data above n = 32: native binary64
     (0, 25, 4, 1),   # binary64 data at n <= 32: the Ozaki form
 ])
 def test_auto_precision_plan(lib, dt, n, want_prec, want_tc):
-    """TSQR_PREC_AUTO resolves to 3xTF32 for binary32 data at n >= 64 (the
-    threshold at which the split-precision products are asked for), to the
+    """TSQR_PREC_AUTO resolves to 3xTF32 for binary32 data at n >= 20 (where
+    it is the faster Step 3; the split-precision products are asked for from
+    n = 64), to the
     Ozaki form for binary64 data at n <= 32, and to the data's own arithmetic
     otherwise."""
     st, info = _plan(lib, 0, 1_000_000, n, dt, prec=3)
