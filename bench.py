@@ -105,7 +105,7 @@ def load_peaks():
 # traffic bench.py reports from a committed ncu capture.
 KERNEL_SOURCES = ["qr_kernels.cuh", "device.cuh", "df64.cuh", "layout.cuh", "kern_inst.cuh", "kern_f64.cu",
                   "kern_df64.cu", "kern_f32.cu", "kern_r_f64.cu", "tiles_f64.h", "tiles_f32.h", "plan.cu", "plan.h",
-                  "oz_kernels.cuh", "kern_oz.cu", "tcgen05.cuh"]
+                  "oz_kernels.cuh", "kern_oz.cu", "tcgen05.cuh", "chunks.cuh"]
 
 
 def kernel_source_hash() -> str:

@@ -527,7 +527,7 @@ tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, c
   if (rc != TSQR_OK) return static_cast<tsqr_status>(rc);
   const int L = static_cast<int>(P.levels.size());
   const int g = P.gram_oz ? 1 : 0;                     // the tensor-core Gram after Step 1
-  const int w = (P.tc3 && P.n <= kTcMaxN) ? 1 : 0;     // the W chain before the 3xTF32 stream
+  const int w = (P.tc3 && P.n <= kTcMaxN) ? 1 : 0;  // the W chain before the 3xTF32 chunk stream
   switch (op) {
     case TSQR_OP_DIRECT_HOST: *launches = (3 + g + w) * chunks + 3 * (L - 1) + 1; break;  // chunks x (Step 1, T, Step 3)
     case TSQR_OP_DIRECT: *launches = 3 * L + 1 + g + w; break;    // L up (+ T build), sign fix, L down
