@@ -579,86 +579,55 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
     for (int c = i + lane; c < n; c += 32) g[i * n + c] = static_cast<double>(t[c * (c + 1) / 2 + i]);
 }
 
-// Few slots (the upper tree levels): one slot per CTA of kBuildTWarps warps;
-// step j splits the sum index l over the warps, and warp 0 adds the
-// partials in warp order (deterministic) before the CTA moves on.
-constexpr int kBuildTWarps = 8;
-
+// Few slots (the upper tree levels): one slot per CTA, column c of T formed
+// by thread c with no barrier in between.  The column recursion's T has the
+// inverse diag(1/tau) + (the strict upper triangle of G) -- exactly, for the
+// computed tau and G (by induction: T_j = [T, a; 0, tau_j] with a = -tau_j T
+// G(0:j, j) has the inverse [T^-1, G(0:j, j); 0, 1/tau_j]) -- so each column
+// is an independent back substitution: T(c,c) = tau_c and, for i = c-1 down
+// to 0, T(i,c) = -tau_i sum_{k=i+1}^{c} G(i,k) T(k,c) (tau_i = 0 gives a zero
+// row, as the recursion does).  The sum runs over k ascending in two
+// interleaved chains.  G and T in shared memory, n x n each.
 template <class F>
-__global__ void __launch_bounds__(32 * kBuildTWarps) k_build_t_cta(double* __restrict__ Tst, int n) {
+__global__ void __launch_bounds__(128) k_build_t_cta(double* __restrict__ Tst, int n) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
-  const int np = n * (n + 1) / 2;
-  F* t = reinterpret_cast<F*>(tsm_raw);
-  F* part = t + ((np + 1) & ~1);  // kBuildTWarps x 32 kBuildTSegs partial sums
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  F* G = reinterpret_cast<F*>(tsm_raw);  // n x n: tau on the diagonal, G above it
+  F* T = G + n * n;                       // n x n: column c is thread c's
   double* g = Tst + static_cast<int64_t>(blockIdx.x) * n * n;
-  // n <= 128 < blockDim.x: one entry per thread and row; kBuildTStage rows'
-  // loads in flight together
-  for (int i0 = 0; i0 < n; i0 += kBuildTStage) {
-    double v[kBuildTStage];
-#pragma unroll
-    for (int r = 0; r < kBuildTStage; ++r) {
-      const int i = i0 + r, c = i + static_cast<int>(threadIdx.x);
-      v[r] = (i < n && c < n) ? g[i * n + c] : 0.0;
-    }
-#pragma unroll
-    for (int r = 0; r < kBuildTStage; ++r) {
-      const int i = i0 + r, c = i + static_cast<int>(threadIdx.x);
-      if (i < n && c < n) t[c * (c + 1) / 2 + i] = static_cast<F>(v[r]);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, c = idx - i * n;
+    G[idx] = c >= i ? static_cast<F>(g[idx]) : F(0);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    T[c * n + c] = G[c * n + c];
+    for (int i = c - 1; i >= 0; --i) {
+      F a0 = F(0), a1 = F(0);
+      int k = i + 1;
+      for (; k + 1 <= c; k += 2) {
+        a0 = fma(G[i * n + k], T[k * n + c], a0);
+        a1 = fma(G[i * n + k + 1], T[(k + 1) * n + c], a1);
+      }
+      if (k <= c) a0 = fma(G[i * n + k], T[k * n + c], a0);
+      T[i * n + c] = -G[i * n + i] * (a0 + a1);
     }
   }
   __syncthreads();
-  for (int j = 1; j < n; ++j) {
-    const F* gj = t + j * (j + 1) / 2;
-    const int l0 = j * w / kBuildTWarps, l1 = j * (w + 1) / kBuildTWarps;
-    F acc[kBuildTSegs][2];
-#pragma unroll
-    for (int s = 0; s < kBuildTSegs; ++s) acc[s][0] = acc[s][1] = F(0);
-    const F* tl = t + l0 * (l0 + 1) / 2;
-    for (int l = l0; l < l1; ++l) {
-      const F gl = gj[l];
-#pragma unroll
-      for (int s = 0; s < kBuildTSegs; ++s) {
-        if (32 * s > l) break;
-        const int i = lane + 32 * s;
-        if (i <= l) {  // static accumulator indices keep acc in registers
-          if (l & 1) acc[s][1] = fma(tl[i], gl, acc[s][1]);
-          else acc[s][0] = fma(tl[i], gl, acc[s][0]);
-        }
-      }
-      tl += l + 1;
-    }
-#pragma unroll
-    for (int s = 0; s < kBuildTSegs; ++s) part[(w * kBuildTSegs + s) * 32 + lane] = acc[s][0] + acc[s][1];
-    __syncthreads();
-    if (w == 0) {
-      const F tj = gj[j];
-      F* tcol = t + j * (j + 1) / 2;
-#pragma unroll
-      for (int s = 0; s < kBuildTSegs; ++s) {
-        const int i = lane + 32 * s;
-        if (i < j) {
-          F v = F(0);
-          for (int ww = 0; ww < kBuildTWarps; ++ww) v += part[(ww * kBuildTSegs + s) * 32 + lane];
-          tcol[i] = -tj * v;
-        }
-      }
-    }
-    __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, c = idx - i * n;
+    if (c >= i) g[idx] = static_cast<double>(T[idx]);
   }
-  for (int i = 0; i < n; ++i)
-    for (int c = i + threadIdx.x; c < n; c += blockDim.x) g[i * n + c] = static_cast<double>(t[c * (c + 1) / 2 + i]);
 }
 
 template <class F>
 static cudaError_t build_t_typed(double* Tst, int64_t p, int n, int sms, cudaStream_t st) {
   const size_t np = static_cast<size_t>(n) * (n + 1) / 2;
   if (p < 2 * static_cast<int64_t>(sms)) {
-    // few slots: latency decides, so one CTA of several warps per slot
-    const size_t smem = (((np + 1) & ~static_cast<size_t>(1)) + kBuildTWarps * kBuildTSegs * 32) * sizeof(F);
+    // few slots: latency decides, so one CTA per slot, a thread per column
+    const size_t smem = 2 * static_cast<size_t>(n) * n * sizeof(F);
     cudaError_t e = cudaFuncSetAttribute(k_build_t_cta<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_build_t_cta<F><<<static_cast<unsigned>(p), 32 * kBuildTWarps, smem, st>>>(Tst, n);
+    k_build_t_cta<F><<<static_cast<unsigned>(p), 128, smem, st>>>(Tst, n);
     return cudaGetLastError();
   }
   // many slots: one warp per slot, as many warps (<= 16) as packed triangles fit in 220 KB

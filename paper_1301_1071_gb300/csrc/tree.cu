@@ -49,25 +49,32 @@ __device__ __forceinline__ void tri_rows(const double* U, const double* D, int l
   }
 }
 
-// One CTA per node.  Y: the level's input stack (rows x n, binary64), node b
-// = rows [b f n, min((b + 1) f n, rows)); T: one n x n slot per node (upper
-// triangle); C: cblocks coefficient blocks (cblocks == 1: all nodes use C).
-// A thread group of ceil(n/2) row pairs x ceil(n/CJ) column groups forms one
-// n x n product; KB groups take KB blocks of the node at once (small n:
-// the 24 further blocks of a 25-way node at n = 25 take 3 passes, not 24).
-// Group 0 forms W.  Threads: KB x group size <= MAXT.
+// P CTAs per node, CTA (node, panel) for the panel's column groups (the
+// columns of W = T C and of the node's Q blocks are independent, so a level
+// of few nodes still fills the GPU).  Y: the level's input stack (rows x n,
+// binary64), node b = rows [b f n, min((b + 1) f n, rows)); T: one n x n slot
+// per node (upper triangle); C: cblocks coefficient blocks (cblocks == 1: all
+// nodes use C).  A thread group of ceil(n/2) row pairs x ncp column groups
+// (CJ columns each) forms the panel of one n x n product; KB groups take KB
+// blocks of the node at once (small n: the 24 further blocks of a 25-way node
+// at n = 25 take 3 passes, not 24).  Group 0 forms W.  Threads: KB x group
+// size <= MAXT.
 template <int CJ, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int n, int f, const double* T,
-                                                    const double* C, int64_t cblocks, int KB) {
+                                                    const double* C, int64_t cblocks, int KB, int P) {
   extern __shared__ __align__(16) double tsm[];
   const int ncg = (n + CJ - 1) / CJ;
+  const int ncp = (ncg + P - 1) / P;  // column groups per panel
   const int ld = ncg * CJ + 1;
-  const int gsz = (n + 1) / 2 * ncg;  // threads per group
-  double* Wb = tsm;                   // T, then W = T C
+  const int gsz = (n + 1) / 2 * ncp;  // threads per group
+  double* Wb = tsm;                   // T, then W = T C (the panel's columns)
   const int tid = threadIdx.x, NT = blockDim.x;
   const int grp = tid / gsz, gt = tid - grp * gsz;
   double* Bb = tsm + (1 + (grp < KB ? grp : 0)) * n * ld;  // the group's block (group 0's holds C first)
-  const int64_t node = blockIdx.x;
+  const int64_t node = blockIdx.x / P;
+  const int pnl = static_cast<int>(blockIdx.x - node * P);
+  const int cb0 = pnl * ncp * CJ;                           // the panel's first column
+  const int cb1 = (pnl + 1) * ncp * CJ < n ? (pnl + 1) * ncp * CJ : n;  // ... and its end (<= cb0: none)
   const int64_t r0 = node * f * n;
   const int nb = static_cast<int>((rows - r0) / n < f ? (rows - r0) / n : f);
   const double* Tn = T + node * n * n;
@@ -81,14 +88,16 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
     B0[idx] = c < n ? Cn[i * n + c] : 0.0;
   }
   __syncthreads();
-  const int g = gt / ncg, cg = gt - g * ncg;
+  const int g = gt / ncp, cg = gt - g * ncp;
   const bool active = grp < KB;  // every thread of a group has a row pair
-  const int c0 = cg * CJ;
+  // the thread's column group; the last panel may have fewer (or none)
+  const bool colok = pnl * ncp + cg < ncg;
+  const int c0 = cb0 + cg * CJ;
   double top[CJ], bot[CJ];
-  // W = T C (group 0)
-  if (grp == 0) tri_rows<CJ>(Wb, B0, ld, n, g, c0, top, bot);
+  // W = T C (group 0, the panel's columns)
+  if (grp == 0 && colok) tri_rows<CJ>(Wb, B0, ld, n, g, c0, top, bot);
   __syncthreads();
-  if (grp == 0) {
+  if (grp == 0 && colok) {
 #pragma unroll
     for (int b = 0; b < CJ; ++b) {
       Wb[g * ld + c0 + b] = top[b];
@@ -96,13 +105,15 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
     }
   }
   __syncthreads();
-  // block 1 of the node: C - W
-  for (int idx = tid; idx < n * n; idx += NT) {
-    const int i = idx / n, c = idx - i * n;
-    Yn[idx] = B0[i * ld + c] - Wb[i * ld + c];
+  // block 1 of the node: C - W (the panel's columns)
+  const int pw = cb1 > cb0 ? cb1 - cb0 : 0;
+  for (int idx = tid; idx < n * pw; idx += NT) {
+    const int i = idx / pw, c = cb0 + idx - i * pw;
+    Yn[i * n + c] = B0[i * ld + c] - Wb[i * ld + c];
   }
   // blocks 2..nb: -V_k W, KB at a time (V_k staged whole before its rows
-  // are overwritten)
+  // are overwritten; the node's other panels stage their own copies before
+  // writing their own columns only)
   for (int kb = 1; kb < nb; kb += KB) {
     const int k = kb + grp;
     const bool mine = active && k < nb;
@@ -115,11 +126,14 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
       }
     }
     __syncthreads();
-    if (mine) {
+    // every panel of the node has staged these blocks before any overwrites
+    // its columns of them (the node's P CTAs are one cluster)
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    if (mine && colok) {
       tri_rows<CJ>(Bb, Wb, ld, n, g, c0, top, bot);
 #pragma unroll
       for (int b = 0; b < CJ; ++b) {
-        if (c0 + b < n) {
+        if (c0 + b < cb1) {
           Yk[g * n + c0 + b] = -top[b];
           if (n - 1 - g != g) Yk[(n - 1 - g) * n + c0 + b] = -bot[b];
         }
@@ -143,122 +157,107 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
 // over the node's rows of Y (blocks 2..f; block 1 holds R and is never read),
 // tau_j and the Gram entries v_i^T v_j (i < j) into the node's T slot
 // (k_build_t forms T).  WANT_Y = false: R only.
+// Threads: G per column (G a power of two, the G lanes of a column in one
+// warp), column c = tid / G.  Per column j two CTA barriers: column j's group
+// forms the norm, the reflector scalars and v (its G lanes reduce by
+// shuffles); then every later column's group forms its dot with v and its
+// update -- each column is touched by its own group only, so the dots and
+// the update of a column need no barrier between them.
 // The node sits in shared memory, row r at M[r * ldm].
 template <bool WANT_Y>
-__global__ void __launch_bounds__(512) k_tree_up(const double* X, int64_t rows, int n, int f, double* Y,
-                                                 double* Rout, double* Tst) {
+__global__ void __launch_bounds__(1024) k_tree_up(const double* X, int64_t rows, int n, int f, double* Y,
+                                                  double* Rout, double* Tst, int G) {
   extern __shared__ __align__(16) double usm[];
   const int ldm = n + 1;
-  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int c = tid / G, u = tid - c * G;  // my column and my lane within its group
   const int64_t node = blockIdx.x;
   const int64_t r0 = node * f * n;
   const int nb = static_cast<int>((rows - r0) / n < f ? (rows - r0) / n : f);
   double* M = usm;                      // nb n rows
-  double* part = M + nb * n * ldm;      // n x (f - 1) partial dots
-  double* wv = part + n * (f - 1);      // tau w_c per column
-  double* red = wv + n;                 // 32 warp sums
-  double* sc = red + 32;                // beta, scal, tau, taus[n]
-  double* taus = sc + 4;
+  double* taus = M + nb * n * ldm;      // tau per column
   const double* Xn = X + r0 * n;
   for (int idx = tid; idx < nb * n * n; idx += NT) {
-    const int r = idx / n, c = idx - r * n;
-    M[r * ldm + c] = c >= r % n ? Xn[idx] : 0.0;  // the blocks are triangular; below: exact zeros
+    const int r = idx / n, cc = idx - r * n;
+    M[r * ldm + cc] = cc >= r % n ? Xn[idx] : 0.0;  // the blocks are triangular; below: exact zeros
   }
   __syncthreads();
   const int nsub = nb - 1;  // blocks below the first
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
   for (int j = 0; j < n; ++j) {
-    const int ej = nsub * (j + 1);  // sub-column entries (k >= 1, lr <= j)
-    // squared norm of the sub-column
-    double ss = 0.0;
-    for (int e = tid; e < ej; e += NT) {
-      const int k = 1 + e / (j + 1), lr = e - (k - 1) * (j + 1);
-      const double v = M[(k * n + lr) * ldm + j];
-      ss = fma(v, v, ss);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) red[warp] = ss;
-    __syncthreads();
-    if (tid == 0) {
-      double s2 = 0.0;
-      for (int w = 0; w < (NT >> 5); ++w) s2 += red[w];  // fixed order
+    if (c == j) {
+      // squared norm of the sub-column: block k, rows lr = u, u + G, .. <= j
+      double ss = 0.0;
+      for (int k = 1; k <= nsub; ++k) {
+        const double* col = M + static_cast<size_t>(k) * n * ldm + j;
+        for (int lr = u; lr <= j; lr += G) ss = fma(col[lr * ldm], col[lr * ldm], ss);
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(gmask, ss, o);
       const double alpha = M[j * ldm + j];
-      const double sigma = sqrt(fma(alpha, alpha, s2));
+      const double sigma = sqrt(fma(alpha, alpha, ss));
+      double beta, scal, tau;
       if (sigma == 0.0) {
-        sc[0] = alpha; sc[1] = 0.0; sc[2] = 0.0;
+        beta = alpha;
+        scal = 0.0;
+        tau = 0.0;
       } else {
-        const double beta = alpha >= 0.0 ? -sigma : sigma;
-        sc[0] = beta;
-        sc[1] = 1.0 / (alpha - beta);
-        sc[2] = (beta - alpha) / beta;
+        beta = alpha >= 0.0 ? -sigma : sigma;
+        scal = 1.0 / (alpha - beta);
+        tau = (beta - alpha) / beta;
       }
-      taus[j] = sc[2];
-      M[j * ldm + j] = sc[0];
+      // v: the scaled sub-column
+      for (int k = 1; k <= nsub; ++k) {
+        double* col = M + static_cast<size_t>(k) * n * ldm + j;
+        for (int lr = u; lr <= j; lr += G) col[lr * ldm] *= scal;
+      }
+      if (u == 0) {
+        taus[j] = tau;
+        M[j * ldm + j] = beta;
+      }
     }
     __syncthreads();
-    const double scal = sc[1], tau = sc[2];
-    // v: the scaled sub-column
-    for (int e = tid; e < ej; e += NT) {
-      const int k = 1 + e / (j + 1), lr = e - (k - 1) * (j + 1);
-      M[(k * n + lr) * ldm + j] *= scal;
+    const double tau = taus[j];
+    if (c > j && c < n && tau != 0.0) {
+      // w_c = a_jc + v^T a_c over the sub-column rows; a_c -= (tau w_c) v
+      double w = 0.0;
+      for (int k = 1; k <= nsub; ++k) {
+        const double* blk = M + static_cast<size_t>(k) * n * ldm;
+        for (int lr = u; lr <= j; lr += G) w = fma(blk[lr * ldm + j], blk[lr * ldm + c], w);
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) w += __shfl_xor_sync(gmask, w, o);
+      const double tw = tau * (M[j * ldm + c] + w);
+      if (u == 0) M[j * ldm + c] -= tw;
+      for (int k = 1; k <= nsub; ++k) {
+        double* blk = M + static_cast<size_t>(k) * n * ldm;
+        for (int lr = u; lr <= j; lr += G) blk[lr * ldm + c] = fma(-tw, blk[lr * ldm + j], blk[lr * ldm + c]);
+      }
     }
     __syncthreads();
-    const int nc = n - 1 - j;  // trailing columns
-    if (nc > 0 && tau != 0.0) {
-      // partial dots v_k^T a_c over block k, items (c, k)
-      for (int it = tid; it < nc * nsub; it += NT) {
-        const int k = 1 + it / nc, c = j + 1 + (it - (k - 1) * nc);
-        const double* col = M + static_cast<size_t>(k) * n * ldm;
-        double acc = 0.0;
-        for (int lr = 0; lr <= j; ++lr) acc = fma(col[lr * ldm + j], col[lr * ldm + c], acc);
-        part[c * (f - 1) + (k - 1)] = acc;
-      }
-      __syncthreads();
-      // w_c = a_jc + sum_k (block order); row j of R
-      for (int c = j + 1 + tid; c < n; c += NT) {
-        double w = M[j * ldm + c];
-        for (int k = 0; k < nsub; ++k) w += part[c * (f - 1) + k];
-        const double tw = tau * w;
-        wv[c] = tw;
-        M[j * ldm + c] -= tw;
-      }
-      __syncthreads();
-      // a_c -= (tau w_c) v on the sub-column rows, items (k, lr, c)
-      const int per = (j + 1) * nc;
-      for (int it = tid; it < nsub * per; it += NT) {
-        const int k = 1 + it / per;
-        const int rem = it - (k - 1) * per;
-        const int lr = rem / nc, c = j + 1 + (rem - lr * nc);
-        double* row = M + (static_cast<size_t>(k) * n + lr) * ldm;
-        row[c] = fma(-wv[c], row[j], row[c]);
-      }
-      __syncthreads();
-    }
   }
   // R of the node (raw signs)
   double* Rn = Rout + node * n * n;
   for (int idx = tid; idx < n * n; idx += NT) {
-    const int i = idx / n, c = idx - i * n;
-    Rn[idx] = c >= i ? M[i * ldm + c] : 0.0;
+    const int i = idx / n, cc = idx - i * n;
+    Rn[idx] = cc >= i ? M[i * ldm + cc] : 0.0;
   }
   if constexpr (WANT_Y) {
     // Householder vectors over the node's rows (block 1: R, never read)
     double* Yn = Y + r0 * n;
     for (int idx = tid; idx < nb * n * n; idx += NT) {
-      const int r = idx / n, c = idx - r * n;
-      Yn[idx] = M[r * ldm + c];
+      const int r = idx / n, cc = idx - r * n;
+      Yn[idx] = M[r * ldm + cc];
     }
     // tau and the Gram entries G(i, c) = sum_k sum_{lr <= i} v_i(lr) v_c(lr), i < c
     double* Tn = Tst + node * n * n;
     for (int idx = tid; idx < n * n; idx += NT) {
-      const int i = idx / n, c = idx - i * n;
-      if (c < i) continue;
+      const int i = idx / n, cc = idx - i * n;
+      if (cc < i) continue;
       double g = taus[i];
-      if (c > i) {
+      if (cc > i) {
         g = 0.0;
         for (int k = 1; k < nb; ++k) {
           const double* blk = M + static_cast<size_t>(k) * n * ldm;
-          for (int lr = 0; lr <= i; ++lr) g = fma(blk[lr * ldm + i], blk[lr * ldm + c], g);
+          for (int lr = 0; lr <= i; ++lr) g = fma(blk[lr * ldm + i], blk[lr * ldm + cc], g);
         }
       }
       Tn[idx] = g;
@@ -274,7 +273,12 @@ cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, c
   const int maxt = CJ == 10 ? 512 : 1024;
   const int ncg = (n + CJ - 1) / CJ;
   const int ld = ncg * CJ + 1;
-  const int gsz = (n + 1) / 2 * ncg;
+  // panels per node: a level of few nodes is spread over clusters of up to
+  // 5 CTAs (column panels); a wide level keeps one CTA per node
+  int P = 1;
+  while (P < 5 && P < ncg && p * P < 2 * kDefaultSMs) ++P;
+  const int ncp = (ncg + P - 1) / P;
+  const int gsz = (n + 1) / 2 * ncp;
   const size_t buf = static_cast<size_t>(n) * ld * sizeof(double);
   if (gsz > maxt || 2 * buf > kSmemMax) return cudaErrorInvalidConfiguration;
   // groups: as many further blocks at once as threads and shared memory allow
@@ -287,12 +291,23 @@ cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, c
   auto fn = CJ == 10 ? k_tree_down<10, 512> : k_tree_down<5, 1024>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)p, NT, smem, st>>>(Y, rows, n, f, T, C, cblocks, KB);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(p * P));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(P);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, Y, rows, n, f, T, C, cblocks, KB, P);
 }
 
 size_t tree_up_smem(int n, int f) {
-  return (static_cast<size_t>(f) * n * (n + 1) + static_cast<size_t>(n) * (f - 1) + n + 32 + 4 + n) * sizeof(double);
+  return (static_cast<size_t>(f) * n * (n + 1) + n) * sizeof(double);
 }
 
 bool tree_up_fits(int n, int f) { return f >= 2 && tree_up_smem(n, f) <= kSmemMax; }
@@ -301,10 +316,14 @@ cudaError_t launch_tree_up(const double* X, int64_t rows, int n, int f, int64_t 
                            double* Tst, cudaStream_t st) {
   if (!tree_up_fits(n, f)) return cudaErrorInvalidConfiguration;
   const size_t smem = tree_up_smem(n, f);
+  // lanes per column: about 512 threads in all, a power of two from 4 to 32
+  int G = 4;
+  while (G < 32 && 2 * G * n <= 512) G *= 2;
+  const int NT = (G * n + 31) / 32 * 32;
   auto fn = Y ? k_tree_up<true> : k_tree_up<false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<(unsigned)p, 512, smem, st>>>(X, rows, n, f, Y, Rout, Tst);
+  fn<<<(unsigned)p, NT, smem, st>>>(X, rows, n, f, Y, Rout, Tst, G);
   return cudaGetLastError();
 }
 
