@@ -516,7 +516,9 @@ constexpr int kGmMaxN = 32;     // one 32-row quarter per digit slice
 constexpr int kGmShift = 17;    // P = sum_d D_d 2^(8 (7-d) - kGmShift) fits 63 bits
 constexpr int kGmRegions = 8;   // accumulator regions e = j + t <= 7
 constexpr int kGmTmemCols = 256;
+constexpr int kGmPart = 33;     // row stride of the epilogue's partial sums (8-byte words)
 
+static_assert(4 * 32 * kGmPart * 8 <= 2 * 128 * kGmK * 2, "the partial sums fit the two digit buffers");
 struct GramOzSmem {
   size_t ys, p0, p4, red, cexp, gacc, bar, lbar, tslot, total;
   TSQR_HD GramOzSmem(int n) {
@@ -557,7 +559,11 @@ __global__ void __launch_bounds__(kGmThreads, 2)
   int* red = reinterpret_cast<int*>(smem + L.red);
   int* cexp = reinterpret_cast<int*>(smem + L.cexp);
   double* gacc = reinterpret_cast<double*>(smem + L.gacc);
-  long long* part = reinterpret_cast<long long*>(smem + L.p0);  // epilogue: 4 x 32 x 32 partial sums
+  // epilogue: 4 x 32 x 32 partial sums at row stride kGmPart (odd in 8-byte
+  // words: a warp's 32 rows, and a row's 32 columns, fall in distinct banks);
+  // 33.8 KB over the two digit buffers (adjacent), free once the products
+  // completed
+  long long* part = reinterpret_cast<long long*>(smem + L.p0);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
   uint64_t* lbar = reinterpret_cast<uint64_t*>(smem + L.lbar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L.tslot);
@@ -764,7 +770,7 @@ __global__ void __launch_bounds__(kGmThreads, 2)
         }
       }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) part[(q * 32 + lane) * 32 + cb + i] = acc[i];
+      for (int i = 0; i < 16; ++i) part[(q * 32 + lane) * kGmPart + cb + i] = acc[i];
     }
     tc_fence_before();
     __syncthreads();  // partial sums complete; tensor memory read
@@ -772,8 +778,8 @@ __global__ void __launch_bounds__(kGmThreads, 2)
     for (int pr = tid; pr < nn; pr += kGmThreads) {
       const int i = pr / n, c = pr % n;
       if (c > i) {
-        const long long P = part[i * 32 + c] + part[(32 + i) * 32 + c] + part[(64 + i) * 32 + c] +
-                            part[(96 + i) * 32 + c];
+        const long long P = part[i * kGmPart + c] + part[(32 + i) * kGmPart + c] +
+                            part[(64 + i) * kGmPart + c] + part[(96 + i) * kGmPart + c];
         if (P != 0) gacc[pr] += oz_scaled(P, cexp[i] + cexp[c] - 2099);
       }
     }
