@@ -158,11 +158,12 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
 // tau_j and the Gram entries v_i^T v_j (i < j) into the node's T slot
 // (k_build_t forms T).  WANT_Y = false: R only.
 // Threads: G per column (G a power of two, the G lanes of a column in one
-// warp), column c = tid / G.  Per column j two CTA barriers: column j's group
-// forms the norm, the reflector scalars and v (its G lanes reduce by
-// shuffles); then every later column's group forms its dot with v and its
-// update -- each column is touched by its own group only, so the dots and
-// the update of a column need no barrier between them.
+// warp), column c = tid / G; the lanes of a group split the column's
+// sub-column (all blocks, rows 0..j) as one index space.  Per column j two
+// CTA barriers: column j's group forms the norm, the reflector scalars and v
+// (its G lanes reduce by shuffles); then every later column's group forms its
+// dot with v and its update -- each column is touched by its own group only,
+// so the dots and the update of a column need no barrier between them.
 // The node sits in shared memory, row r at M[r * ldm].
 template <bool WANT_Y>
 __global__ void __launch_bounds__(1024) k_tree_up(const double* X, int64_t rows, int n, int f, double* Y,
@@ -185,12 +186,26 @@ __global__ void __launch_bounds__(1024) k_tree_up(const double* X, int64_t rows,
   const int nsub = nb - 1;  // blocks below the first
   const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
   for (int j = 0; j < n; ++j) {
+    // the sub-column of column j: entries e = 0 .. nsub (j + 1) - 1, block
+    // k = 1 + e / (j + 1), row lr = e % (j + 1); lane u takes e = u, u + G, ..
+    // (stepped without division: G = dq (j + 1) + dr)
+    const int len = j + 1, ne = nsub * len;
+    const int dq = G / len, dr = G - dq * len;
+    const int k0 = 1 + u / len, l0 = u - (u / len) * len;
     if (c == j) {
-      // squared norm of the sub-column: block k, rows lr = u, u + G, .. <= j
       double ss = 0.0;
-      for (int k = 1; k <= nsub; ++k) {
-        const double* col = M + static_cast<size_t>(k) * n * ldm + j;
-        for (int lr = u; lr <= j; lr += G) ss = fma(col[lr * ldm], col[lr * ldm], ss);
+      {
+        int k = k0, lr = l0;
+        for (int e = u; e < ne; e += G) {
+          const double v = M[(k * n + lr) * ldm + j];
+          ss = fma(v, v, ss);
+          lr += dr;
+          k += dq;
+          if (lr >= len) {
+            lr -= len;
+            ++k;
+          }
+        }
       }
       for (int o = G >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(gmask, ss, o);
       const double alpha = M[j * ldm + j];
@@ -205,10 +220,17 @@ __global__ void __launch_bounds__(1024) k_tree_up(const double* X, int64_t rows,
         scal = 1.0 / (alpha - beta);
         tau = (beta - alpha) / beta;
       }
-      // v: the scaled sub-column
-      for (int k = 1; k <= nsub; ++k) {
-        double* col = M + static_cast<size_t>(k) * n * ldm + j;
-        for (int lr = u; lr <= j; lr += G) col[lr * ldm] *= scal;
+      {  // v: the scaled sub-column
+        int k = k0, lr = l0;
+        for (int e = u; e < ne; e += G) {
+          M[(k * n + lr) * ldm + j] *= scal;
+          lr += dr;
+          k += dq;
+          if (lr >= len) {
+            lr -= len;
+            ++k;
+          }
+        }
       }
       if (u == 0) {
         taus[j] = tau;
@@ -220,16 +242,34 @@ __global__ void __launch_bounds__(1024) k_tree_up(const double* X, int64_t rows,
     if (c > j && c < n && tau != 0.0) {
       // w_c = a_jc + v^T a_c over the sub-column rows; a_c -= (tau w_c) v
       double w = 0.0;
-      for (int k = 1; k <= nsub; ++k) {
-        const double* blk = M + static_cast<size_t>(k) * n * ldm;
-        for (int lr = u; lr <= j; lr += G) w = fma(blk[lr * ldm + j], blk[lr * ldm + c], w);
+      {
+        int k = k0, lr = l0;
+        for (int e = u; e < ne; e += G) {
+          const double* row = M + (k * n + lr) * ldm;
+          w = fma(row[j], row[c], w);
+          lr += dr;
+          k += dq;
+          if (lr >= len) {
+            lr -= len;
+            ++k;
+          }
+        }
       }
       for (int o = G >> 1; o > 0; o >>= 1) w += __shfl_xor_sync(gmask, w, o);
       const double tw = tau * (M[j * ldm + c] + w);
       if (u == 0) M[j * ldm + c] -= tw;
-      for (int k = 1; k <= nsub; ++k) {
-        double* blk = M + static_cast<size_t>(k) * n * ldm;
-        for (int lr = u; lr <= j; lr += G) blk[lr * ldm + c] = fma(-tw, blk[lr * ldm + j], blk[lr * ldm + c]);
+      {
+        int k = k0, lr = l0;
+        for (int e = u; e < ne; e += G) {
+          double* row = M + (k * n + lr) * ldm;
+          row[c] = fma(-tw, row[j], row[c]);
+          lr += dr;
+          k += dq;
+          if (lr >= len) {
+            lr -= len;
+            ++k;
+          }
+        }
       }
     }
     __syncthreads();
@@ -316,9 +356,11 @@ cudaError_t launch_tree_up(const double* X, int64_t rows, int n, int f, int64_t 
                            double* Tst, cudaStream_t st) {
   if (!tree_up_fits(n, f)) return cudaErrorInvalidConfiguration;
   const size_t smem = tree_up_smem(n, f);
-  // lanes per column: about 512 threads in all, a power of two from 4 to 32
+  // lanes per column: a power of two from 4 to 32, about two sub-column
+  // blocks per lane (a column's work grows with the node's f - 1 lower
+  // blocks), at most 1024 threads
   int G = 4;
-  while (G < 32 && 2 * G * n <= 512) G *= 2;
+  while (G < 32 && G < 2 * (f - 1) && 2 * G * n <= 1024) G *= 2;
   const int NT = (G * n + 31) / 32 * 32;
   auto fn = Y ? k_tree_up<true> : k_tree_up<false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
