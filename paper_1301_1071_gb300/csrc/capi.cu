@@ -262,13 +262,13 @@ tsqr_status run_tree(const Plan& P, double* R, int64_t ldr, void* work, cudaStre
   for (size_t l = 1; l < L; ++l) {
     const Level& lv = P.levels[l];
     // a node is f stacked triangles: the structured factorisation (tree.cu)
-    // when the node fits one CTA's shared memory
+    // in one CTA's shared memory, else over a cluster of f CTAs
     const int f = static_cast<int>(lv.b / n);
     const cudaError_t e =
-        tree_up_fits(n, f)
-            ? launch_tree_up(S(l - 1), lv.rows, n, f, lv.p, S(l - 1), S(l), T(l), st)
-            : launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, S(l - 1), S(l), T(l), status,
-                              st);
+        tree_up_fits(n, f)      ? launch_tree_up(S(l - 1), lv.rows, n, f, lv.p, S(l - 1), S(l), T(l), st)
+        : tree_up_cl_fits(n, f) ? launch_tree_up_cl(S(l - 1), lv.rows, n, f, lv.p, S(l - 1), S(l), T(l), st)
+                                : launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, S(l - 1),
+                                                  S(l), T(l), status, st);
     if (e != cudaSuccess) return TSQR_ERR_CUDA;
     if (launch_build_t(T(l), lv.p * lv.kt, n, false, st) != cudaSuccess) return TSQR_ERR_CUDA;
   }
@@ -355,10 +355,10 @@ tsqr_status run_r_only(const Plan& P, int esz, const void* X, double* R, void* w
     const Level& lv = P.levels[l];
     const int f = static_cast<int>(lv.b / n);
     const cudaError_t e =
-        tree_up_fits(n, f)
-            ? launch_tree_up(S(l - 1), lv.rows, n, f, lv.p, nullptr, S(l), nullptr, st)
-            : launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, nullptr, S(l), nullptr, status,
-                              st);
+        tree_up_fits(n, f)      ? launch_tree_up(S(l - 1), lv.rows, n, f, lv.p, nullptr, S(l), nullptr, st)
+        : tree_up_cl_fits(n, f) ? launch_tree_up_cl(S(l - 1), lv.rows, n, f, lv.p, nullptr, S(l), nullptr, st)
+                                : launch_local_qr(P.cfg64, S(l - 1), lv.rows, n, lv.b, lv.bt, lv.kt, lv.p, nullptr,
+                                                  S(l), nullptr, status, st);
     if (e != cudaSuccess) return TSQR_ERR_CUDA;
   }
   if (launch_sign_fix(S(L - 1), n, R, n, ctop, status, st) != cudaSuccess) return TSQR_ERR_CUDA;

@@ -24,11 +24,16 @@ cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, i
 // triangular blocks of X (rows x n) -> its R (raw signs) into Rout's block
 // b; with Y (may alias X): the Householder vectors over the node's rows and
 // tau + Gram entries into the node's T slot (Tst); Y == NULL: R only.
-// tree_up_fits: the node fits one CTA's shared memory (else the row-block
-// kernel takes the level).
+// tree_up_fits: the node fits one CTA's shared memory.  tree_up_cl_fits:
+// the node fits a cluster of f CTAs, one block each (launch_tree_up_cl, same
+// outputs).  Neither: the row-block kernel takes the level.
+constexpr int kTreeClMaxF = 8;  // portable cluster size
 bool tree_up_fits(int n, int f);
 cudaError_t launch_tree_up(const double* X, int64_t rows, int n, int f, int64_t p, double* Y, double* Rout,
                            double* Tst, cudaStream_t st);
+bool tree_up_cl_fits(int n, int f);
+cudaError_t launch_tree_up_cl(const double* X, int64_t rows, int n, int f, int64_t p, double* Y, double* Rout,
+                              double* Tst, cudaStream_t st);
 
 // Step-2 down pass of one tree level (binary64): node b's rows of Y (f
 // stacked blocks of n rows, the last node possibly fewer) become its

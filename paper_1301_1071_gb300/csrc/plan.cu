@@ -45,7 +45,6 @@ static int reg_cap(int maxt) {
   int r = 16384 / (32 * w) / 8 * 8;
   return r > 255 ? 255 : r;
 }
-constexpr size_t kSmemPerSM = 233472;  // 228 KB per SM, 1 KB of it reserved per CTA
 
 // Picks the register tile and row-group count.  want_b > 0: the smallest
 // capacity B >= want_b (ties: the taller register tile); want_b == 0: the
@@ -196,10 +195,16 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   if (b0 > m) b0 = m;  // one block
   const int64_t kt0 = b0 <= B0 ? 1 : 1 + (b0 - B0 + bt - 1) / bt;
   if (kt0 > (1 << 20)) return TSQR_ERR_SHAPE;
-  // tree node = f stacked R factors, f >= 2
-  int64_t fmax = P.cfg64.B / n;
-  int64_t f = fanout > 0 ? fanout : fmax;
-  if (f < 2 || f > fmax) return TSQR_ERR_SHAPE;
+  // tree node = f stacked R factors, f >= 2: up to the binary64 row-block
+  // tile's rows (fmax), or any f whose node fits one CTA's shared memory or
+  // a cluster of f CTAs.  Default: fmax while a node of 4 triangles fits one
+  // CTA, else (n > 84, where one CTA holds at most 3) nodes of kTreeClMaxF
+  // triangles on clusters: 20,000,000 x 100 has 4 tree levels instead of 10
+  const int64_t fmax = P.cfg64.B / n;
+  const int ni = static_cast<int>(n);
+  const int64_t f = fanout > 0 ? fanout : (fmax >= 4 && tree_up_fits(ni, 4) ? fmax : kTreeClMaxF);
+  if (f < 2 || (f > fmax && !tree_up_fits(ni, static_cast<int>(f)) && !tree_up_cl_fits(ni, static_cast<int>(f))))
+    return TSQR_ERR_SHAPE;
 
   P.prec = prec;
   P.tc3 = prec == TSQR_PREC_TF32X3 && n <= kTcwMaxN;

@@ -11,6 +11,7 @@ namespace tsqr {
 
 constexpr int kNpc = 5;                // columns per thread (register tile width)
 constexpr size_t kSmemMax = 232448;    // 227 KB dynamic shared memory per CTA
+constexpr size_t kSmemPerSM = 233472;  // 228 KB per SM, 1 KB of it reserved per CTA
 constexpr size_t kHeaderBytes = 256;   // status word + padding at the start of work
 
 // Kernel kind of a tall pass: storage / compute types.

@@ -261,24 +261,6 @@ cudaError_t launch_bwd_prep(const double* R, const double* dR, const double* G, 
 constexpr int kJacCl = 8;    // CTAs per cluster (portable cluster size)
 constexpr int kJacNT = 256;  // threads per CTA
 
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-// shared-memory address of the same variable in CTA `rank` of the cluster
-__device__ __forceinline__ uint32_t cluster_map(const void* p, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
-
 struct JacobiSmem {
   int np, npair, nr, ld;
   size_t x, j, part, fin, pc, ps, d, sv, sg, pp, pq, rank, bytes;

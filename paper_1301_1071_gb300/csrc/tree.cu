@@ -81,12 +81,17 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
   const double* Cn = C + (cblocks == 1 ? 0 : node * n * n);
   double* Yn = Y + r0 * n;
   double* B0 = tsm + n * ld;
-  // T (upper triangle; the slot's lower part is not defined) and C
+  // T (upper triangle; the slot's lower part is not defined) and C, copied
+  // asynchronously (every thread's copies in flight at once; the zeros
+  // around them are plain stores)
   for (int idx = tid; idx < n * ld; idx += NT) {
     const int i = idx / ld, c = idx - i * ld;
-    Wb[idx] = (c < n && c >= i) ? Tn[i * n + c] : 0.0;
-    B0[idx] = c < n ? Cn[i * n + c] : 0.0;
+    if (c < n && c >= i) cp_async_8(Wb + idx, Tn + i * n + c);
+    else Wb[idx] = 0.0;
+    if (c < n) cp_async_8(B0 + idx, Cn + i * n + c);
+    else B0[idx] = 0.0;
   }
+  cp_async_wait_all();
   __syncthreads();
   const int g = gt / ncp, cg = gt - g * ncp;
   const bool active = grp < KB;  // every thread of a group has a row pair
@@ -122,9 +127,11 @@ __global__ void __launch_bounds__(MAXT) k_tree_down(double* Y, int64_t rows, int
     if (mine) {
       for (int idx = gt; idx < n * ld; idx += gsz) {
         const int i = idx / ld, c = idx - i * ld;
-        Bb[idx] = (c < n && c >= i) ? Yk[i * n + c] : 0.0;
+        if (c < n && c >= i) cp_async_8(Bb + idx, Yk + i * n + c);
+        else Bb[idx] = 0.0;
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     // every panel of the node has staged these blocks before any overwrites
     // its columns of them (the node's P CTAs are one cluster)
@@ -305,6 +312,173 @@ __global__ void __launch_bounds__(1024) k_tree_up(const double* X, int64_t rows,
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Up pass over a cluster, for nodes of f <= kTreeClMaxF triangles too large
+// for one CTA's shared memory (n > 84 at f = 4): CTA q of the node's cluster
+// holds block q (block 0 = R_1).  The factorisation is the one above with
+// each column's sums split by block and one cluster barrier per column.
+// Column j's vector is v = scal x (x: the column's entries below the pivot,
+// scal = 1 / (alpha - beta)), so every sum it enters can be formed from x
+// before scal is known:
+//   (1) column j's lanes form their block's squared norm of x, every later
+//       column c's lanes their block's dot x^T a_c (block 0 instead: the
+//       pivot alpha and the pivot row's entries a_jc); lane u of a group
+//       stores its group's partial into the receive buffers of CTAs u,
+//       u + G, .. (remote stores), so every CTA receives all f partials;
+//   (2) cluster barrier;
+//   (3) column j's lanes sum the f norm partials they received in a fixed
+//       shuffle order (so every CTA forms the same beta, scal and tau) and
+//       publish the scalars; CTA barrier; every later group sums its dot
+//       partials the same way, w_c = a_jc + scal sum_k x_k^T a_c, and
+//       a_c -= tau w_c v over the group's own rows; CTA barrier (column
+//       j + 1 has been updated).
+// The receive buffers alternate by the parity of j: a CTA refills one only
+// after the next barrier, which every CTA reaches after its reads of it.
+// x is kept unscaled during the loop (no later column reads it) and scaled
+// into v at the end.  The Gram entries of T are summed by block and then
+// over the ranks in order, in chunks of gch rows.  Outputs as k_tree_up.
+// Threads: G = 4 lanes per column, column c = tid / G: few lanes keep the
+// shuffle trees (binary64 adds) short, and with a Gram chunk of 16 rows two
+// CTAs fit an SM (levels of many nodes run in half the waves).
+template <bool WANT_Y>
+__global__ void __launch_bounds__(1024) k_tree_up_cl(const double* X, int64_t rows, int n, int f, double* Y,
+                                                     double* Rout, double* Tst, int G, int gch) {
+  extern __shared__ __align__(16) double usm[];
+  const int ldm = n + 1, ldp = n + 2;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int c = tid / G, u = tid - c * G;
+  const int q = static_cast<int>(cluster_ctarank());
+  const int64_t node = blockIdx.x / f;
+  const int64_t r0 = node * f * n;
+  const int nb = static_cast<int>((rows - r0) / n < f ? (rows - r0) / n : f);
+  const bool lower = q > 0 && q < nb;  // a block below the first (the last node may have fewer)
+  double* M = usm;                     // this CTA's block, row r at M[r * ldm]
+  double* part = M + n * ldm;          // [2][f][n + 2]: partials received from rank r (column c; n: norm, n + 1: alpha)
+  double* taus = part + 2 * f * ldp;   // tau per column
+  double* scals = taus + n;            // 1 / (alpha - beta) per column
+  double* gp = scals + n;              // partial Gram rows, gch x n
+  if (q < nb) {
+    const double* Xb = X + (r0 + static_cast<int64_t>(q) * n) * n;
+    for (int idx = tid; idx < n * n; idx += NT) {
+      const int r = idx / n, cc = idx - r * n;
+      M[r * ldm + cc] = cc >= r ? Xb[idx] : 0.0;
+    }
+  }
+  __syncthreads();
+  cluster_barrier();  // every CTA of the cluster has started (its receive buffers exist)
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
+  for (int j = 0; j < n; ++j) {
+    double* pb = part + (j & 1) * f * ldp;
+    // (1) partials of column j's norm (group j) and of the dots x^T a_c (groups c > j)
+    if (c >= j && c < n) {
+      double s = 0.0;
+      if (lower)
+        for (int lr = u; lr <= j; lr += G) s = fma(M[lr * ldm + j], M[lr * ldm + c], s);
+      for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+      if (q == 0) s = M[j * ldm + c];  // block 0: alpha (c == j) or a_jc
+      for (int r = u; r < f; r += G) st_cluster(cluster_map(pb + q * ldp + (c == j ? n : c), static_cast<uint32_t>(r)), s);
+    }
+    cluster_barrier();
+    // (3) the reflector from the received partials (column j's lanes: one
+    //     sqrt and two divisions per CTA; binary64 division is costly on
+    //     this part), then the update
+    if (c == j) {
+      // ranks >= 1 summed in a fixed order: lane u takes ranks u, u + G, ..,
+      // then a shuffle tree
+      double ss = 0.0;
+      for (int r = u > 0 ? u : G; r < f; r += G) ss += pb[r * ldp + n];
+      for (int o = G >> 1; o > 0; o >>= 1) ss += __shfl_xor_sync(gmask, ss, o);
+      const double alpha = pb[n];  // rank 0's slot for column j
+      const double sigma = sqrt(fma(alpha, alpha, ss));
+      double beta, scal, tau;
+      if (sigma == 0.0) {
+        beta = alpha;
+        scal = 0.0;
+        tau = 0.0;
+      } else {
+        beta = alpha >= 0.0 ? -sigma : sigma;
+        scal = 1.0 / (alpha - beta);
+        tau = (beta - alpha) / beta;
+      }
+      if (u == 0) {
+        taus[j] = tau;
+        scals[j] = scal;
+        if (q == 0) M[j * ldm + j] = beta;
+      }
+    }
+    __syncthreads();
+    const double tau = taus[j];
+    if (c > j && c < n && tau != 0.0) {
+      const double scal = scals[j];
+      double sd = 0.0;
+      for (int r = u > 0 ? u : G; r < f; r += G) sd += pb[r * ldp + c];
+      for (int o = G >> 1; o > 0; o >>= 1) sd += __shfl_xor_sync(gmask, sd, o);
+      const double tw = tau * fma(scal, sd, pb[c]);  // pb[c]: rank 0's a_jc
+      if (q == 0) {
+        if (u == 0) M[j * ldm + c] -= tw;
+      } else if (lower) {
+        const double ts = tw * scal;
+        for (int lr = u; lr <= j; lr += G) M[lr * ldm + c] = fma(-ts, M[lr * ldm + j], M[lr * ldm + c]);
+      }
+    }
+    __syncthreads();  // column j + 1's entries are read by every later group
+  }
+  // v = scal x over the lower blocks
+  if (lower)
+    for (int idx = tid; idx < n * n; idx += NT) {
+      const int r = idx / n, cc = idx - r * n;
+      if (r <= cc) M[r * ldm + cc] *= scals[cc];
+    }
+  __syncthreads();
+  if (q == 0) {
+    double* Rn = Rout + node * n * n;
+    for (int idx = tid; idx < n * n; idx += NT) {
+      const int i = idx / n, cc = idx - i * n;
+      Rn[idx] = cc >= i ? M[i * ldm + cc] : 0.0;
+    }
+  }
+  if constexpr (WANT_Y) {
+    if (q < nb) {
+      double* Yb = Y + (r0 + static_cast<int64_t>(q) * n) * n;
+      for (int idx = tid; idx < n * n; idx += NT) {
+        const int r = idx / n, cc = idx - r * n;
+        Yb[idx] = M[r * ldm + cc];
+      }
+    }
+    // tau and the Gram entries G(i, c) = sum_k sum_{lr <= i} v_i(lr) v_c(lr), i < c
+    double* Tn = Tst + node * n * n;
+    for (int i0 = 0; i0 < n; i0 += gch) {
+      const int nr = n - i0 < gch ? n - i0 : gch;
+      for (int e = tid; e < nr * n; e += NT) {
+        const int i = i0 + e / n, cc = e - (e / n) * n;
+        double g = 0.0;
+        if (lower && cc > i)
+          for (int lr = 0; lr <= i; ++lr) g = fma(M[lr * ldm + i], M[lr * ldm + cc], g);
+        gp[e] = g;
+      }
+      cluster_barrier();
+      for (int e = q * NT + tid; e < nr * n; e += f * NT) {
+        const int i = i0 + e / n, cc = e - (e / n) * n;
+        if (cc < i) continue;
+        double g = taus[i];
+        if (cc > i) {
+          double pr[kTreeClMaxF];
+#pragma unroll
+          for (int r = 0; r < kTreeClMaxF; ++r) pr[r] = r < f ? ld_cluster(cluster_map(gp + e, r)) : 0.0;
+          g = 0.0;
+#pragma unroll
+          for (int r = 0; r < kTreeClMaxF; ++r) g += pr[r];
+        }
+        Tn[i * n + cc] = g;
+      }
+      cluster_barrier();  // gp is refilled by the next chunk (and read until here)
+    }
+  } else {
+    cluster_barrier();  // no CTA leaves while another may still store into its buffers
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_tree_down(double* Y, int64_t rows, int n, int f, int64_t p, const double* T, const double* C,
@@ -367,6 +541,53 @@ cudaError_t launch_tree_up(const double* X, int64_t rows, int n, int f, int64_t 
   if (e != cudaSuccess) return e;
   fn<<<(unsigned)p, NT, smem, st>>>(X, rows, n, f, Y, Rout, Tst, G);
   return cudaGetLastError();
+}
+
+static size_t tree_up_cl_smem(int n, int gch) {
+  return (static_cast<size_t>(n) * (n + 1) + 2 * static_cast<size_t>(kTreeClMaxF) * (n + 2) +
+          2 * static_cast<size_t>(n) + static_cast<size_t>(gch) * n) *
+         sizeof(double);
+}
+
+// Gram rows per chunk of the cluster up pass: 16, fewer where two CTAs per
+// SM would not fit otherwise, at least 8
+static int tree_up_cl_gch(int n) {
+  int g = 16;
+  while (g > 8 && 2 * (tree_up_cl_smem(n, g) + 1024) > kSmemPerSM) g -= 8;
+  return g;
+}
+
+// lanes per column (4; 0: the node's columns exceed 1024 threads)
+static int tree_up_cl_lanes(int n, int) { return 4 * n <= 1024 ? 4 : 0; }
+
+bool tree_up_cl_fits(int n, int f) {
+  return f >= 2 && f <= kTreeClMaxF && tree_up_cl_lanes(n, f) > 0 &&
+         tree_up_cl_smem(n, tree_up_cl_gch(n)) <= kSmemMax;
+}
+
+cudaError_t launch_tree_up_cl(const double* X, int64_t rows, int n, int f, int64_t p, double* Y, double* Rout,
+                              double* Tst, cudaStream_t st) {
+  if (!tree_up_cl_fits(n, f)) return cudaErrorInvalidConfiguration;
+  const int gch = tree_up_cl_gch(n);
+  const size_t smem = tree_up_cl_smem(n, gch);
+  const int G = tree_up_cl_lanes(n, f);
+  const int NT = (G * n + 31) / 32 * 32;
+  auto fn = Y ? k_tree_up_cl<true> : k_tree_up_cl<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(p * f));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(f);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, X, rows, n, f, Y, Rout, Tst, G, gch);
 }
 
 }  // namespace tsqr

@@ -329,3 +329,32 @@ def test_ozaki_launches_include_the_tensor_core_gram(lib):
 
     assert count(4, 25) == count(0, 25) + 1
     assert count(4, 50) == count(0, 50)  # above n = 32: the native binary64 form
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_cluster_tree_fanin(lib, dt):
+    """Tree nodes too large for one CTA's shared memory (n > 84 at four
+    triangles) are factored over a cluster of one CTA per triangle: the
+    default fan-in there is 8 (20,000,000 x 100: 4 tree levels, where two
+    triangles per node gave 10), any fan-in 2..8 is accepted, and 9 (no
+    single-CTA node, no portable cluster) is rejected."""
+    st, info = _plan(lib, 0, 20_000_000, 100, dt)
+    assert st == 0 and info.tree_fanout == 8
+    assert info.tree_levels == len(_tree_levels(info.blocks, 8))
+    for f in (2, 5, 8):
+        st, info = _plan(lib, 0, 2_000_000, 100, dt, block_rows=2000, fanout=f)
+        assert st == 0 and info.tree_fanout == f
+        assert info.tree_levels == len(_tree_levels(info.blocks, f))
+    assert _plan(lib, 0, 2_000_000, 100, dt, block_rows=2000, fanout=9)[0] == 2  # TSQR_ERR_SHAPE
+    # below the cluster range the single-CTA node keeps its larger fan-in
+    st, info = _plan(lib, 0, 8_000_000, 25, dt)
+    assert st == 0 and info.tree_fanout == 25
+
+
+def _tree_levels(p, f):
+    """Node counts of the Alg. 2 tree over p blocks with fan-in f."""
+    out = []
+    while p > 1:
+        p = -(-p // f)
+        out.append(p)
+    return out

@@ -80,6 +80,11 @@ SHAPES = [
     (30_000, 56, 0, 0),       # the wide register tile (8 columns per thread, 50 < n <= 64)
     (25_000, 51, 3000, 0),    # wide tile, padded columns, several tiles per block
     (40_000, 77, 2500, 0),    # 10 columns per thread (n > 64), padded, several tiles per block
+    # n > 84: tree nodes of 8 triangles on a cluster of 8 CTAs (one triangle each)
+    (60_000, 100, 1000, 0),   # 60 blocks: levels of 8, 1 nodes (ragged: 8 x 7 + 4)
+    (60_000, 100, 1000, 5),   # fanout 5 on clusters of 5, ragged levels (12 -> 3 -> 1)
+    (30_000, 100, 1500, 2),   # fanout 2: one CTA per node
+    (45_000, 90, 500, 0),     # 90 blocks, three cluster levels, a node of 2 blocks
     (1_000_003, 25, 0, 0),    # default block height (two tiles per block)
 ]
 

@@ -56,6 +56,8 @@ R_SHAPES = [
     (37, 37, 0, 0, 1.0),           # square
     (60_000, 20, 7001, 0, 1e12),   # blocks of several register tiles
     (30_000, 100, 0, 0, 1e4),      # n = NMAX
+    (60_000, 100, 1000, 0, 1e8),   # cluster tree nodes (8 triangles, one per CTA)
+    (45_000, 90, 500, 6, 1.0),     # clusters of 6, ragged levels
 ]
 
 

@@ -54,6 +54,7 @@ def _run(A, **kw):
     (25_000, 96, 2000, 0),     # wide, several tiles
     (60_000, 100, 0, 0),       # the largest n
     (30_001, 100, 4099, 0),    # ragged last block and last tile
+    (200_000, 100, 2000, 0),   # three cluster tree levels (100 -> 13 -> 2 -> 1 nodes)
 ])
 def test_tf32x3_parity(m, n, b, f):
     A = ti.gaussian(m, n, 3000 + m + n).astype(np.float32)
