@@ -60,7 +60,7 @@ extern "C" {
 typedef enum tsqr_status {
   TSQR_OK = 0,
   TSQR_ERR_ARG = 1,       /* null pointer, bad enum/option value */
-  TSQR_ERR_SHAPE = 2,     /* n < 1, n > TSQR_NMAX, m < n, block_rows out of range */
+  TSQR_ERR_SHAPE = 2,     /* n < 1, n > TSQR_NMAX, m < n, block_rows or tree_fanout out of range */
   TSQR_ERR_ALIGN = 3,     /* a leading dimension != n, or a pointer not 16-byte aligned */
   TSQR_ERR_WORKSPACE = 4, /* work == NULL or work_bytes too small */
   TSQR_ERR_CUDA = 5,      /* a CUDA runtime call or launch failed */
@@ -124,7 +124,14 @@ typedef struct tsqr_opts {
   int64_t block_rows; /* rows per Step-1 row block; 0 = automatic.  Must be >= n.
                          A block taller than one CTA's register tile is factored
                          by that CTA tile by tile (a flat reduction tree). */
-  int32_t tree_fanout; /* R factors merged per Step-2 tree node; 0 = automatic (>= 2) */
+  int32_t tree_fanout; /* R factors merged per Step-2 tree node; 0 = automatic.
+                          >= 2; at most what one CTA's shared memory holds
+                          (f n (n+1) binary64 values) or 8 (a node over a
+                          cluster of f CTAs, one R factor each), else
+                          TSQR_ERR_SHAPE.  Automatic: one CTA per node with
+                          as many R factors as the binary64 register tile has
+                          rows for, where that is at least 4 and 4 fit the
+                          CTA; else 8 per node on a cluster. */
   int32_t sync;        /* 1 = synchronise the stream and return the device status */
   /* Optional stage timing (tsqr_direct, tsqr_svd): NULL, or 4 cudaEvent_t
      handles (as void*) recorded on the stream at the start, after Step 1's
