@@ -26,6 +26,7 @@ def _T():
     (2_500_000, 50, 2000, torch.float32, "native"),
     (2_500_000, 50, 2000, torch.float32, "tf32x3"),
     (2_000_000, 25, 4000, torch.float64, "df64"),
+    (1_500_000, 100, 2000, torch.float32, "tf32x3"),  # 750 blocks: tree nodes on clusters of 8 CTAs
 ])
 def test_host_matches_device_path_bitwise(m, n, b, dtype, prec):
     T = _T()

@@ -30,7 +30,8 @@ def _cuda(a, dtype=torch.float64):
 
 # ------------------------------------------------------------------ SVD ---
 
-@pytest.mark.parametrize("m,n,seed", [(20_000, 10, 1), (5000, 25, 2), (3001, 16, 3), (4000, 50, 4)])
+@pytest.mark.parametrize("m,n,seed", [(20_000, 10, 1), (5000, 25, 2), (3001, 16, 3), (4000, 50, 4),
+                                      (30_000, 100, 5)])  # n = 100: tree nodes on clusters
 def test_svd_parity_f64(m, n, seed):
     A = ti.power_spectrum(m, n, seed)
     U, S, V = _T().svd(_cuda(A))
