@@ -495,6 +495,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       //      and the reflector scalars double-buffered, so nothing is
       //      overwritten before every warp has finished with it.
       int jb3 = 0;  // j mod 3
+      // this warp's next own column jn = cs + c0 CS and its count c0 of own
+      // columns at or left of the pivot, stepped per column (warp-uniform; no
+      // division or modulo by CS in the loop)
+      int jn = cs, c0 = 0;
       for (int j = 0; j < n; ++j) {
         const int jb = j & 1;
         const int jn3 = jb3 == 2 ? 0 : jb3 + 1;
@@ -503,7 +507,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         const T* pcur = piv + jb * NPAD;  // row j (this warp's columns)
         T* pnext = piv + (jb ^ 1) * NPAD;
         T* rcur = red + jb * NW * 32;     // this warp's column sums
-        const bool owner = (cs == j % CS);
+        const bool owner = (j == jn);
+        if (owner) {
+          ++c0;
+          jn += CS;
+        }
         if (j > 0 && !owner) named_bar_sync(1 + jb, NT);
         const T* rf = refl + jb * 8;
         Reflector<T> f;
@@ -520,8 +528,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
           if constexpr (GRAM) {
             column_dots(a, xcur, rbase, s);
           } else {
-            const int c0a = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
-            with_c0<NPC>(c0a, [&](auto ic) { column_dots_from<decltype(ic)::value>(a, xcur, rbase, s); });
+            with_c0<NPC>(c0, [&](auto ic) { column_dots_from<decltype(ic)::value>(a, xcur, rbase, s); });
           }
           TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
         }
@@ -555,8 +562,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         }
 
         // phase C: trailing update with the look-ahead of column j + 1
-        const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
-        const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
+        const bool own_next = (j + 1 < n) && (j + 1 == jn);
         T* rfn = refl + (jb ^ 1) * 8;
         const int bn = 1 + (jb ^ 1);
         with_c0<NPC>(c0, [&](auto ic) {
@@ -564,9 +570,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
                                                       taus, bn, NT);
         });
         if (j + 1 < n) {
+          // row j + 1 is register row (j + 1) / 32 (warp-uniform) of lane
+          // (j + 1) % 32 (one row group: rbase = lane)
+          const int qn = (j + 1) >> 5;
 #pragma unroll
           for (int q = 0; q < QH; ++q)
-            if (rbase + 32 * q == j + 1) {
+            if (q == qn && lane == ((j + 1) & 31)) {
 #pragma unroll
               for (int c = 0; c < NPC; ++c) pnext[cs + c * CS] = a[q][c];
             }
