@@ -517,6 +517,7 @@ constexpr int kGmShift = 17;    // P = sum_d D_d 2^(8 (7-d) - kGmShift) fits 63 
 constexpr int kGmRegions = 8;   // accumulator regions e = j + t <= 7
 constexpr int kGmTmemCols = 256;
 constexpr int kGmPart = 33;     // row stride of the epilogue's partial sums (8-byte words)
+constexpr int kGmEntries = (kGmMaxN * kGmMaxN + kGmThreads - 1) / kGmThreads;  // Gram entries per thread
 
 static_assert(4 * 32 * kGmPart * 8 <= 2 * 128 * kGmK * 2, "the partial sums fit the two digit buffers");
 struct GramOzSmem {
@@ -583,6 +584,15 @@ __global__ void __launch_bounds__(kGmThreads, 2)
   }
   if (warp == 0) tc_alloc(tslot, kGmTmemCols);
   for (int idx = tid; idx < nn; idx += kGmThreads) gacc[idx] = 0.0;
+  // this thread's entries of the n x n Gram: pr = tid + e kGmThreads = i n + c
+  // (past n x n: i = c = 0, never an entry above the diagonal)
+  int ei[kGmEntries], ec[kGmEntries];
+#pragma unroll
+  for (int e = 0; e < kGmEntries; ++e) {
+    const int pr = tid + e * kGmThreads;
+    ei[e] = pr < nn ? pr / n : 0;
+    ec[e] = pr < nn ? pr - (pr / n) * n : 0;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -761,12 +771,18 @@ __global__ void __launch_bounds__(kGmThreads, 2)
         tc_ld_x8(ta + 8, w2);
         tc_wait_ld();
         const int sh = kGmBits * (kGmDigits - 1 - (e + q)) - kGmShift;
+        if (sh >= 0) {  // warp-uniform: one shift direction per region
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const long long D0 = static_cast<long long>(__float2int_rz(__uint_as_float(v[i])));
-          const long long D1 = static_cast<long long>(__float2int_rz(__uint_as_float(w2[i])));
-          acc[i] += sh >= 0 ? (D0 << sh) : (D0 >> -sh);
-          acc[8 + i] += sh >= 0 ? (D1 << sh) : (D1 >> -sh);
+          for (int i = 0; i < 8; ++i) {
+            acc[i] += static_cast<long long>(__float2int_rz(__uint_as_float(v[i]))) << sh;
+            acc[8 + i] += static_cast<long long>(__float2int_rz(__uint_as_float(w2[i]))) << sh;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            acc[i] += static_cast<long long>(__float2int_rz(__uint_as_float(v[i]))) >> -sh;
+            acc[8 + i] += static_cast<long long>(__float2int_rz(__uint_as_float(w2[i]))) >> -sh;
+          }
         }
       }
 #pragma unroll
@@ -775,9 +791,10 @@ __global__ void __launch_bounds__(kGmThreads, 2)
     tc_fence_before();
     __syncthreads();  // partial sums complete; tensor memory read
     tc_fence_after();
-    for (int pr = tid; pr < nn; pr += kGmThreads) {
-      const int i = pr / n, c = pr % n;
-      if (c > i) {
+#pragma unroll
+    for (int e = 0; e < kGmEntries; ++e) {
+      const int pr = tid + e * kGmThreads, i = ei[e], c = ec[e];
+      if (c > i) {  // entries past n x n have c = i = 0
         const long long P = part[i * kGmPart + c] + part[(32 + i) * kGmPart + c] +
                             part[(64 + i) * kGmPart + c] + part[(96 + i) * kGmPart + c];
         if (P != 0) gacc[pr] += oz_scaled(P, cexp[i] + cexp[c] - 2099);
@@ -787,10 +804,13 @@ __global__ void __launch_bounds__(kGmThreads, 2)
     if (last_of_tile) {
       __syncthreads();
       double* Tout = Tst + (static_cast<int64_t>(blockIdx.x) * kt + t) * nn;
-      for (int pr = tid; pr < nn; pr += kGmThreads) {
-        const int i = pr / n, c = pr % n;
-        if (c > i) Tout[pr] = gacc[pr];
-        gacc[pr] = 0.0;
+#pragma unroll
+      for (int e = 0; e < kGmEntries; ++e) {
+        const int pr = tid + e * kGmThreads;
+        if (pr < nn) {
+          if (ec[e] > ei[e]) Tout[pr] = gacc[pr];
+          gacc[pr] = 0.0;
+        }
       }
     }
     __syncthreads();  // part (over the digit buffer) and gacc are free again

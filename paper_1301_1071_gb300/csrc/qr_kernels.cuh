@@ -599,8 +599,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         }
       }
     } else {
+      // this warp's next own column jn and its count c0 of own columns at or
+      // left of the pivot, stepped per column (as in the look-ahead loop)
+      int jn = cs, c0 = 0;
       for (int j = 0; j < n; ++j) {
         const int jb = j & 1;
+        const bool own_j = (j == jn);
+        if (own_j) {
+          ++c0;
+          jn += CS;
+        }
         const T* xcur = xbuf + jb * B;          // x_j (column j, current values)
         T* xnext = xbuf + (jb ^ 1) * B;         // x_{j+1}
         const T* pcur = piv + jb * NPAD;        // row j
@@ -614,7 +622,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         //      column j, published before its dot products so that its scalar
         //      sequence overlaps the other warps' phase A
         Reflector<T> f;
-        const bool owner = (rg == 0) && (cs == j % CS);
+        const bool owner = (rg == 0) && own_j;
         if (owner) {
           if (lane == 0) {
             T Sj = T(0);
@@ -689,9 +697,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         }
 
         // ---- phase C: trailing update, v_j, publish x_{j+1}; pivot row = R row j
-        const int c0 = (j >= cs) ? (j - cs) / CS + 1 : 0;  // warp-uniform
-        const bool own_j = (cs == j % CS);
-        const bool own_next = (j + 1 < n) && (cs == (j + 1) % CS);
+        const bool own_next = (j + 1 < n) && (j + 1 == jn);
         with_c0<NPC>(c0, [&](auto ic) {
           tile_update<decltype(ic)::value, NPC, R>(a, d, xcur, xnext, j, rbase, own_j, own_next, f.scal, nnext + rg);
         });
@@ -729,9 +735,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
       //      written: the Gram entries come from k_gram_oz.
       {
         double* Tout = Tst + (static_cast<int64_t>(blockIdx.x) * kt + t) * n * n;
-        for (int idx = tid; idx < n * n; idx += NT) {
-          const int i = idx / n, kk = idx % n;
-          if (GRAM ? kk >= i : kk == i) Tout[idx] = static_cast<double>(kk > i ? gram[idx] : taus[i]);
+        if constexpr (GRAM) {
+          // row i by a warp, its entries kk >= i by the lanes (no division)
+          for (int i = warp; i < n; i += NW)
+            for (int kk = i + lane; kk < n; kk += 32)
+              Tout[i * n + kk] = static_cast<double>(kk > i ? gram[i * n + kk] : taus[i]);
+        } else {
+          for (int i = tid; i < n; i += NT) Tout[i * n + i] = static_cast<double>(taus[i]);
         }
       }
       __syncthreads();
