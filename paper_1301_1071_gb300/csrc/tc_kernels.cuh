@@ -777,6 +777,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nrb = (n + kTcwRB - 1) / kTcwRB, ncb = (n + kTcwCB - 1) / kTcwCB;
   const bool wblk = tid < nrb * ncb;
   const int kk0 = (tid / ncb) * kTcwRB, c0b = (tid % ncb) * kTcwCB;
+  const float inv_n = 1.0f / static_cast<float>(n);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -871,11 +872,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int idx = tid + e * kTcThreads;
           tv[e] = idx < nn ? __ldg(Tb + idx) : 0.0;
         }
+        // entry idx = kk n + i, kk = floor((idx + 1/2) / n) in binary32 (exact:
+        // idx < 10^4 and the quotient lies at least 1/(2n) from an integer)
 #pragma unroll
         for (int e = 0; e < kTcwMaxE; ++e) {
           const int idx = tid + e * kTcThreads;
           if (idx < nn) {
-            const int kk = idx / n, i = idx % n;
+            const int kk = __float2int_rz((static_cast<float>(idx) + 0.5f) * inv_n), i = idx - kk * n;
             tts[i * n + kk] = i >= kk ? static_cast<float>(tv[e]) : 0.0f;
           }
         }
