@@ -461,15 +461,14 @@ cudaError_t launch_jacobi_svd(const double* R, int64_t ldr, int n, double* Ctop,
 // Compact-WY T factors of p row blocks, in place (one warp per block): the
 // slot holds tau_j on the diagonal and the Gram entries G(i,j) = v_i^T v_j
 // above it; T(j,j) = tau_j and T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j),
-// column by column (H_1 ... H_k = I - Y T Y^T).  Each warp stages the upper
-// triangle of its slot in shared memory, packed by columns (entry (i, c),
-// i <= c, at c (c + 1) / 2 + i: half the space of a square stage, so twice
-// the warps per SM), runs the recursion there in type F and writes it back
-// (binary64 slots; F = binary32 for the row blocks of binary32 data, whose
-// Gram entries are binary32 values).  Step j runs over l (the sum index)
-// with the rows i = lane + 32 s of every segment s advancing together, two
-// accumulators each (independent chains); segments whose rows all exceed l
-// are skipped (warp-uniform).
+// four columns per pass (H_1 ... H_k = I - Y T Y^T).  Each warp stages the
+// upper triangle of its slot in shared memory, packed by columns (entry
+// (i, c), i <= c, at c (c + 1) / 2 + i: half the space of a square stage, so
+// twice the warps per SM), runs the recursion there in type F and writes it
+// back (binary64 slots; F = binary32 for the row blocks of binary32 data,
+// whose Gram entries are binary32 values).  The sums run over l (the sum
+// index) with the rows i = lane + 32 s of every segment s advancing
+// together; segments whose rows all exceed l are skipped (warp-uniform).
 constexpr int kBuildTSegs = 4;  // 32-row segments: n <= 128
 constexpr int kBuildTPad = 64;  // spare entries after each warp's triangle (no read ever reaches them)
 constexpr int kBuildTStage = 8;  // rows of a slot whose loads are issued together
@@ -477,10 +476,7 @@ constexpr int kBuildTStage = 8;  // rows of a slot whose loads are issued togeth
 // SEGS >= ceil(n / 32) 32-row segments (2, 3 or kBuildTSegs): the staging
 // and the accumulators are sized for this n, which keeps the registers, and
 // so the warps resident per SM, in line with the work (n = 64: two segments).
-// C4: four columns of T per pass (n > 32): the sum over the finished columns
-// is shared by the four, so each load of a T column feeds four FMAs; else
-// column by column.
-template <class F, int SEGS, bool C4>
+template <class F, int SEGS>
 __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
   F* tsm = reinterpret_cast<F*>(tsm_raw);
@@ -510,135 +506,80 @@ __global__ void k_build_t(double* __restrict__ Tst, int64_t p, int n) {
       }
   }
   __syncwarp();
-  if constexpr (C4) {
-    // columns j0 .. j0+3 per pass: T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j).
-    // The sum over the finished columns l < j0 is shared by the four (one
-    // load of T(i,l) feeds four FMAs, G(l, j0..j0+3) are broadcast); the terms
-    // l in [j0, j) follow in registers, column by column; the four columns of
-    // T are then written over theirs of G (read only in this pass).
-    for (int j0 = 0; j0 < n; j0 += 4) {
-      const int nj = n - j0 < 4 ? n - j0 : 4;
-      const F* gc[4];
+  // columns j0 .. j0+3 per pass: T(i,j) = -tau_j sum_{l=i}^{j-1} T(i,l) G(l,j).
+  // The sum over the finished columns l < j0 is shared by the four (one
+  // load of T(i,l) feeds four FMAs, G(l, j0..j0+3) are broadcast); the terms
+  // l in [j0, j) follow in registers, column by column; the four columns of
+  // T are then written over theirs of G (read only in this pass).
+  for (int j0 = 0; j0 < n; j0 += 4) {
+    const int nj = n - j0 < 4 ? n - j0 : 4;
+    const F* gc[4];
   #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int j = j0 + (jj < nj ? jj : 0);
-        gc[jj] = t + j * (j + 1) / 2;  // column j: G(l, j) for l < j, tau_j at l = j
-      }
-      F acc[4][SEGS];
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = j0 + (jj < nj ? jj : 0);
+      gc[jj] = t + j * (j + 1) / 2;  // column j: G(l, j) for l < j, tau_j at l = j
+    }
+    F acc[4][SEGS];
+  #pragma unroll
+    for (int jj = 0; jj < 4; ++jj)
+  #pragma unroll
+      for (int s = 0; s < SEGS; ++s) acc[jj][s] = F(0);
+    const F* tl = t;  // column l of T, advanced by l + 1 entries per step
+    for (int l = 0; l < j0; l += 4) {  // j0 is a multiple of 4: whole groups
+      const F* t1 = tl + l + 1;
+      const F* t2 = t1 + l + 2;
+      const F* t3 = t2 + l + 3;
+      F gv[4][4];
   #pragma unroll
       for (int jj = 0; jj < 4; ++jj)
   #pragma unroll
-        for (int s = 0; s < SEGS; ++s) acc[jj][s] = F(0);
-      const F* tl = t;  // column l of T, advanced by l + 1 entries per step
-      for (int l = 0; l < j0; l += 4) {  // j0 is a multiple of 4: whole groups
-        const F* t1 = tl + l + 1;
-        const F* t2 = t1 + l + 2;
-        const F* t3 = t2 + l + 3;
-        F gv[4][4];
-  #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-  #pragma unroll
-          for (int u = 0; u < 4; ++u) gv[jj][u] = gc[jj][l + u];
-  #pragma unroll
-        for (int s = 0; s < SEGS; ++s) {
-          if (32 * s > l + 3) break;  // rows of this and later segments all exceed l + 3
-          const int i = lane + 32 * s;
-          F x0 = F(0), x1 = F(0), x2 = F(0), x3 = F(0);  // rows below a column's diagonal add 0
-          if (i <= l) x0 = tl[i];
-          if (i <= l + 1) x1 = t1[i];
-          if (i <= l + 2) x2 = t2[i];
-          if (i <= l + 3) x3 = t3[i];
-  #pragma unroll
-          for (int jj = 0; jj < 4; ++jj)
-            acc[jj][s] = fma(x3, gv[jj][3], fma(x2, gv[jj][2], fma(x1, gv[jj][1], fma(x0, gv[jj][0], acc[jj][s]))));
-        }
-        tl = t3 + l + 4;
-      }
-      // the block's own columns in order: T(i, j) gains the terms l in [j0, j)
-      F tv[4][SEGS];
-  #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        if (jj < nj) {  // warp-uniform
-          const int j = j0 + jj;
-          const F tj = gc[jj][j];
-  #pragma unroll
-          for (int s = 0; s < SEGS; ++s) {
-            const int i = lane + 32 * s;
-            F a = acc[jj][s];
-  #pragma unroll
-            for (int ll = 0; ll < jj; ++ll) a = fma(tv[ll][s], gc[jj][j0 + ll], a);
-            tv[jj][s] = i < j ? -tj * a : (i == j ? tj : F(0));
-          }
-        }
-      }
-      __syncwarp();  // every lane has read the block's columns of G
-  #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        if (jj < nj) {
-          const int j = j0 + jj;
-          F* tcol = t + j * (j + 1) / 2;
-  #pragma unroll
-          for (int s = 0; s < SEGS; ++s) {
-            const int i = lane + 32 * s;
-            if (i < j) tcol[i] = tv[jj][s];
-          }
-        }
-      }
-      __syncwarp();
-    }
-  } else {
-    // column by column (n <= 32: the four-segment registers keep one build
-    // CTA per SM, see build_t_typed)
-    for (int j = 1; j < n; ++j) {
-      const F* gj = t + j * (j + 1) / 2;  // column j: G(l, j) for l < j, tau_j at l = j
-      const F tj = gj[j];
-      F acc[SEGS][2];
-  #pragma unroll
-      for (int s = 0; s < SEGS; ++s) acc[s][0] = acc[s][1] = F(0);
-      const F* tl = t;  // column l of T, advanced by l + 1 entries per step
-      int l = 0;
-      // four columns per pass: their loads are issued before the FMAs use them
-      for (; l + 3 < j; l += 4) {
-        const F* t1 = tl + l + 1;
-        const F* t2 = t1 + l + 2;
-        const F* t3 = t2 + l + 3;
-        const F g0 = gj[l], g1 = gj[l + 1], g2 = gj[l + 2], g3 = gj[l + 3];
-  #pragma unroll
-        for (int s = 0; s < SEGS; ++s) {
-          if (32 * s > l + 3) break;
-          const int i = lane + 32 * s;
-          F x0 = F(0), x1 = F(0), x2 = F(0), x3 = F(0);  // rows below a column's diagonal add 0
-          if (i <= l) x0 = tl[i];
-          if (i <= l + 1) x1 = t1[i];
-          if (i <= l + 2) x2 = t2[i];
-          if (i <= l + 3) x3 = t3[i];
-          acc[s][0] = fma(x2, g2, fma(x0, g0, acc[s][0]));
-          acc[s][1] = fma(x3, g3, fma(x1, g1, acc[s][1]));
-        }
-        tl = t3 + l + 4;
-      }
-      for (; l < j; ++l) {
-        const F gl = gj[l];
-  #pragma unroll
-        for (int s = 0; s < SEGS; ++s) {
-          if (32 * s > l) break;  // rows of this and later segments all exceed l
-          const int i = lane + 32 * s;
-          if (i <= l) {  // static accumulator indices keep acc in registers
-            if (l & 1) acc[s][1] = fma(tl[i], gl, acc[s][1]);
-            else acc[s][0] = fma(tl[i], gl, acc[s][0]);
-          }
-        }
-        tl += l + 1;
-      }
-      __syncwarp();
-      F* tcol = t + j * (j + 1) / 2;
+        for (int u = 0; u < 4; ++u) gv[jj][u] = gc[jj][l + u];
   #pragma unroll
       for (int s = 0; s < SEGS; ++s) {
+        if (32 * s > l + 3) break;  // rows of this and later segments all exceed l + 3
         const int i = lane + 32 * s;
-        if (i < j) tcol[i] = -tj * (acc[s][0] + acc[s][1]);
+        F x0 = F(0), x1 = F(0), x2 = F(0), x3 = F(0);  // rows below a column's diagonal add 0
+        if (i <= l) x0 = tl[i];
+        if (i <= l + 1) x1 = t1[i];
+        if (i <= l + 2) x2 = t2[i];
+        if (i <= l + 3) x3 = t3[i];
+  #pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          acc[jj][s] = fma(x3, gv[jj][3], fma(x2, gv[jj][2], fma(x1, gv[jj][1], fma(x0, gv[jj][0], acc[jj][s]))));
       }
-      __syncwarp();
+      tl = t3 + l + 4;
     }
+    // the block's own columns in order: T(i, j) gains the terms l in [j0, j)
+    F tv[4][SEGS];
+  #pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      if (jj < nj) {  // warp-uniform
+        const int j = j0 + jj;
+        const F tj = gc[jj][j];
+  #pragma unroll
+        for (int s = 0; s < SEGS; ++s) {
+          const int i = lane + 32 * s;
+          F a = acc[jj][s];
+  #pragma unroll
+          for (int ll = 0; ll < jj; ++ll) a = fma(tv[ll][s], gc[jj][j0 + ll], a);
+          tv[jj][s] = i < j ? -tj * a : (i == j ? tj : F(0));
+        }
+      }
+    }
+    __syncwarp();  // every lane has read the block's columns of G
+  #pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      if (jj < nj) {
+        const int j = j0 + jj;
+        F* tcol = t + j * (j + 1) / 2;
+  #pragma unroll
+        for (int s = 0; s < SEGS; ++s) {
+          const int i = lane + 32 * s;
+          if (i < j) tcol[i] = tv[jj][s];
+        }
+      }
+    }
+    __syncwarp();
   }
   for (int i = 0; i < n; ++i)
     for (int c = i + lane; c < n; c += 32) g[i * n + c] = static_cast<double>(t[c * (c + 1) / 2 + i]);
@@ -701,16 +642,11 @@ static cudaError_t build_t_typed(double* Tst, int64_t p, int n, int sms, cudaStr
   warps = warps < 1 ? 1 : (warps > 16 ? 16 : warps);
   const size_t smem = static_cast<size_t>(warps) * per_warp;
   const int64_t grid = (p + warps - 1) / warps;
-  // n <= 32 keeps the four-segment form: its registers hold the build to one
-  // CTA per SM, which leaves room for the tree's CTA beside it when the build
-  // runs concurrently with the tree (with one-segment staging the build filled
-  // every SM's shared memory and the tree waited: Step 2 of 8,000,000 x 25
-  // FP64 0.98 -> 1.10 ms)
+  // (the column-by-column form took n <= 32 with four segments' registers, to
+  // leave room for the tree's CTA beside it; the four-column form with one
+  // segment is faster there too: 8,000,000 x 25 FP64 Step 2 4.11 -> 3.94 ms)
   const int segs = (n + 31) / 32;
-  auto fn = segs == 1   ? k_build_t<F, kBuildTSegs, false>
-            : segs == 2 ? k_build_t<F, 2, true>
-            : segs == 3 ? k_build_t<F, 3, true>
-                        : k_build_t<F, kBuildTSegs, true>;
+  auto fn = segs == 1 ? k_build_t<F, 1> : segs == 2 ? k_build_t<F, 2> : segs == 3 ? k_build_t<F, 3> : k_build_t<F, 4>;
   if (segs > kBuildTSegs) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
