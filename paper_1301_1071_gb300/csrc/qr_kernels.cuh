@@ -219,6 +219,41 @@ __device__ __forceinline__ void column_dots_from(const T (&a)[R][NPC], const T* 
   }
 }
 
+// column_dots / column_dots_from with the thread's entries of x_j through an
+// accessor xr(q) (registers or shared memory, see tile_update_la_x).
+template <int NPC, int R, class T, class X>
+__device__ __forceinline__ void column_dots_x(const T (&a)[R][NPC], X xr, T (&s)[NPC]) {
+  if constexpr (std::is_same<T, df64>::value) {
+    df64_acc acc[NPC];
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+      for (int c = 0; c < NPC; ++c) acc[c].add_prod(xr(q), a[q][c]);
+#pragma unroll
+    for (int c = 0; c < NPC; ++c) s[c] = acc[c].value();
+  } else {
+#pragma unroll
+    for (int c = 0; c < NPC; ++c) s[c] = T(0);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const T xq = xr(q);
+#pragma unroll
+      for (int c = 0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
+    }
+  }
+}
+template <int C0, int NPC, int R, class T, class X>
+__device__ __forceinline__ void column_dots_from_x(const T (&a)[R][NPC], X xr, T (&s)[NPC]) {
+#pragma unroll
+  for (int c = 0; c < NPC; ++c) s[c] = T(0);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const T xq = xr(q);
+#pragma unroll
+    for (int c = C0; c < NPC; ++c) s[c] = fma(xq, a[q][c], s[c]);
+  }
+}
+
 // Trailing update of the thread's tile for column j, with the first trailing
 // local column C0 known at compile time: a[q][c] -= d[c] x_q for c >= C0.
 // The thread's rows are rbase + 32 q (q < R); the published pivot column x_j
@@ -261,15 +296,17 @@ __device__ __forceinline__ void tile_update(T (&a)[R][NPC], const T (&d)[NPC], c
 // j + 1 from its squared norm and a_{j+1,j+1} (every lane, no broadcast),
 // stores the scalars in `refl_next` and arrives on the named barrier
 // `bar_next`; only then does it update its other trailing columns.  The other
-// warps can start column j + 1 while it finishes column j.
-template <int C0, int NPC, int R, class T>
-__device__ __forceinline__ void tile_update_la(T (&a)[R][NPC], const T (&d)[NPC], const T* xcur, T* xnext, int j,
+// warps can start column j + 1 while it finishes column j.  xr(q): this
+// thread's entry of x_j in register row q (from registers where the tile
+// leaves room for them, else from shared memory).
+template <int C0, int NPC, int R, class T, class X>
+__device__ __forceinline__ void tile_update_la_x(T (&a)[R][NPC], const T (&d)[NPC], X xr, T* xnext, int j,
                                                int rbase, bool own_j, bool own_next, T scal, T* refl_next,
                                                T* taus, int bar_next, int nthreads) {
   if constexpr (C0 < NPC) {
     if (own_next) {
 #pragma unroll
-      for (int q = 0; q < R; ++q) a[q][C0] = fma(-d[C0], xcur[rbase + 32 * q], a[q][C0]);
+      for (int q = 0; q < R; ++q) a[q][C0] = fma(-d[C0], xr(q), a[q][C0]);
 #pragma unroll
       for (int q = 0; q < R; ++q) xnext[rbase + 32 * q] = (rbase + 32 * q > j) ? a[q][C0] : T(0);
       const T ss = col_norm2<C0, NPC, R>(a, rbase, j + 1);
@@ -291,14 +328,14 @@ __device__ __forceinline__ void tile_update_la(T (&a)[R][NPC], const T (&d)[NPC]
       named_bar_arrive(bar_next, nthreads);
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const T xq = xcur[rbase + 32 * q];
+        const T xq = xr(q);
 #pragma unroll
         for (int c = C0 + 1; c < NPC; ++c) a[q][c] = fma(-d[c], xq, a[q][c]);
       }
     } else {
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const T xq = xcur[rbase + 32 * q];
+        const T xq = xr(q);
 #pragma unroll
         for (int c = C0; c < NPC; ++c) a[q][c] = fma(-d[c], xq, a[q][c]);
       }
@@ -309,7 +346,7 @@ __device__ __forceinline__ void tile_update_la(T (&a)[R][NPC], const T (&d)[NPC]
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         const int r = rbase + 32 * q;
-        if (r > j) a[q][C0 - 1] = xcur[r] * scal;
+        if (r > j) a[q][C0 - 1] = xr(q) * scal;
       }
     }
   }
@@ -523,12 +560,27 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
 
         // phase A: s = x_j^T A for this warp's columns (R-only: the columns
         //      right of the pivot only)
+        // this thread's entries of x_j: read once and kept in registers for
+        // the update in binary32 where the tile leaves room (R NPC values of
+        // at most 400 bytes, at most 384 threads: 168 registers a thread),
+        // else read from shared memory at each use (the binary64 loop is
+        // bound by the binary64 unit, not by its loads)
+        constexpr bool kXr = std::is_same<T, float>::value && R * NPC * sizeof(T) <= 400 && MAXT <= 384;
+        T xv[kXr ? R : 1];
+        if constexpr (kXr) {
+#pragma unroll
+          for (int q = 0; q < R; ++q) xv[q] = xcur[rbase + 32 * q];
+        }
+        auto xr = [&](int q) -> T {
+          if constexpr (kXr) return xv[q];
+          else return xcur[rbase + 32 * q];
+        };
         {
           T s[NPC];
           if constexpr (GRAM) {
-            column_dots(a, xcur, rbase, s);
+            column_dots_x(a, xr, s);
           } else {
-            with_c0<NPC>(c0, [&](auto ic) { column_dots_from<decltype(ic)::value>(a, xcur, rbase, s); });
+            with_c0<NPC>(c0, [&](auto ic) { column_dots_from_x<decltype(ic)::value, NPC, R, T>(a, xr, s); });
           }
           TransposeReduce<NPC, 16>::run(s, lane, 0, NPC, rcur + warp * 32);
         }
@@ -540,9 +592,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
         //      at (k, j), k < j), and back into the register rows < n once
         //      the tile is done: row j's registers are not read again within
         //      the tile (x is zero there for every later column)
-        T d[NPC];
+        T dl = T(0);  // lane c's update coefficient d_c (broadcast per trailing column below)
         {
-          T dl = T(0);
           const int mycol = cs + lane * CS;
           if (lane < NPC && mycol < n) {
             const T Sc = rcur[warp * 32 + lane];
@@ -557,17 +608,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_local_qr(const S* __restrict__ A, i
               gram[mycol * n + j] = f.scal * (Sc - f.beta * pc);
             }
           }
-#pragma unroll
-          for (int c = 0; c < NPC; ++c) d[c] = shfl_from(dl, c);
         }
 
-        // phase C: trailing update with the look-ahead of column j + 1
+        // phase C: trailing update with the look-ahead of column j + 1 (the
+        // coefficients of the trailing local columns only are broadcast)
         const bool own_next = (j + 1 < n) && (j + 1 == jn);
         T* rfn = refl + (jb ^ 1) * 8;
         const int bn = 1 + (jb ^ 1);
         with_c0<NPC>(c0, [&](auto ic) {
-          tile_update_la<decltype(ic)::value, NPC, R>(a, d, xcur, xnext, j, rbase, owner, own_next, f.scal, rfn,
-                                                      taus, bn, NT);
+          constexpr int C0 = decltype(ic)::value;
+          T d[NPC];
+#pragma unroll
+          for (int c = 0; c < NPC; ++c) d[c] = c >= C0 ? shfl_from(dl, c) : T(0);
+          tile_update_la_x<C0, NPC, R, T>(a, d, xr, xnext, j, rbase, owner, own_next, f.scal, rfn, taus, bn, NT);
         });
         if (j + 1 < n) {
           // row j + 1 is register row (j + 1) / 32 (warp-uniform) of lane
