@@ -95,6 +95,18 @@ def test_against_long_double_mgs(m, n):
     assert _rel(Q, Qm) <= 50 * n * kappa * EPS
 
 
+def test_long_double_mgs_pin_stays_orthonormal_at_high_kappa():
+    # The MGS pin re-orthogonalises every column once ("twice is enough"), so
+    # its Q stays orthonormal to long-double rounding even at kappa 1e12,
+    # where one Gram-Schmidt pass would lose ~kappa * 2^-64 ~ 1e-7.
+    A = ti.conditioned(60, 12, 1e12, 205)
+    Qm, Rm = oracle.mgs_ld(A)
+    e2, _ = oracle.orth_error(Qm)
+    assert e2 <= 1e-14
+    rF, _ = oracle.residual(A, Qm, Rm)
+    assert rF <= 1e-14
+
+
 @pytest.mark.parametrize("m,n,kappa", [(200, 10, 1.0), (500, 25, 1e8), (300, 16, 1e15)])
 def test_library_cross_check(m, n, kappa):
     # numpy's LAPACK QR, sign-normalised: an independent implementation.
@@ -425,6 +437,28 @@ def test_orth_error_known_answer():
     assert e2h <= 4 * EPS
 
 
+def test_orth_error_known_answer_off_diagonal():
+    # A symmetric perturbation with off-diagonal entries: Q = H (I + delta S)
+    # gives Q^TQ - I = 2 delta S + delta^2 S^2 exactly (H^T H = I), so both the
+    # 2-norm and the Frobenius norm (every off-diagonal entry counted twice)
+    # have closed forms.
+    n = 5
+    H = _hadamard(6)[:, :n] / 8.0
+    S = np.array([[0.0, 1.0, 0.0, 0.0, 2.0],
+                  [1.0, 0.0, -1.0, 0.0, 0.0],
+                  [0.0, -1.0, 0.0, 0.5, 0.0],
+                  [0.0, 0.0, 0.5, 0.0, 0.0],
+                  [2.0, 0.0, 0.0, 0.0, 0.0]])
+    delta = 1e-10
+    Q = H @ (np.eye(n) + delta * S)
+    E = 2 * delta * S + delta ** 2 * (S @ S)
+    e2, eF = oracle.orth_error(Q)
+    expect2 = np.max(np.abs(np.linalg.eigvalsh(E)))
+    expectF = np.sqrt(np.sum(E * E))
+    assert abs(e2 - expect2) <= 1e-4 * expect2
+    assert abs(eF - expectF) <= 1e-4 * expectF
+
+
 def test_residual_known_answer():
     A = ti.gaussian(300, 5, 71)
     Q, R = oracle.householder_qr(A)
@@ -439,6 +473,17 @@ def test_gram_dot2_cancellation():
     x = np.array([[1e16], [1.0], [-1e16], [1.0]])
     y = np.ones((4, 1))
     assert oracle.gram_dot2(x, y)[0, 0] == 2.0
+
+
+def test_gram_dot2_keeps_the_product_rounding_error():
+    # a = 1 + 2^-30: a*a = 1 + 2^-29 + 2^-60 rounds to 1 + 2^-29 in binary64,
+    # so a*a - 1*(1 + 2^-29) is exactly 2^-60 but plain FP64 gives 0.  Dot2
+    # recovers the product's rounding error with an FMA (TwoProduct).
+    a = 1.0 + 2.0 ** -30
+    x = np.array([[a], [-1.0]])
+    y = np.array([[a], [1.0 + 2.0 ** -29]])
+    assert float(x[0, 0] * y[0, 0] + x[1, 0] * y[1, 0]) == 0.0
+    assert oracle.gram_dot2(x, y)[0, 0] == 2.0 ** -60
 
 
 @pytest.mark.parametrize("n", [37, 64, 100])
