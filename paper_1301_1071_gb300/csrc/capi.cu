@@ -162,13 +162,17 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   return pa < pb + nb && pb < pa + na;
 }
 
+// An m x n matrix whose byte size at 8 bytes an entry int64 holds (the
+// planner, the overlap checks and the kernels index with it).
+bool rows_fit(int64_t m, int64_t n) { return n >= 1 && m <= INT64_MAX / 8 / n; }
+
 // Shared argument checks of the tall-matrix entry points.
 tsqr_status check_tall(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, const tsqr_opts* o) {
   if (!A) return TSQR_ERR_ARG;
   if (esz_of(dtype) == 0) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(o);
   if (s != TSQR_OK) return s;
-  if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  if (n < 1 || n > TSQR_NMAX || m < n || !rows_fit(m, n)) return TSQR_ERR_SHAPE;
   if (lda != n || !aligned16(A)) return TSQR_ERR_ALIGN;
   return TSQR_OK;
 }
@@ -589,7 +593,7 @@ tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
   if (op == TSQR_OP_ACCURACY) {
-    if (n < 1 || n > TSQR_NMAX || m < 1) return TSQR_ERR_SHAPE;
+    if (n < 1 || n > TSQR_NMAX || m < 1 || !rows_fit(m, n)) return TSQR_ERR_SHAPE;
     *bytes = kHeaderBytes + accuracy_geom(m, static_cast<int>(n)).part_bytes;
     return TSQR_OK;
   }
@@ -634,7 +638,7 @@ tsqr_status tsqr_direct_host(const void* A, int64_t m, int64_t n, int32_t dtype,
   if (stream == copy_stream) return TSQR_ERR_ARG;
   tsqr_status s = check_opts(opts);
   if (s != TSQR_OK) return s;
-  if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  if (n < 1 || n > TSQR_NMAX || m < n || !rows_fit(m, n)) return TSQR_ERR_SHAPE;
   if (!aligned16(dbuf)) return TSQR_ERR_ALIGN;
   const int esz = esz_of(dtype);
   if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
@@ -781,7 +785,7 @@ tsqr_status tsqr_accuracy(const void* A, const void* Q, const double* R, int64_t
                           double* out, void* work, size_t work_bytes, void* stream) {
   const int esz = esz_of(dtype);
   if (!Q || !out || esz == 0 || (A == nullptr) != (R == nullptr)) return TSQR_ERR_ARG;
-  if (n < 1 || n > TSQR_NMAX || m < 1) return TSQR_ERR_SHAPE;
+  if (n < 1 || n > TSQR_NMAX || m < 1 || !rows_fit(m, n)) return TSQR_ERR_SHAPE;
   const size_t need = kHeaderBytes + accuracy_geom(m, static_cast<int>(n)).part_bytes;
   if (!work || !aligned16(work) || work_bytes < need) return TSQR_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -2,6 +2,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <cstdint>
 #include <numeric>
 
 #include "../../include/tsqr.h"
@@ -13,6 +14,21 @@
 namespace tsqr {
 
 static size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Workspace offsets with overflow checks: *ok is cleared when a sum or
+// product does not fit in size_t (only sizes far beyond any device reach it).
+static size_t add_ck(size_t a, size_t b, bool* ok) {
+  if (a > SIZE_MAX - b) { *ok = false; return 0; }
+  return a + b;
+}
+static size_t mul_ck(size_t a, size_t b, bool* ok) {
+  if (b != 0 && a > SIZE_MAX / b) { *ok = false; return 0; }
+  return a * b;
+}
+static size_t al16_ck(size_t x, bool* ok) {
+  if (x > SIZE_MAX - 15) { *ok = false; return 0; }
+  return al16(x);
+}
 
 // Register-tile heights and their thread bounds (must match tiles_f64.h and
 // tiles_f32.h).  Each SM sub-partition holds 16K registers
@@ -149,6 +165,9 @@ int resolve_prec(int prec, int esz, int64_t n) {
 
 int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Plan* plan, int prec, int sms) {
   if (n < 1 || n > TSQR_NMAX || m < n) return TSQR_ERR_SHAPE;
+  // every m x n matrix of the call, at 8 bytes an entry, must have a byte
+  // size that int64 holds (the planner and the kernels index with it)
+  if (m > INT64_MAX / 8 / n) return TSQR_ERR_SHAPE;
   prec = resolve_prec(prec, esz, n);
   if (prec != TSQR_PREC_NATIVE && !(prec == TSQR_PREC_DF64 && esz == 8) && !(prec == TSQR_PREC_TF32X3 && esz == 4) &&
       !(prec == TSQR_PREC_OZAKI && esz == 8))
@@ -242,18 +261,19 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
     l.kt = 1;
     P.levels.push_back(l);
   }
+  bool ok = true;
   size_t o = kHeaderBytes;
   const size_t nn = (size_t)n * n * sizeof(double);
   for (auto& l : P.levels) {
     l.off_S = o;
-    o = al16(o + (size_t)l.p * nn);
+    o = al16_ck(add_ck(o, mul_ck((size_t)l.p, nn, &ok), &ok), &ok);
     l.off_T = o;
-    o = al16(o + (size_t)l.p * l.kt * nn);
+    o = al16_ck(add_ck(o, mul_ck(mul_ck((size_t)l.p, (size_t)l.kt, &ok), nn, &ok), &ok), &ok);
   }
   P.off_ctop = o;
-  o = al16(o + nn);
+  o = al16_ck(add_ck(o, nn, &ok), &ok);
   P.off_small = o;
-  o = al16(o + kSmallSlots * nn);
+  o = al16_ck(add_ck(o, kSmallSlots * nn, &ok), &ok);
   P.bytes = o;
   GramGeom g = gram_geom(m, (int)n, esz);
   P.gram_chunk = g.chunk;
@@ -265,6 +285,7 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
   P.off_gsmall = o;
   o = al16(o + kSmallSlots * nn);
   P.bytes_gram = o;
+  if (!ok) return TSQR_ERR_SHAPE;
   *plan = P;
   return TSQR_OK;
 }

@@ -358,3 +358,37 @@ def _tree_levels(p, f):
         p = -(-p // f)
         out.append(p)
     return out
+
+
+@pytest.mark.parametrize("m", [2**62, 2**63 - 1, 2**61 // 25 + 1])
+def test_unrepresentable_sizes_rejected(lib, m):
+    """A problem whose m x n x 8 bytes int64 cannot hold is a shape error for
+    every op (no workspace size that wrapped around)."""
+    for op in range(9):
+        for dt in (0, 1):
+            st, _ = _ws(lib, op, m, 25, dt)
+            assert st == 2, (op, dt)
+    st, _ = _plan(lib, 0, m, 25, 0)
+    assert st == 2
+
+
+def test_plan_and_workspace_invariants_over_sizes(lib):
+    """Over sizes from tiny to far beyond any device (m up to 2^50 rows),
+    explicit and automatic block heights and fan-ins: the row blocks cover
+    the m rows, the tree ends in one R, and the workspace of every op that
+    stacks R factors holds at least one binary64 n x n R per row block."""
+    for m in [1, 99, 100, 101, 10**6, 2**31 + 5, 10**12, 2**50]:
+        for n in [1, 7, 25, 100]:
+            for b in [0, n, 1000, 2**40]:
+                for f in [0, 2, 3, 2**20]:
+                    for dt in (0, 1):
+                        st, info = _plan(lib, 0, m, n, dt, block_rows=b, fanout=f)
+                        if st != 0:
+                            assert st in (2,), (m, n, b, f, dt, st)
+                            continue
+                        assert info.blocks >= 1 and info.blocks * info.block_rows >= m
+                        assert (info.blocks - 1) * info.block_rows < m
+                        assert (info.tree_levels == 0) == (info.blocks == 1)
+                        for op in (0, 1, 3, 6, 7):
+                            s2, w = _ws(lib, op, m, n, dt, b, f)
+                            assert s2 == 0 and w >= info.blocks * n * n * 8, (op, m, n, b, f, dt)
