@@ -290,7 +290,10 @@ tsqr_status tsqr_direct_static(const void* A, int64_t m, int64_t n, int64_t lda,
  *  - stream, copy_stream: two different CUDA streams of the current device.
  *    On return everything is enqueued and `stream` has been made to wait for
  *    the last copy on `copy_stream`: synchronising `stream` (or opts->sync = 1,
- *    which also returns the device status) completes the call.
+ *    which also returns the device status) completes the call.  An error
+ *    returned after work was queued on `copy_stream` also leaves `stream`
+ *    waiting for it (or, where that cannot be enqueued, the call waits for
+ *    `copy_stream` on the host before returning).
  *  - The call creates and releases 2 x chunks + 1 CUDA events (no device
  *    memory); chunks <= 8.
  *  - Errors: as tsqr_direct (TSQR_ERR_ARG also for a NULL pointer or equal

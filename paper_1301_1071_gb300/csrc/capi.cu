@@ -405,6 +405,25 @@ struct HostEvents {
   }
 };
 
+// Once work is queued on the copy stream, every exit (an error included)
+// records `ev` on it and makes `st` wait for it (or, if that cannot be
+// enqueued, waits for the copy stream on the host), so that the call stays
+// ordered on `stream` alone.
+struct CopyJoin {
+  cudaStream_t cst = nullptr, st = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool armed = false;
+  cudaError_t join() {
+    if (!armed) return cudaSuccess;
+    armed = false;
+    cudaError_t e = cudaEventRecord(ev, cst);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    if (e != cudaSuccess) cudaStreamSynchronize(cst);
+    return e;
+  }
+  ~CopyJoin() { join(); }
+};
+
 tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, double* Rh, char* dbuf, void* work,
                             cudaStream_t st, cudaStream_t cst) {
   const int n = static_cast<int>(P.n);
@@ -427,6 +446,11 @@ tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, 
   // the copy stream must not overwrite dbuf before earlier work on `stream` is done
   TSQR_CUDA(cudaEventRecord(ev_done, st));
   TSQR_CUDA(cudaStreamWaitEvent(cst, ev_done, 0));
+  CopyJoin join;  // declared after E: joins before the events are released
+  join.cst = cst;
+  join.st = st;
+  join.ev = ev_done;
+  join.armed = true;
   auto chunk_rows = [&](int c, int64_t* b0, int64_t* pcnt, int64_t* r0, int64_t* rows) {
     *b0 = c * pc;
     *pcnt = (l0.p - *b0 < pc) ? l0.p - *b0 : pc;
@@ -469,8 +493,7 @@ tsqr_status run_direct_host(const Plan& P, int chunks, const char* A, char* Qh, 
     TSQR_CUDA(cudaStreamWaitEvent(cst, ev_q[c], 0));
     TSQR_CUDA(cudaMemcpyAsync(Qh + r0 * row_bytes, Y, rows * row_bytes, cudaMemcpyDeviceToHost, cst));
   }
-  TSQR_CUDA(cudaEventRecord(ev_done, cst));
-  TSQR_CUDA(cudaStreamWaitEvent(st, ev_done, 0));
+  TSQR_CUDA(join.join());
   return TSQR_OK;
 }
 
