@@ -134,6 +134,25 @@ def _check_tall(A: torch.Tensor):
     return m, n
 
 
+def _check_buf(t, shape, dtype, device, name):
+    """Raises unless ``t`` is a contiguous tensor of exactly ``shape`` and
+    ``dtype`` on ``device``: the library reads or writes the whole shape
+    through its pointer and can check neither its size nor its device."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+        raise ValueError(f"{name} must be {tuple(shape)} {dtype}, got {tuple(t.shape)} {t.dtype}")
+    if t.device != torch.device(device):
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
 def _opts(block_rows=0, fanout=0, sync=False, events=None, prec="native") -> Opts:
     o = Opts()
     o.block_rows = int(block_rows)
@@ -200,8 +219,12 @@ def workspace_size(op: int, m: int, n: int, dtype: torch.dtype, block_rows=0, fa
 
 
 def _workspace(op, m, n, dtype, device, block_rows, fanout, work, prec="native"):
+    """The caller's workspace when it is a contiguous buffer on ``device`` of
+    at least the bytes the call needs, else a new one."""
     need = workspace_size(op, m, n, dtype, block_rows, fanout, prec)
-    if work is None or work.numel() < need:
+    if work is not None and (work.device != torch.device(device) or not work.is_contiguous()):
+        raise ValueError(f"work must be a contiguous buffer on {device}, got {work.device}")
+    if work is None or _nbytes(work) < need:
         work = torch.empty(need, dtype=torch.uint8, device=device)
     return work
 
@@ -222,10 +245,14 @@ def direct(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Te
     m, n = _check_tall(A)
     A = A.contiguous()
     lib = load()
-    Q, R = out if out is not None else (torch.empty_like(A), torch.empty(n, n, dtype=torch.float64, device=A.device))
+    if out is not None:
+        Q = _check_buf(out[0], (m, n), A.dtype, A.device, "out[0] (Q)")
+        R = _check_buf(out[1], (n, n), torch.float64, A.device, "out[1] (R)")
+    else:
+        Q, R = torch.empty_like(A), torch.empty(n, n, dtype=torch.float64, device=A.device)
     work = _workspace(OP_DIRECT, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
     o = _opts(block_rows, fanout, events=stage_events, prec=prec)
-    st = lib.tsqr_direct(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, _ptr(work), work.numel(),
+    st = lib.tsqr_direct(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, _ptr(work), _nbytes(work),
                          ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_direct")
     _status(work, "tsqr_direct", check)
@@ -250,6 +277,10 @@ def direct_host(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, out: tupl
         raise ValueError(f"unsupported shape {tuple(A.shape)}: need 1 <= n <= {NMAX} and m >= n")
     A = A.contiguous()
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if dev.type != "cuda":
+        raise ValueError(f"device must be a CUDA device, got {dev}")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
     with torch.cuda.device(dev):
         return _direct_host(A, m, n, dev, block_rows, fanout, out, dbuf, work, copy_stream, check, prec)
 
@@ -257,17 +288,20 @@ def direct_host(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, out: tupl
 def _direct_host(A, m, n, dev, block_rows, fanout, out, dbuf, work, copy_stream, check, prec):
     lib = load()
     if out is not None:
-        Q, R = out
+        Q = _check_buf(out[0], (m, n), A.dtype, "cpu", "out[0] (Q)")
+        R = _check_buf(out[1], (n, n), torch.float64, "cpu", "out[1] (R)")
     else:
         Q = torch.empty(m, n, dtype=A.dtype, pin_memory=True)
         R = torch.empty(n, n, dtype=torch.float64, pin_memory=True)
     if dbuf is None:
         dbuf = torch.empty(m, n, dtype=A.dtype, device=dev)
+    else:
+        _check_buf(dbuf, (m, n), A.dtype, dev, "dbuf")
     work = _workspace(OP_DIRECT_HOST, m, n, A.dtype, dev, block_rows, fanout, work, prec)
     cs = copy_stream if copy_stream is not None else torch.cuda.Stream(device=dev)
     o = _opts(block_rows, fanout, prec=prec)
     st = lib.tsqr_direct_host(_ptr(A), m, n, _dtype_code(A), _ptr(Q), _ptr(R), _ptr(dbuf), _ptr(work),
-                              work.numel(), ctypes.byref(o), _stream(dev), ctypes.c_void_p(cs.cuda_stream))
+                              _nbytes(work), ctypes.byref(o), _stream(dev), ctypes.c_void_p(cs.cuda_stream))
     _raise(st, "tsqr_direct_host")
     _status(work, "tsqr_direct_host", check)
     return Q, R
@@ -303,7 +337,7 @@ def svd(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tenso
     work = _workspace(OP_SVD, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
     o = _opts(block_rows, fanout, prec=prec)
     st = lib.tsqr_svd(_ptr(A), m, n, n, _dtype_code(A), _ptr(U), n, _ptr(S), _ptr(V), n, _ptr(work),
-                      work.numel(), ctypes.byref(o), _stream(A.device))
+                      _nbytes(work), ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_svd")
     _status(work, "tsqr_svd", check)
     return U, S, V
@@ -319,7 +353,7 @@ def r(A: torch.Tensor, block_rows: int = 0, fanout: int = 0, work: torch.Tensor 
     R = torch.empty(n, n, dtype=torch.float64, device=A.device)
     work = _workspace(OP_R, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
     o = _opts(block_rows, fanout, prec=prec)
-    st = lib.tsqr_r(_ptr(A), m, n, n, _dtype_code(A), _ptr(R), n, _ptr(work), work.numel(), ctypes.byref(o),
+    st = lib.tsqr_r(_ptr(A), m, n, n, _dtype_code(A), _ptr(R), n, _ptr(work), _nbytes(work), ctypes.byref(o),
                     _stream(A.device))
     _raise(st, "tsqr_r")
     _status(work, "tsqr_r", check)
@@ -338,7 +372,7 @@ def svd_values(A: torch.Tensor, want_v: bool = True, block_rows: int = 0, fanout
     V = torch.empty(n, n, dtype=torch.float64, device=A.device) if want_v else None
     work = _workspace(OP_SVD_VALUES, m, n, A.dtype, A.device, block_rows, fanout, work, prec)
     o = _opts(block_rows, fanout, prec=prec)
-    st = lib.tsqr_svd_values(_ptr(A), m, n, n, _dtype_code(A), _ptr(S), _ptr(V), n, _ptr(work), work.numel(),
+    st = lib.tsqr_svd_values(_ptr(A), m, n, n, _dtype_code(A), _ptr(S), _ptr(V), n, _ptr(work), _nbytes(work),
                              ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_svd_values")
     _status(work, "tsqr_svd_values", check)
@@ -356,7 +390,7 @@ def cholqr(A: torch.Tensor, refine: int = 0, work: torch.Tensor | None = None, c
     work = _workspace(OP_CHOLQR, m, n, A.dtype, A.device, 0, 0, work)
     o = _opts()
     st = lib.cholqr(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, int(refine), _ptr(work),
-                    work.numel(), ctypes.byref(o), _stream(A.device))
+                    _nbytes(work), ctypes.byref(o), _stream(A.device))
     _raise(st, "cholqr")
     _status(work, "cholqr", check)
     return Q, R
@@ -374,7 +408,7 @@ def indirect_refine(A: torch.Tensor, refine: int = 1, block_rows: int = 0, fanou
     work = _workspace(OP_INDIRECT, m, n, A.dtype, A.device, block_rows, fanout, work)
     o = _opts(block_rows, fanout)
     st = lib.tsqr_indirect_refine(_ptr(A), m, n, n, _dtype_code(A), _ptr(Q), n, _ptr(R), n, int(refine),
-                                  _ptr(work), work.numel(), ctypes.byref(o), _stream(A.device))
+                                  _ptr(work), _nbytes(work), ctypes.byref(o), _stream(A.device))
     _raise(st, "tsqr_indirect_refine")
     _status(work, "tsqr_indirect_refine", check)
     return Q, R
@@ -386,15 +420,15 @@ def backward(Q: torch.Tensor, R: torch.Tensor, dQ: torch.Tensor | None, dR: torc
     """QR adjoint: dA = (dQ + Q copyltu(M)) R^{-T}, M = R dR^T - dQ^T Q."""
     m, n = _check_tall(Q)
     Q = Q.contiguous()
-    R = R.to(torch.float64).contiguous()
-    dQ = None if dQ is None else dQ.to(Q.dtype).contiguous()
-    dR = None if dR is None else dR.to(torch.float64).contiguous()
+    R = _check_buf(R.to(torch.float64).contiguous(), (n, n), torch.float64, Q.device, "R")
+    dQ = None if dQ is None else _check_buf(dQ.to(Q.dtype).contiguous(), (m, n), Q.dtype, Q.device, "dQ")
+    dR = None if dR is None else _check_buf(dR.to(torch.float64).contiguous(), (n, n), torch.float64, Q.device, "dR")
     lib = load()
     dA = torch.empty_like(Q)
     work = _workspace(OP_BACKWARD, m, n, Q.dtype, Q.device, 0, 0, work)
     o = _opts()
     st = lib.tsqr_backward(_ptr(Q), _ptr(R), _ptr(dQ), _ptr(dR), m, n, _dtype_code(Q), _ptr(dA), _ptr(work),
-                           work.numel(), ctypes.byref(o), _stream(Q.device))
+                           _nbytes(work), ctypes.byref(o), _stream(Q.device))
     _raise(st, "tsqr_backward")
     _status(work, "tsqr_backward", check)
     return dA
@@ -408,19 +442,24 @@ def accuracy(Q: torch.Tensor, R: torch.Tensor | None = None, A: torch.Tensor | N
     A and R ``res_F`` = ||A - QR||_F/||A||_F and ``res_2`` = ||A - QR||_2/||R||_2.
     The 2-norms of the symmetric n x n results are taken on the host."""
     import numpy as np
+    if not Q.is_cuda or Q.dim() != 2:
+        raise ValueError("Q must be a 2-D CUDA tensor (there is no CPU path)")
     m, n = Q.shape
     if (A is None) != (R is None):
         raise ValueError("give both A and R, or neither")
     Q = Q.contiguous()
+    _dtype_code(Q)
     if A is not None:
-        A = A.to(Q.dtype).contiguous()
-        R = R.to(torch.float64).contiguous()
+        A = _check_buf(A.to(Q.dtype).contiguous(), (m, n), Q.dtype, Q.device, "A")
+        R = _check_buf(R.to(torch.float64).contiguous(), (n, n), torch.float64, Q.device, "R")
     lib = load()
     out = torch.empty(3 * n * n + 2, dtype=torch.float64, device=Q.device)
     need = workspace_size(OP_ACCURACY, m, n, Q.dtype)
-    if work is None or work.numel() < need:
+    if work is not None and (work.device != Q.device or not work.is_contiguous()):
+        raise ValueError(f"work must be a contiguous buffer on {Q.device}, got {work.device}")
+    if work is None or _nbytes(work) < need:
         work = torch.empty(need, dtype=torch.uint8, device=Q.device)
-    st = lib.tsqr_accuracy(_ptr(A), _ptr(Q), _ptr(R), m, n, _dtype_code(Q), _ptr(out), _ptr(work), work.numel(),
+    st = lib.tsqr_accuracy(_ptr(A), _ptr(Q), _ptr(R), m, n, _dtype_code(Q), _ptr(out), _ptr(work), _nbytes(work),
                            _stream(Q.device))
     _raise(st, "tsqr_accuracy")
     _status(work, "tsqr_accuracy", True)

@@ -392,3 +392,33 @@ def test_plan_and_workspace_invariants_over_sizes(lib):
                         for op in (0, 1, 3, 6, 7):
                             s2, w = _ws(lib, op, m, n, dt, b, f)
                             assert s2 == 0 and w >= info.blocks * n * n * 8, (op, m, n, b, f, dt)
+
+
+def test_binding_rejects_caller_buffers_of_the_wrong_shape_dtype_or_device():
+    """The library can check neither the size nor the device of a buffer it is
+    given a pointer to, so the binding refuses mis-sized, mistyped,
+    non-contiguous or misplaced caller buffers before any call (host-only)."""
+    import torch
+    import paper_1301_1071_gb300 as T
+    cpu = torch.device("cpu")
+    ok = torch.empty(30, 4, dtype=torch.float64)
+    assert T._check_buf(ok, (30, 4), torch.float64, cpu, "Q") is ok
+    with pytest.raises(ValueError, match="must be"):
+        T._check_buf(torch.empty(29, 4, dtype=torch.float64), (30, 4), torch.float64, cpu, "Q")
+    with pytest.raises(ValueError, match="must be"):
+        T._check_buf(torch.empty(30, 4, dtype=torch.float32), (30, 4), torch.float64, cpu, "Q")
+    with pytest.raises(ValueError, match="contiguous"):
+        T._check_buf(torch.empty(4, 30, dtype=torch.float64).t(), (30, 4), torch.float64, cpu, "Q")
+    with pytest.raises(ValueError, match="on cuda"):
+        T._check_buf(ok, (30, 4), torch.float64, torch.device("cuda", 0), "Q")
+    with pytest.raises(TypeError):
+        T._check_buf(ok.numpy(), (30, 4), torch.float64, cpu, "Q")
+    # a workspace that is not on the call's device is refused, not used
+    with pytest.raises(ValueError, match="work"):
+        T._workspace(T.OP_DIRECT, 1000, 10, torch.float64, torch.device("cuda", 0), 0, 0,
+                     torch.empty(1 << 20, dtype=torch.uint8))
+    # work_bytes counts bytes, whatever the workspace tensor's dtype
+    assert T._nbytes(torch.empty(10, dtype=torch.float64)) == 80
+    # no CPU path: the accuracy checker refuses a host Q
+    with pytest.raises(ValueError, match="CUDA"):
+        T.accuracy(torch.empty(30, 4, dtype=torch.float64))
