@@ -112,6 +112,8 @@ cudaError_t launch_form_q(const KernelCfg& k, const void* Y, int64_t m, int n, i
 namespace {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+// NULL (an optional argument left out) or 16-byte aligned
+bool aligned16_or_null(const void* p) { return p == nullptr || aligned16(p); }
 
 // SM count of the current device (the planner's default block height
 // depends on it); the GB300 value when no device answers.
@@ -640,7 +642,7 @@ tsqr_status tsqr_direct(const void* A, int64_t m, int64_t n, int64_t lda, int32_
   tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
   if (s != TSQR_OK) return s;
   if (!Q || !R) return TSQR_ERR_ARG;
-  if (ldq != n || ldr != n || !aligned16(Q)) return TSQR_ERR_ALIGN;
+  if (ldq != n || ldr != n || !aligned16(Q) || !aligned16(R)) return TSQR_ERR_ALIGN;
   const int esz = esz_of(dtype);
   if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
   Plan P;
@@ -685,7 +687,7 @@ tsqr_status tsqr_svd(const void* A, int64_t m, int64_t n, int64_t lda, int32_t d
   tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
   if (s != TSQR_OK) return s;
   if (!U || !S || !V) return TSQR_ERR_ARG;
-  if (ldu != n || ldv != n || !aligned16(U)) return TSQR_ERR_ALIGN;
+  if (ldu != n || ldv != n || !aligned16(U) || !aligned16(S) || !aligned16(V)) return TSQR_ERR_ALIGN;
   const int esz = esz_of(dtype);
   if (overlaps(A, (size_t)m * n * esz, U, (size_t)m * n * esz)) return TSQR_ERR_ARG;
   Plan P;
@@ -705,7 +707,7 @@ tsqr_status tsqr_r(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dty
   tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
   if (s != TSQR_OK) return s;
   if (!R) return TSQR_ERR_ARG;
-  if (ldr != n) return TSQR_ERR_ALIGN;
+  if (ldr != n || !aligned16(R)) return TSQR_ERR_ALIGN;
   Plan P;
   TSQR_TRY(plan_for(TSQR_OP_R, m, n, dtype, opts, work_bytes, work, &P));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -720,7 +722,7 @@ tsqr_status tsqr_svd_values(const void* A, int64_t m, int64_t n, int64_t lda, in
   tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
   if (s != TSQR_OK) return s;
   if (!S) return TSQR_ERR_ARG;
-  if (V && ldv != n) return TSQR_ERR_ALIGN;
+  if ((V && ldv != n) || !aligned16(S) || !aligned16_or_null(V)) return TSQR_ERR_ALIGN;
   Plan P;
   TSQR_TRY(plan_for(TSQR_OP_SVD_VALUES, m, n, dtype, opts, work_bytes, work, &P));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -742,7 +744,7 @@ tsqr_status cholqr(const void* A, int64_t m, int64_t n, int64_t lda, int32_t dty
   tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
   if (s != TSQR_OK) return s;
   if (!Q || !R || refine_steps < 0) return TSQR_ERR_ARG;
-  if (ldq != n || ldr != n || !aligned16(Q)) return TSQR_ERR_ALIGN;
+  if (ldq != n || ldr != n || !aligned16(Q) || !aligned16(R)) return TSQR_ERR_ALIGN;
   const int esz = esz_of(dtype);
   if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
   Plan P;
@@ -777,7 +779,7 @@ tsqr_status tsqr_indirect_refine(const void* A, int64_t m, int64_t n, int64_t ld
   tsqr_status s = check_tall(A, m, n, lda, dtype, opts);
   if (s != TSQR_OK) return s;
   if (!Q || !R || refine_steps < 0) return TSQR_ERR_ARG;
-  if (ldq != n || ldr != n || !aligned16(Q)) return TSQR_ERR_ALIGN;
+  if (ldq != n || ldr != n || !aligned16(Q) || !aligned16(R)) return TSQR_ERR_ALIGN;
   const int esz = esz_of(dtype);
   if (overlaps(A, (size_t)m * n * esz, Q, (size_t)m * n * esz)) return TSQR_ERR_ARG;
   Plan P;
@@ -809,6 +811,7 @@ tsqr_status tsqr_accuracy(const void* A, const void* Q, const double* R, int64_t
   const int esz = esz_of(dtype);
   if (!Q || !out || esz == 0 || (A == nullptr) != (R == nullptr)) return TSQR_ERR_ARG;
   if (n < 1 || n > TSQR_NMAX || m < 1 || !rows_fit(m, n)) return TSQR_ERR_SHAPE;
+  if (!aligned16(Q) || !aligned16(out) || !aligned16_or_null(A) || !aligned16_or_null(R)) return TSQR_ERR_ALIGN;
   const size_t need = kHeaderBytes + accuracy_geom(m, static_cast<int>(n)).part_bytes;
   if (!work || !aligned16(work) || work_bytes < need) return TSQR_ERR_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -824,7 +827,7 @@ tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const 
   tsqr_status s = check_tall(Q, m, n, n, dtype, opts);
   if (s != TSQR_OK) return s;
   if (!R || !dA) return TSQR_ERR_ARG;
-  if (!aligned16(dA) || (dQ && !aligned16(dQ))) return TSQR_ERR_ALIGN;
+  if (!aligned16(dA) || !aligned16_or_null(dQ) || !aligned16(R) || !aligned16_or_null(dR)) return TSQR_ERR_ALIGN;
   Plan P;
   TSQR_TRY(plan_for(TSQR_OP_BACKWARD, m, n, dtype, opts, work_bytes, work, &P));
   cudaStream_t st = static_cast<cudaStream_t>(stream);

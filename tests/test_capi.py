@@ -181,6 +181,7 @@ stand_in_addresses = pytest.mark.skipif(_gpu_visible(), reason="stand-in device 
     (dict(lda=11), 3),                    # lda != n
     (dict(A=_P8), 3),                     # A not 16-byte aligned
     (dict(ldr=9), 3),                     # ldr != n
+    (dict(R=_P8), 3),                     # R not 16-byte aligned
     (dict(work=None), 4),                 # no workspace
     (dict(work_bytes=64), 4),             # workspace too small
     (dict(prec=2), 1),                    # TF32X3 on FP64 data
@@ -203,6 +204,8 @@ def test_r_only_rejects_before_any_launch(lib, args, want):
 @pytest.mark.parametrize("args,want", [
     (dict(S=None), 1),                    # NULL S
     (dict(ldv=9), 3),                     # V given with ldv != n
+    (dict(S=_P8), 3),                     # S not 16-byte aligned
+    (dict(V=_P8), 3),                     # V given, not 16-byte aligned
     (dict(n=0), 2),                       # n < 1
     (dict(work=None), 4),                 # no workspace
 ])
