@@ -425,3 +425,28 @@ def test_binding_rejects_caller_buffers_of_the_wrong_shape_dtype_or_device():
     # no CPU path: the accuracy checker refuses a host Q
     with pytest.raises(ValueError, match="CUDA"):
         T.accuracy(torch.empty(30, 4, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("n", [1, 25, 100])
+def test_workspace_beyond_size_t_rejected(lib, n):
+    """A whose bytes int64 holds, in row blocks of n rows: one binary64 R and
+    one T slot per block add up to more than size_t holds, a shape error
+    rather than a wrapped size; a quarter of the rows still plans, with a
+    workspace holding both stacks."""
+    m = (2**63 - 1) // 8 // n
+    for op in (0, 1, 3, 6, 7):
+        st, _ = _ws(lib, op, m, n, 0, block_rows=n)
+        assert st == 2, op
+    st, w = _ws(lib, 0, m // 4, n, 0, block_rows=n)
+    assert st == 0 and w >= 2 * (m // 4 // n) * n * n * 8
+
+
+def test_reserved_option_field_must_be_zero(lib):
+    f = lib.tsqr_workspace_size
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(Opts),
+                  ctypes.POINTER(ctypes.c_size_t)]
+    f.restype = ctypes.c_int
+    out = ctypes.c_size_t(0)
+    assert f(0, 1000, 10, 0, ctypes.byref(Opts(0, 0, 0, None, 0, 1)), ctypes.byref(out)) == 1
+    assert f(0, 1000, 10, 0, ctypes.byref(Opts(0, 0, 0, None, -1, 0)), ctypes.byref(out)) == 1  # prec < 0
+    assert f(0, 1000, 10, 0, ctypes.byref(Opts(0, 0, 0, None, 0, 0)), ctypes.byref(out)) == 0
