@@ -61,7 +61,9 @@ typedef enum tsqr_status {
   TSQR_OK = 0,
   TSQR_ERR_ARG = 1,       /* null pointer, bad enum/option value */
   TSQR_ERR_SHAPE = 2,     /* n < 1, n > TSQR_NMAX, m < n, m n 8 bytes beyond int64, block_rows or
-                             tree_fanout out of range, a workspace size beyond size_t */
+                             tree_fanout out of range, a workspace size beyond size_t, a block
+                             height or a count of row blocks (or of their T slots) beyond
+                             2^31 - 1 */
   TSQR_ERR_ALIGN = 3,     /* a leading dimension != n, or a pointer not 16-byte aligned */
   TSQR_ERR_WORKSPACE = 4, /* work == NULL or work_bytes too small */
   TSQR_ERR_CUDA = 5,      /* a CUDA runtime call or launch failed */

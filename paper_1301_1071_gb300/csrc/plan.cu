@@ -261,6 +261,15 @@ int make_plan(int64_t m, int64_t n, int esz, int64_t block_rows, int fanout, Pla
     l.kt = 1;
     P.levels.push_back(l);
   }
+  // The kernels take a block's height as int and launch one CTA per row
+  // block, per T slot (the T build) or per triangle of a tree node (cluster
+  // nodes): heights and grids beyond int and gridDim.x (2^31 - 1) are shape
+  // errors here rather than truncated launch arguments.
+  if (b0 > INT32_MAX) return TSQR_ERR_SHAPE;
+  for (size_t i = 0; i < P.levels.size(); ++i) {
+    const Level& l = P.levels[i];
+    if (l.p > INT32_MAX / l.kt || (i > 0 && l.p > INT32_MAX / f)) return TSQR_ERR_SHAPE;
+  }
   bool ok = true;
   size_t o = kHeaderBytes;
   const size_t nn = (size_t)n * n * sizeof(double);

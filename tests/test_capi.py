@@ -428,17 +428,37 @@ def test_binding_rejects_caller_buffers_of_the_wrong_shape_dtype_or_device():
 
 
 @pytest.mark.parametrize("n", [1, 25, 100])
-def test_workspace_beyond_size_t_rejected(lib, n):
-    """A whose bytes int64 holds, in row blocks of n rows: one binary64 R and
-    one T slot per block add up to more than size_t holds, a shape error
-    rather than a wrapped size; a quarter of the rows still plans, with a
-    workspace holding both stacks."""
+def test_int64_limit_in_blocks_of_n_rows_rejected(lib, n):
+    """A whose bytes int64 just holds, in row blocks of n rows: its R and T
+    stacks alone would pass size_t, and its blocks gridDim.x; a shape error
+    for every op that stacks R factors, not a wrapped size."""
     m = (2**63 - 1) // 8 // n
     for op in (0, 1, 3, 6, 7):
         st, _ = _ws(lib, op, m, n, 0, block_rows=n)
         assert st == 2, op
-    st, w = _ws(lib, 0, m // 4, n, 0, block_rows=n)
-    assert st == 0 and w >= 2 * (m // 4 // n) * n * n * 8
+
+
+def test_grid_and_block_height_limits(lib):
+    """The kernels launch one CTA per row block (per T slot in the T build)
+    and take a block's height as int: more than 2^31 - 1 blocks or T slots,
+    or a block taller than 2^31 - 1 rows, is a shape error rather than a
+    truncated launch; below each limit the problem plans."""
+    lim = 2**31 - 1
+    n = 25
+    assert _ws(lib, 0, (lim + 1) * n, n, 0, block_rows=n)[0] == 2   # 2^31 row blocks
+    st, w = _ws(lib, 0, 2**30 * n, n, 0, block_rows=n)               # 2^30 row blocks
+    assert st == 0 and w >= 2 * 2**30 * n * n * 8
+    # double-float, n = 1: blocks of up to 2^20 register tiles of 4,096 rows
+    # reach past 2^31 rows (a 2^33-row A is 64 GB)
+    assert _plan(lib, 0, 2**33, 1, 0, block_rows=2**31 + 2**20, prec=1)[0] == 2
+    st, info = _plan(lib, 0, 2**33, 1, 0, block_rows=lim, prec=1)
+    assert st == 0 and info.block_rows == lim and info.tiles_per_block > 1
+    # binary64, n = 25: tall blocks whose T slots (one per tile) pass 2^31 - 1
+    st, info = _plan(lib, 0, 2**29, 25, 0, block_rows=2**28)
+    kt = info.tiles_per_block
+    assert st == 0 and info.blocks == 2 and kt > 1
+    assert _plan(lib, 0, (lim // kt + 1) * 2**28, 25, 0, block_rows=2**28)[0] == 2
+    assert _plan(lib, 0, (lim // kt) * 2**28, 25, 0, block_rows=2**28)[0] == 0
 
 
 def test_reserved_option_field_must_be_zero(lib):
