@@ -215,6 +215,76 @@ def cpu_baseline(A_host: np.ndarray, target_s: float = 10.0, max_rows: int = 8_0
             "host_cores": cores}
 
 
+def _timed_rows(fn, make, target_s: float, rows0: int, max_rows: int):
+    """rows/s of fn(sample) on make(rows) rows, the sample grown until one
+    call takes about target_s / 3 seconds (at most max_rows rows)."""
+    rows = min(rows0, max_rows)
+    while True:
+        X = make(rows)
+        t0 = time.perf_counter()
+        fn(X)
+        t = time.perf_counter() - t0
+        if t >= target_s / 3 or rows >= max_rows:
+            return rows, t
+        rows = int(min(max_rows, rows * target_s / max(t, 1e-3)))
+
+
+def cpu_config_baselines(target_s: float = 3.0):
+    """The oracle on all host cores at each of the other configurations (a
+    bounded row sample of each, drawn with the configuration's recipe on the
+    host; the device runs draw theirs on the device), the serial oracle at
+    the 100,000 x 10 configuration, numpy's LAPACK QR (a library CPU
+    baseline, comparison only) and the peak resident memory.  Each entry
+    reports an error instead of raising."""
+    import resource
+
+    import oracle
+    cores = os.cpu_count() or 1
+    out = {}
+
+    def gram_pair(A):
+        Q, R = oracle.householder_qr(A)
+        g = np.random.default_rng(ti.SEED_GRAD)
+        oracle.qr_backward(Q, R, g.standard_normal(A.shape), np.triu(g.standard_normal((A.shape[1], A.shape[1]))))
+
+    entries = [
+        ("small_100kx10", 100_000, lambda r: ti.gaussian(100_000, 10, ti.SEED_SMALL, rows=r), oracle.householder_qr,
+         "thin QR (Q and R)"),
+        ("mixed_50Mx50_upcast", 50_000_000,
+         lambda r: ti.column_scaled(r, 50, 1e-4, ti.SEED_MIXED).astype(np.float32).astype(np.float64),
+         oracle.householder_qr, "thin QR (Q and R) of the FP32 matrix upcast"),
+        ("svd_20Mx100", 20_000_000, lambda r: ti.power_spectrum(20_000_000, 100, ti.SEED_SVD, rows=r), oracle.svd,
+         "SVD via thin QR and the SVD of R"),
+        ("grad_4Mx64", 4_000_000, lambda r: ti.gaussian(4_000_000, 64, ti.SEED_GRAD, rows=r), gram_pair,
+         "thin QR + adjoint"),
+    ]
+    for name, m_full, make, fn, what in entries:
+        try:
+            oracle.set_num_threads(cores)
+            rows, t = _timed_rows(fn, make, target_s, 20_000, m_full)
+            e = {"value": rows / t, "unit": "rows/s", "cores": cores, "kind": "oracle", "op": what,
+                 "sample": f"first {rows:,} rows of the {m_full:,}-row configuration, {t:.2f} s"}
+            if name == "small_100kx10":
+                oracle.set_num_threads(1)
+                rows1, t1 = _timed_rows(fn, make, target_s, 20_000, m_full)
+                e["serial"] = {"value": rows1 / t1, "unit": "rows/s", "cores": 1,
+                               "sample": f"first {rows1:,} rows, one thread, {t1:.2f} s"}
+            out[name] = e
+        except Exception as ex:  # reported, not fatal
+            out[name] = {"error": f"{type(ex).__name__}: {ex}"}
+        finally:
+            oracle.set_num_threads(cores)
+    try:
+        make = lambda r: ti.conditioned(8_000_000, 25, 1e15, ti.SEED_SWEEP, rows=r)
+        rows, t = _timed_rows(lambda X: np.linalg.qr(X, mode="reduced"), make, target_s, 100_000, 8_000_000)
+        out["numpy_lapack_qr_8Mx25"] = {"value": rows / t, "unit": "rows/s", "kind": "library (comparison only)",
+                                        "sample": f"first {rows:,} rows x 25 of the sweep matrix, {t:.2f} s"}
+    except Exception as ex:  # reported, not fatal
+        out["numpy_lapack_qr_8Mx25"] = {"error": f"{type(ex).__name__}: {ex}"}
+    out["memory_peak_mb"] = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 1024.0
+    return out
+
+
 def run_reference(args, w):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -418,6 +488,10 @@ def main():
         line["configs"] = configs
     if not args.no_extras and rank == 0:
         line["cpu_baseline"] = cpu_baseline(A_host)
+        try:
+            line["cpu_baseline"]["configs"] = cpu_config_baselines()
+        except Exception as e:  # reported, not fatal
+            line["cpu_baseline"]["configs"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
