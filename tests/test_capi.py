@@ -470,3 +470,17 @@ def test_reserved_option_field_must_be_zero(lib):
     assert f(0, 1000, 10, 0, ctypes.byref(Opts(0, 0, 0, None, 0, 1)), ctypes.byref(out)) == 1
     assert f(0, 1000, 10, 0, ctypes.byref(Opts(0, 0, 0, None, -1, 0)), ctypes.byref(out)) == 1  # prec < 0
     assert f(0, 1000, 10, 0, ctypes.byref(Opts(0, 0, 0, None, 0, 0)), ctypes.byref(out)) == 0
+
+
+@pytest.mark.parametrize("dt,esz,precs", [(0, 8, (0, 1, 3, 4)), (1, 4, (0, 2, 3))])
+def test_default_blocks_start_on_16_byte_boundaries(lib, dt, esz, precs):
+    """The planner's own block heights keep every row block (and, with its
+    tile heights, every register tile) starting on a 16-byte boundary, so
+    that Step 1 and Step 3 stage them by bulk copies rather than the plain
+    loads they fall back to for an unaligned start."""
+    for n in range(1, 101):
+        for m in (100_000, 1_000_003, 8_000_000, 50_000_000):
+            for prec in precs:
+                st, info = _plan(lib, 0, m, n, dt, prec=prec)
+                if st == 0 and info.blocks > 1:
+                    assert (info.block_rows * n * esz) % 16 == 0, (n, m, prec, info.block_rows)
