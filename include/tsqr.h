@@ -261,9 +261,10 @@ tsqr_status tsqr_backward(const void* Q, const double* R, const void* dQ, const 
  *  - Every GPU that loads the library holds the array until the process exits.
  *  - The first call on each device (with that device current) looks up the
  *    array's device address; make that first call before any stream capture.
- *  - All calls share the one array: calls that overlap on the GPU (different
- *    streams, host threads or processes' concurrent kernels on the same
- *    device) race and give undefined results.  Order them on one stream.
+ *  - All calls of one process on one device share the one array: calls that
+ *    overlap on the GPU (issued on different streams, or from different host
+ *    threads) race and give undefined results.  Order them on one stream.
+ *    (Each process's CUDA context holds its own copy of the array.)
  *  - The status word lives in the array and is cleared at every call; pass
  *    opts->sync = 1 to get a data-dependent error as the return value.
  */
