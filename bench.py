@@ -471,11 +471,15 @@ def main():
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
     }
 
-    if not args.no_extras and rank == 0:
+    # The extras (other precision modes, comparators, the other
+    # configurations, the CPU oracle) run on single-GPU runs only: under
+    # torchrun every rank's GPU would stay held while rank 0 ran them.
+    extras_on = not args.no_extras and rank == 0 and ws == 1
+    if extras_on:
         others = [p for p in (("native", "df64", "ozaki") if elem == 8 else ("native", "tf32x3"))
                   if p != resolved]
         line["extras"] = extras(T, torch, A, n, m, dev, other_precs=others, prec=args.prec)
-    if not args.no_extras and rank == 0:
+    if extras_on:
         del Q, work, dbuf, work_h
         torch.cuda.empty_cache()
         is_sweep = args.workload == "sweep" and not args.m
@@ -486,7 +490,7 @@ def main():
         torch.cuda.empty_cache()
         configs.update(config_extras(T, torch, dev))
         line["configs"] = configs
-    if not args.no_extras and rank == 0:
+    if extras_on:
         line["cpu_baseline"] = cpu_baseline(A_host)
         try:
             line["cpu_baseline"]["configs"] = cpu_config_baselines()
