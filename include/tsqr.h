@@ -147,7 +147,12 @@ typedef struct tsqr_opts {
 
 /*
  * Workspace bytes needed by `op` for an m x n matrix of `dtype` under `opts`
- * (NULL = defaults).  Host-only; launches nothing.
+ * (NULL = defaults).  Host-only; launches nothing.  The workspace holds what
+ * the paper's MapReduce passes keep on disk between steps: the stacked R
+ * factors of every Step-2 level (Sec. III-B, III-C), the compact-WY T
+ * factors and the coefficient blocks Q2 (no call of the paper corresponds).
+ * Errors: TSQR_ERR_ARG (NULL bytes, unknown op or dtype, bad opts),
+ * TSQR_ERR_SHAPE (as the op's entry point).
  */
 tsqr_status tsqr_workspace_size(int32_t op, int64_t m, int64_t n, int32_t dtype,
                                 const tsqr_opts* opts, size_t* bytes);
@@ -330,7 +335,10 @@ tsqr_status tsqr_accuracy(const void* A, const void* Q, const double* R, int64_t
 
 /*
  * Number of kernel launches one call of `op` makes for this shape and opts
- * (refine_steps applies to TSQR_OP_CHOLQR / TSQR_OP_INDIRECT).  Host-only.
+ * (refine_steps applies to TSQR_OP_CHOLQR / TSQR_OP_INDIRECT).  Host-only;
+ * a measurement aid with no counterpart in the paper.  Errors as
+ * tsqr_workspace_size (TSQR_ERR_ARG also for NULL launches or
+ * refine_steps < 0).
  */
 tsqr_status tsqr_launch_count(int32_t op, int64_t m, int64_t n, int32_t dtype, const tsqr_opts* opts,
                               int32_t refine_steps, int32_t* launches);
@@ -365,11 +373,15 @@ tsqr_status tsqr_plan_query(int32_t op, int64_t m, int64_t n, int32_t dtype, con
 
 /*
  * Synchronises `stream` and returns the device status word of the last call
- * that used `work` (TSQR_OK if it succeeded).
+ * that used `work` (TSQR_OK if it succeeded).  A boundary utility with no
+ * counterpart in the paper.  work: that call's workspace (device); stream:
+ * the stream the call was issued on.  Returns TSQR_ERR_ARG for a NULL work
+ * and TSQR_ERR_CUDA when the read-back or the synchronisation fails.
  */
 tsqr_status tsqr_read_status(const void* work, void* stream);
 
-/* Static, human-readable name of a status code. */
+/* Static, human-readable name of a status code (never NULL; an unknown
+ * code gives "unknown tsqr_status").  No counterpart in the paper. */
 const char* tsqr_status_string(int32_t status);
 
 #ifdef __cplusplus
