@@ -392,6 +392,14 @@ def test_plan_and_workspace_invariants_over_sizes(lib):
                         assert info.blocks >= 1 and info.blocks * info.block_rows >= m
                         assert (info.blocks - 1) * info.block_rows < m
                         assert (info.tree_levels == 0) == (info.blocks == 1)
+                        # Alg. 2: each level merges tree_fanout R factors per node
+                        levels, nodes = 0, info.blocks
+                        while nodes > 1:
+                            nodes = -(-nodes // info.tree_fanout)
+                            levels += 1
+                        assert info.tree_levels == levels, (m, n, b, f, dt)
+                        if f:
+                            assert info.blocks == 1 or info.tree_fanout == f
                         for op in (0, 1, 3, 6, 7):
                             s2, w = _ws(lib, op, m, n, dt, b, f)
                             assert s2 == 0 and w >= info.blocks * n * n * 8, (op, m, n, b, f, dt)
