@@ -492,3 +492,38 @@ def test_default_blocks_start_on_16_byte_boundaries(lib, dt, esz, precs):
                 st, info = _plan(lib, 0, m, n, dt, prec=prec)
                 if st == 0 and info.blocks > 1:
                     assert (info.block_rows * n * esz) % 16 == 0, (n, m, prec, info.block_rows)
+
+
+@stand_in_addresses
+def test_invalid_arguments_never_reach_a_launch(lib):
+    """Seeded random argument combinations for tsqr_direct and tsqr_r: with
+    no GPU, a call whose host checks pass ends in a failed launch
+    (TSQR_ERR_CUDA), so every combination with an invalid argument must be
+    refused with its own code before that point."""
+    import random
+    P, I64, I32, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+    fd = lib.tsqr_direct
+    fd.argtypes = [P, I64, I64, I64, I32, P, I64, P, I64, P, SZ, ctypes.POINTER(Opts), P]
+    fd.restype = ctypes.c_int
+    fr = _r_fn(lib)
+    rng = random.Random(1301107106)
+    for _ in range(3000):
+        ptrs = [rng.choice([_P16, _P16, _P16, None, _P8]) for _ in range(4)]  # A, Q (or R), R, work
+        n = rng.choice([1, 10, 25, 100, 0, 101])
+        m = rng.choice([n, 1000, 10**6, 5, 0, 2**62])
+        ld = rng.choice([n, n, n + 1])
+        dt = rng.choice([0, 1, 1, 7])
+        wb = rng.choice([1 << 40, 1 << 40, 64])
+        br, fo = rng.choice([0, 0, 5, 1000]), rng.choice([0, 0, 1, 2])
+        prec, res = rng.choice([0, 0, 1, 2, 3, 4, 5]), rng.choice([0, 0, 0, 1])
+        o = Opts(br, fo, 0, None, prec, res)
+        A, Q, R, W = ptrs
+        rest = (1 <= n <= 100 and n <= m <= 2**60 // max(n, 1) and ld == n and dt in (0, 1) and wb > 64
+                and res == 0 and 0 <= prec <= 4 and fo != 1 and (br == 0 or br >= n))
+        valid_r = rest and A == R == W == _P16   # tsqr_r takes no Q
+        valid_d = valid_r and Q == _P16
+        st_d = fd(A, m, n, ld, dt, Q, ld, R, ld, W, wb, ctypes.byref(o), None)
+        st_r = fr(A, m, n, ld, dt, R, ld, W, wb, ctypes.byref(o), None)
+        case = (ptrs, n, m, ld, dt, wb, br, fo, prec, res)
+        assert valid_d or st_d != 5, case
+        assert valid_r or st_r != 5, case
