@@ -45,6 +45,22 @@ FP32_PEAK_GFLOPS = 80540.0  # nominal GB300 FP32 CUDA-core rate (152 SMs x 128 F
 ALG_PASSES = {"direct": 4, "direct_native": 4, "cholqr": 3, "cholqr_ir": 6, "indirect": 3, "indirect_ir": 6, "backward": 5,
               "r_only": 1, "svd_values": 1}
 
+# The paper's own direct-TSQR job times (Sec. V-B, Table VI), reported
+# beside the GPU figures as context only: another method implementation,
+# machine and matrix size.  The cluster (Sec. V): Hadoop MapReduce on 10
+# nodes / 40 cores, one Intel Core i7-960 at 3.2 GHz, 24 GB of RAM and six
+# 2-TB disks per node, Gigabit Ethernet; Python (Dumbo) over Hadoop
+# streaming, every pass reading or writing HDFS.
+_PAPER_JOBS = [(4_000_000_000, 4, 6128), (2_500_000_000, 10, 4035), (600_000_000, 25, 1910),
+               (500_000_000, 50, 3090), (150_000_000, 100, 2154)]
+PAPER_CONTEXT = {
+    "source": "Sec. V-B, Table VI (job times, direct TSQR)",
+    "machine": "Hadoop MapReduce, 10 nodes / 40 cores (Intel Core i7-960 3.2 GHz, 24 GB RAM, 6 x 2 TB disks "
+               "per node, Gigabit Ethernet), Python/Dumbo over Hadoop streaming, data on HDFS",
+    "direct_tsqr": [{"m": m_, "n": n_, "job_s": t_, "rows_s": m_ / t_} for m_, n_, t_ in _PAPER_JOBS],
+    "note": "context only: not the target and not this workload",
+}
+
 WORKLOADS = {
     "sweep": dict(m=8_000_000, n=25, dtype="f64", kappa=1e15, block_rows=0, seed=ti.SEED_SWEEP,
                   name="stability-sweep matrix 8,000,000x25 FP64, A=G diag(sigma) V^T, "
@@ -469,6 +485,7 @@ def main():
         "step_fractions": {"step1": s1 / (s1 + s2 + s3), "step2": s2 / (s1 + s2 + s3),
                            "step3": s3 / (s1 + s2 + s3)},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "paper_context": PAPER_CONTEXT,
     }
 
     # The extras (other precision modes, comparators, the other

@@ -35,3 +35,15 @@ def test_reference_arm_prints_one_json_line():
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_paper_context_restates_table_vi():
+    """The paper's direct-TSQR job times (Sec. V-B, Table VI) reported as
+    context: rows/s = rows / job seconds (e.g. 600,000,000 x 25 in 1,910 s)."""
+    ctx = bench.PAPER_CONTEXT
+    json.dumps(ctx)
+    rows = {(r["m"], r["n"]): r for r in ctx["direct_tsqr"]}
+    assert rows[(600_000_000, 25)]["job_s"] == 1910
+    assert abs(rows[(600_000_000, 25)]["rows_s"] - 3.1414e5) < 1e2
+    assert abs(rows[(4_000_000_000, 4)]["rows_s"] - 6.527e5) < 1e2
+    assert len(rows) == 5 and "40 cores" in ctx["machine"]
