@@ -604,8 +604,10 @@ def stability_sweep(T, torch, dev, A15=None, steps=3, m=8_000_000, n=25, prec="a
     TSQR (the benchmarked mode and plain binary64), Cholesky QR, Cholesky QR +
     one refinement step and indirect TSQR + one refinement step;
     ||Q^T Q - I||_2 and ||A - QR||_F/||A||_F from the compensated device
-    checker, rows/s and algorithmic HBM GB/s of each."""
+    checker, rows/s, algorithmic HBM GB/s and its fraction of the measured
+    HBM peak of each."""
     timed = _timer(torch, steps)
+    hbm_peak, _ = load_peaks()
     methods = [("direct", lambda A: T.direct(A, check=False, prec=prec)),
                ("direct_native", lambda A: T.direct(A, check=False)),
                ("cholqr", lambda A: T.cholqr(A, refine=0, check=False)),
@@ -634,9 +636,10 @@ def stability_sweep(T, torch, dev, A15=None, steps=3, m=8_000_000, n=25, prec="a
                     st = e.status
                 if st == 0:
                     acc = T.accuracy(Qx, Rx, A)
+                    gbs = ALG_PASSES[name] * m * n * 8 / (ms * 1e-3) / 1e9
                     row[name] = {"orth_error_2": acc["orth_2"], "residual_F": acc["res_F"], "ms": ms,
-                                 "rows_s": m / (ms * 1e-3),
-                                 "hbm_gbs_algorithmic": ALG_PASSES[name] * m * n * 8 / (ms * 1e-3) / 1e9}
+                                 "rows_s": m / (ms * 1e-3), "hbm_gbs_algorithmic": gbs,
+                                 "hbm_frac": gbs / hbm_peak}
                 else:
                     row[name] = {"status": T.STATUS.get(st, st), "ms": ms}
                 del Qx

@@ -47,3 +47,88 @@ def test_paper_context_restates_table_vi():
     assert abs(rows[(600_000_000, 25)]["rows_s"] - 3.1414e5) < 1e2
     assert abs(rows[(4_000_000_000, 4)]["rows_s"] - 6.527e5) < 1e2
     assert len(rows) == 5 and "40 cores" in ctx["machine"]
+
+
+class _FakeEvent:
+    def __init__(self, enable_timing=False):
+        pass
+
+    def record(self):
+        pass
+
+    def elapsed_time(self, other):
+        return 2.0
+
+
+class _FakeTensor:
+    def __init__(self, a):
+        self.a = a
+
+    def to(self, dev):
+        return self
+
+
+class _FakeTorch:
+    class cuda:
+        Event = _FakeEvent
+
+        @staticmethod
+        def synchronize():
+            pass
+
+        @staticmethod
+        def empty_cache():
+            pass
+
+    @staticmethod
+    def from_numpy(a):
+        return _FakeTensor(a)
+
+
+class _FakeLib:
+    """Stands in for the CUDA binding: Cholesky QR breaks down from kappa
+    1e12 on, the way the method does (Sec. IV)."""
+    STATUS = {6: "TSQR_ERR_NOT_SPD"}
+
+    class TSQRError(RuntimeError):
+        def __init__(self, status):
+            super().__init__(status)
+            self.status = status
+
+    def _qr(self, A):
+        return A, None
+
+    def direct(self, A, check=True, prec="native"):
+        return self._qr(A)
+
+    def cholqr(self, A, refine=0, check=True):
+        kappa = float(A.a[0, 0])
+        if check and kappa >= 1e12:
+            raise self.TSQRError(6)
+        return self._qr(A)
+
+    def indirect_refine(self, A, refine=1, check=True):
+        return self._qr(A)
+
+    def accuracy(self, Q, R=None, A=None):
+        return {"orth_2": 1e-16, "orth_F": 1e-16, "res_F": 1e-16, "res_2": 1e-16}
+
+
+def test_stability_sweep_table_shape(monkeypatch):
+    """The bench's stability table (Sec. IV) run against stand-ins for torch
+    and the binding: one row per kappa, every method with its accuracy, rate,
+    algorithmic GB/s and HBM fraction, and a breakdown reported as a status."""
+    import numpy as np
+    monkeypatch.setattr(bench.ti, "conditioned", lambda m, n, kappa, seed: np.full((2, 2), kappa))
+    out = bench.stability_sweep(_FakeLib(), _FakeTorch, "cpu", A15=None, steps=2, m=1000, n=25)
+    assert list(out["by_kappa"]) == ["1e+00", "1e+04", "1e+08", "1e+12", "1e+15"]
+    peak, _ = bench.load_peaks()
+    for kappa, row in out["by_kappa"].items():
+        assert set(row) == {"direct", "direct_native", "cholqr", "cholqr_ir", "indirect_ir"}
+        for name, e in row.items():
+            assert "error" not in e, (kappa, name, e)
+            if name.startswith("cholqr") and float(kappa) >= 1e12:
+                assert e["status"] == "TSQR_ERR_NOT_SPD"
+                continue
+            assert e["ms"] == 1.0 and abs(e["rows_s"] - 1e6) < 1e-6
+            assert abs(e["hbm_frac"] - e["hbm_gbs_algorithmic"] / peak) < 1e-12
