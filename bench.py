@@ -491,33 +491,54 @@ def main():
     # The extras (other precision modes, comparators, the other
     # configurations, the CPU oracle) run on single-GPU runs only: under
     # torchrun every rank's GPU would stay held while rank 0 ran them.
+    # Each extra is guarded: its failure (an out-of-memory error in one of the
+    # large configurations, say) is recorded in the line, which is printed
+    # with the headline measurement whatever happens to the extras.
     extras_on = not args.no_extras and rank == 0 and ws == 1
     if extras_on:
         others = [p for p in (("native", "df64", "ozaki") if elem == 8 else ("native", "tf32x3"))
                   if p != resolved]
-        line["extras"] = extras(T, torch, A, n, m, dev, other_precs=others, prec=args.prec)
+        line["extras"] = guarded(torch, extras, T, torch, A, n, m, dev, other_precs=others, prec=args.prec)
     if extras_on:
         del Q, work, dbuf, work_h
         torch.cuda.empty_cache()
         is_sweep = args.workload == "sweep" and not args.m
-        configs = {"small_100kx10": small_config(T, torch, dev)}
+        configs = {"small_100kx10": guarded(torch, small_config, T, torch, dev)}
         if is_sweep:
-            configs["stability_sweep_8Mx25"] = stability_sweep(T, torch, dev, A15=A, prec=args.prec)
+            configs["stability_sweep_8Mx25"] = guarded(torch, stability_sweep, T, torch, dev, A15=A, prec=args.prec)
         del A
         torch.cuda.empty_cache()
-        configs.update(config_extras(T, torch, dev))
+        more = guarded(torch, config_extras, T, torch, dev)
+        if "error" in more:
+            configs["config_extras"] = more
+        else:
+            configs.update(more)
         line["configs"] = configs
     if extras_on:
-        line["cpu_baseline"] = cpu_baseline(A_host)
-        try:
-            line["cpu_baseline"]["configs"] = cpu_config_baselines()
-        except Exception as e:  # reported, not fatal
-            line["cpu_baseline"]["configs"] = {"error": f"{type(e).__name__}: {e}"}
+        cb = guarded(torch, cpu_baseline, A_host)
+        if "error" not in cb:
+            cb["configs"] = guarded(torch, cpu_config_baselines)
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def guarded(torch, fn, *args, **kw):
+    """fn(*args, **kw), or {"error": ...} when it raises (the device memory
+    its frames held is released before returning)."""
+    try:
+        return fn(*args, **kw)
+    except Exception as e:  # reported, not fatal
+        msg = f"{type(e).__name__}: {e}"
+    try:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    except Exception:  # the context itself may be unusable; the line is still printed
+        pass
+    return {"error": msg[:2000]}
 
 
 def _timer(torch, steps):

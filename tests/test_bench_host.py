@@ -132,3 +132,11 @@ def test_stability_sweep_table_shape(monkeypatch):
                 continue
             assert e["ms"] == 1.0 and abs(e["rows_s"] - 1e6) < 1e-6
             assert abs(e["hbm_frac"] - e["hbm_gbs_algorithmic"] / peak) < 1e-12
+
+
+def test_guarded_extras_record_errors_instead_of_raising():
+    def boom(x, y=0):
+        raise MemoryError(f"out of memory {x} {y}")
+    out = bench.guarded(_FakeTorch, boom, 3, y=4)
+    assert out == {"error": "MemoryError: out of memory 3 4"}
+    assert bench.guarded(_FakeTorch, lambda a, b: {"v": a + b}, 1, 2) == {"v": 3}
