@@ -22,6 +22,30 @@ the pins); this module only compiles it with gcc and marshals numpy arrays.
 * pins: ``mgs_ld``, ``chol_gram_ld``, ``jacobi_svd_ld``, ``sym_eig``.
 * checkers: ``orth_error`` (||Q^TQ-I||_2, _F), ``residual`` (||A-QR||_F/||A||_F,
   ||A-QR||_2/||R||_2), ``gram_dot2``.
+
+Every function is pinned to something other than itself (tests/test_oracle.py;
+no function here is "parity unpinned"):
+
+* ``householder_qr`` / ``householder_r``: the n = 1 closed form; exactly
+  orthonormal columns give Q = A, R = I; diagonal scaling and row
+  permutation; uniqueness against the long-double Cholesky factor of A^T A
+  (Sec. II-A); long-double MGS; numpy's LAPACK QR run as a library; the
+  block identity of the paper's 4-block example (Sec. III-B); the any-tree R
+  of Sec. II-B; a zero column; square A.
+* ``cholqr``: a known factorisation A = Q0 R0; breakdown on rank deficiency;
+  loss of orthogonality with kappa and its repair by refinement (Sec. IV).
+* ``indirect_refine``: agreement at kappa = 1, loss without refinement; the
+  combine R = R2 R1 at kappa 1e6 and 1e10, where the swapped order fails.
+* ``svd``: known singular values (Hadamard x diag x V), a diagonal matrix,
+  long-double eigenvalues of A^T A, the sign and ordering conventions.
+* ``qr_backward``: full and directional central finite differences at
+  2,000 x 8, the n = 1 closed form, torch-CPU autograd, zero cotangents.
+* ``orth_error`` / ``residual`` / ``gram_dot2`` / ``sym_eig``: known answers
+  (Q = H (I + delta E) with diagonal and off-diagonal E; a rank-one residual
+  of known 2-norm; Dot2 cancellation and a product's rounding error; the
+  2 x 2 closed form); the pins ``mgs_ld`` and ``chol_gram_ld`` are checked for
+  their own accuracy at kappa 1e12.
+* the OpenMP loops: bit-identical to the serial oracle at 1 and 4 threads.
 """
 from __future__ import annotations
 
