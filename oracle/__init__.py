@@ -43,8 +43,8 @@ no function here is "parity unpinned"):
 * ``orth_error`` / ``residual`` / ``gram_dot2`` / ``sym_eig``: known answers
   (Q = H (I + delta E) with diagonal and off-diagonal E; a rank-one residual
   of known 2-norm; Dot2 cancellation and a product's rounding error; the
-  2 x 2 closed form); the pins ``mgs_ld`` and ``chol_gram_ld`` are checked for
-  their own accuracy at kappa 1e12.
+  2 x 2 closed form); the pin ``mgs_ld`` is checked for its own
+  orthogonality and residual at kappa 1e12.
 * the OpenMP loops: bit-identical to the serial oracle at 1 and 4 threads.
 """
 from __future__ import annotations
